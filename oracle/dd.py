@@ -1,0 +1,487 @@
+"""FP64 CPU oracle of entropic domain decomposition for optimal transport.
+
+TEST INFRASTRUCTURE ONLY. Only tests/, __graft_entry__.smoke() and bench.py's
+CPU-baseline / reference leg may import this module. The CUDA library never
+imports, links or calls it, and this module shares no code with it.
+
+It follows Bonafini & Schmitzer, "Domain decomposition for entropy regularized
+optimal transport":
+
+* the problem: minimise ε·KL(π|K) over couplings π of μ and ν, with
+  K = exp(−c/ε)·(μ⊗ν) (§2.2, eq. EntropicOTPrimal; §3 eq. Problem);
+* Algorithm 2 (practical domain decomposition, §6.1): for every composite cell J
+  of the current partition, ν_cell = Σ_{i∈J} ν_i, a Sinkhorn solve on
+  (μ_J, ν_cell) warm-started from u_{C,J}, extraction of the new basic
+  Y-marginals ν_i = P_Y(π_cell restricted to X_i × Y), BalanceMeasures and
+  Truncate;
+* the Sinkhorn solver and its stopping rule (§6.2): start with a Y-iteration,
+  stop when the L1 error of the X-marginal after a Y-iteration is at most
+  ‖μ_J‖·Err, so the last step is always a Y-iteration;
+* the multi-scale scheme (§6.4): coarse images are push-forwards under the
+  quad-tree parent map, fine basic marginals are initialised by eq.
+  FineBasicMarginals, and ε·log u is kept fixed when ε changes;
+* basic/composite partitions for images (§7.1): s×s basic cells, partition A
+  of 2×2 blocks, partition B the same blocks shifted by one basic cell.
+
+Potentials are kept in the counting-measure form f = α + ε·log μ,
+g = β + ε·log ν with π(x,y) = exp((f(x) + g(y) − c(x,y))/ε); α = ε·log u and
+β = ε·log v are the paper's scalings in log form. With fixed marginals the
+minimiser does not depend on this choice of reference measure.
+
+Readings of points the paper leaves open (each is listed with its reason in
+the design notes of the repository):
+
+* BalanceMeasures (§6.2): surplus cells (‖ν_i‖ > ‖μ_i‖) give up the fraction
+  d_i/‖ν_i‖ of every entry; the removed mass is shared among deficit cells in
+  proportion to their deficits. This keeps non-negativity, the sum Σ_i ν_i and
+  the support, as the paper requires.
+* Truncate (§6.1 item (ii), §7.1): entries of ν_i not above the absolute
+  threshold (1e-15) are dropped.
+* Dual refinement (§6.4 ends with "glue, then interpolate linearly in log
+  space"): without gluing, each fine pixel takes the coarse α of its parent
+  pixel plus a first-order correction from finite differences of α inside the
+  parent's composite cell (central differences inside, one-sided at the cell
+  edge). Both partitions at the new level start from this α (Algorithm 2,
+  input u).
+* Composite cells that consist of one basic cell (corners of partition B) are
+  solved like the others; Example 3.3 shows it is redundant for the basic
+  marginals, and solving keeps the duals of partition B complete.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+# ----------------------------------------------------------------------------
+# parameters
+# ----------------------------------------------------------------------------
+@dataclass
+class Params:
+    err: float = 1e-6          # Sinkhorn stopping threshold Err (§6.2)
+    max_iter: int = 10000      # cap on Sinkhorn iterations per cell solve
+    trunc: float = 1e-15       # Truncate threshold on ν_i entries (§7.1)
+    balance: bool = True       # run BalanceMeasures (§6.2)
+
+
+# ----------------------------------------------------------------------------
+# a generic discrete problem with a basic partition (§3, Def. 3.1)
+# ----------------------------------------------------------------------------
+class Problem:
+    """μ on X, ν on Y, a cost function and a basic partition of X.
+
+    basic: list of integer arrays, basic[i] = indices of the points of X_i.
+    parts: dict name -> list of composite cells, each a list of basic indices.
+    cost(X, Y): matrix c(x, y) for index arrays X (rows) and Y (columns).
+    """
+
+    def __init__(self, mu, nu, cost, basic, parts):
+        self.mu = np.asarray(mu, dtype=np.float64).ravel()
+        self.nu = np.asarray(nu, dtype=np.float64).ravel()
+        self.cost = cost
+        self.basic = [np.asarray(b, dtype=np.int64) for b in basic]
+        self.parts = parts
+        self.basic_mass = np.array([self.mu[b].sum() for b in self.basic])
+        if np.any(self.basic_mass <= 0):
+            raise ValueError("every basic cell needs positive mass (Def. 3.1)")
+
+    def cell_points(self, J):
+        return np.concatenate([self.basic[i] for i in J])
+
+
+def matrix_problem(mu, nu, C, basic, parts):
+    """Problem with an explicit cost matrix C[x, y]."""
+    C = np.asarray(C, dtype=np.float64)
+    return Problem(mu, nu, lambda X, Y: C[np.ix_(X, Y)], basic, parts)
+
+
+# ----------------------------------------------------------------------------
+# images: pixels, basic cells, partitions A and B (§7.1)
+# ----------------------------------------------------------------------------
+def grid_basic_cells(n, b):
+    """b×b pixel blocks in row-major order of blocks; pixels row-major inside."""
+    nb = n // b
+    cells = []
+    for r in range(nb):
+        for s in range(nb):
+            ii = np.arange(r * b, (r + 1) * b)
+            jj = np.arange(s * b, (s + 1) * b)
+            cells.append((ii[:, None] * n + jj[None, :]).ravel())
+    return cells
+
+
+def grid_partitions(nb):
+    """Partition A: 2×2 blocks of basic cells. Partition B: the same blocks
+    shifted by one basic cell, so it has single cells at the corners and 2×1
+    blocks along the edges (§7.1 "Basic and composite partitions")."""
+    A, B = [], []
+    for a in range(nb // 2):
+        for c in range(nb // 2):
+            A.append([r * nb + s for r in (2 * a, 2 * a + 1) for s in (2 * c, 2 * c + 1)])
+    for a in range(nb // 2 + 1):
+        for c in range(nb // 2 + 1):
+            rr = [r for r in (2 * a - 1, 2 * a) if 0 <= r < nb]
+            cc = [s for s in (2 * c - 1, 2 * c) if 0 <= s < nb]
+            B.append([r * nb + s for r in rr for s in cc])
+    return {"A": A, "B": B}
+
+
+class GridProblem(Problem):
+    """Two n×n images on [0,1]² (pixel spacing `spacing`), cost |x−y|²."""
+
+    def __init__(self, mu_img, nu_img, b, spacing):
+        n = mu_img.shape[0]
+        self.n, self.b, self.spacing = n, b, spacing
+        self.nb = n // b
+        if n % b or self.nb % 2:
+            raise ValueError("n/b must be an even integer")
+        d2 = spacing * spacing
+
+        def cost(X, Y):
+            xi, xj = np.divmod(X, n)
+            yi, yj = np.divmod(Y, n)
+            return d2 * ((xi[:, None] - yi[None, :]) ** 2 + (xj[:, None] - yj[None, :]) ** 2).astype(np.float64)
+
+        super().__init__(mu_img, nu_img, cost, grid_basic_cells(n, b), grid_partitions(self.nb))
+
+
+def pyramid(img, levels):
+    """[coarsest, …, finest]: each coarse pixel holds the mass of its four
+    children (push-forward under the quad-tree parent map, §6.4, §7.1)."""
+    out = [np.asarray(img, dtype=np.float64)]
+    for _ in range(levels - 1):
+        a = out[0]
+        m = a.shape[0] // 2
+        out.insert(0, a.reshape(m, 2, m, 2).sum(axis=(1, 3)))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# the cell solver (§6.2) in log form
+# ----------------------------------------------------------------------------
+def logsumexp(a, axis):
+    m = a.max(axis=axis, keepdims=True)
+    return (m + np.log(np.exp(a - m).sum(axis=axis, keepdims=True))).squeeze(axis)
+
+
+def sinkhorn_cell(C, mu_x, nu_y, f, eps, err, max_iter):
+    """Sinkhorn on one composite cell, warm-started from f (Remark 2.4, §6.2).
+
+    Y-iteration: g(y) = ε·log ν(y) − ε·log Σ_x exp((f(x) − c(x,y))/ε)
+    X-iteration: f(x) = ε·log μ(x) − ε·log Σ_y exp((g(y) − c(x,y))/ε)
+    After each Y-iteration the X-marginal error Σ_x |P_X π(x) − μ(x)| is
+    compared with ‖μ_J‖·Err; the solver stops on a Y-iteration.
+    Returns f, g, the plan P (|X|×|Y|), the number of Y-iterations and the
+    final X-marginal error.
+    """
+    logmu, lognu = np.log(mu_x), np.log(nu_y)
+    tol = err * mu_x.sum()
+    it = 0
+    while True:
+        it += 1
+        g = eps * lognu - eps * logsumexp((f[:, None] - C) / eps, axis=0)
+        P = np.exp((f[:, None] + g[None, :] - C) / eps)
+        err_x = np.abs(P.sum(axis=1) - mu_x).sum()
+        if err_x <= tol or it >= max_iter:
+            return f, g, P, it, err_x
+        f = eps * logmu - eps * logsumexp((g[None, :] - C) / eps, axis=1)
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 2 building blocks
+# ----------------------------------------------------------------------------
+def gather(rows, J):
+    """ν_cell = Σ_{i∈J} ν_i on the union of the supports (Algorithm 2)."""
+    cols = np.unique(np.concatenate([rows[i][0] for i in J]))
+    nu_cell = np.zeros(cols.size)
+    for i in J:
+        nu_cell[np.searchsorted(cols, rows[i][0])] += rows[i][1]
+    return cols, nu_cell
+
+
+def balance_measures(parts, targets):
+    """BalanceMeasures (§6.2), proportional reading (see module docstring).
+
+    parts: list of arrays ν_i on a common support; targets: ‖μ_i‖.
+    Modifies parts in place; returns them.
+    """
+    m = np.array([p.sum() for p in parts])
+    d = m - np.asarray(targets)
+    sur = [k for k in range(len(parts)) if d[k] > 0]
+    dfc = [k for k in range(len(parts)) if d[k] < 0]
+    if not sur or not dfc:
+        return parts
+    delta = np.zeros_like(parts[0])
+    for k in sur:
+        take = parts[k] * (d[k] / m[k])
+        parts[k] = parts[k] - take
+        delta += take
+    dtot = -d[dfc].sum()
+    for k in dfc:
+        parts[k] = parts[k] + delta * (-d[k] / dtot)
+    return parts
+
+
+@dataclass
+class SweepInfo:
+    cost: float = 0.0                  # Σ_J ⟨c, π_J⟩
+    err_x: float = 0.0                 # Σ_J Σ_x |P_X π_J(x) − μ(x)|
+    iters: list = field(default_factory=list)
+    truncated_mass: float = 0.0
+
+
+def half_sweep(prob, part, rows, alpha, eps, params, plans=None):
+    """One iteration of Algorithm 2 over the composite partition `part`.
+
+    rows: list over basic cells of (cols sorted int array, vals float array).
+    alpha: array over X holding α = ε·log u_{C,J} for this partition; updated
+    in place. Returns the new rows and a SweepInfo. If `plans` is a dict, the
+    cell plans are stored there as plans[J index] = (X, cols, P).
+    """
+    new_rows = list(rows)
+    info = SweepInfo()
+    for jn, J in enumerate(prob.parts[part]):
+        cols, nu_cell = gather(rows, J)
+        X = prob.cell_points(J)
+        mu_x = prob.mu[X]
+        C = prob.cost(X, cols)
+        f0 = alpha[X] + eps * np.log(mu_x)
+        f, g, P, it, err_x = sinkhorn_cell(C, mu_x, nu_cell, f0, eps, params.err, params.max_iter)
+        alpha[X] = f - eps * np.log(mu_x)
+        info.cost += float((C * P).sum())
+        info.err_x += float(err_x)
+        info.iters.append(it)
+        if plans is not None:
+            plans[jn] = (X, cols, P)
+        # extraction of the new basic marginals
+        parts, o = [], 0
+        for i in J:
+            k = prob.basic[i].size
+            parts.append(P[o:o + k].sum(axis=0))
+            o += k
+        if params.balance:
+            balance_measures(parts, [prob.basic_mass[i] for i in J])
+        for i, v in zip(J, parts):
+            keep = v > params.trunc
+            info.truncated_mass += float(v[~keep].sum())
+            new_rows[i] = (cols[keep], v[keep])
+    return new_rows, info
+
+
+def product_state(prob):
+    """ν_i = ‖μ_i‖·ν on all of Y: the product coupling μ⊗ν (§6.4)."""
+    cols = np.arange(prob.nu.size)
+    return [(cols.copy(), m * prob.nu) for m in prob.basic_mass]
+
+
+def rows_from_csr(row_ptr, col, val):
+    return [(np.asarray(col[row_ptr[k]:row_ptr[k + 1]], dtype=np.int64),
+             np.asarray(val[row_ptr[k]:row_ptr[k + 1]], dtype=np.float64))
+            for k in range(len(row_ptr) - 1)]
+
+
+def rows_to_dense(rows, ny):
+    D = np.zeros((len(rows), ny))
+    for k, (c, v) in enumerate(rows):
+        D[k, c] = v
+    return D
+
+
+def y_marginal_error(prob, rows):
+    """Σ_y |Σ_i ν_i(y) − ν(y)| (L1 error of the Y-marginal)."""
+    s = np.zeros(prob.nu.size)
+    for c, v in rows:
+        np.add.at(s, c, v)
+    return float(np.abs(s - prob.nu).sum())
+
+
+# ----------------------------------------------------------------------------
+# the coupling behind a state, objective values (Lemma 4.2, Prop. 2.5)
+# ----------------------------------------------------------------------------
+def partition_plan(prob, part, rows, alpha, eps):
+    """π = Σ_J π_J for the partition solved last: on each cell, f from
+    α_{C,J} and one Y-iteration against ν_cell (so P_Y π = ν exactly).
+    Returns a dense |X|×|Y| array (small problems only)."""
+    P = np.zeros((prob.mu.size, prob.nu.size))
+    for J in prob.parts[part]:
+        cols, nu_cell = gather(rows, J)
+        X = prob.cell_points(J)
+        C = prob.cost(X, cols)
+        f = alpha[X] + eps * np.log(prob.mu[X])
+        g = eps * np.log(nu_cell) - eps * logsumexp((f[:, None] - C) / eps, axis=0)
+        P[np.ix_(X, cols)] = np.exp((f[:, None] + g[None, :] - C) / eps)
+    return P
+
+
+def partition_plan_sparse(prob, part, rows, alpha, eps, trunc=0.0):
+    """Same coupling as partition_plan as (row_ptr, col, val) over X pixels,
+    keeping entries above `trunc`."""
+    per_x = {}
+    for J in prob.parts[part]:
+        cols, nu_cell = gather(rows, J)
+        X = prob.cell_points(J)
+        C = prob.cost(X, cols)
+        f = alpha[X] + eps * np.log(prob.mu[X])
+        g = eps * np.log(nu_cell) - eps * logsumexp((f[:, None] - C) / eps, axis=0)
+        P = np.exp((f[:, None] + g[None, :] - C) / eps)
+        for r, x in enumerate(X):
+            keep = P[r] > trunc
+            per_x[int(x)] = (cols[keep], P[r][keep])
+    nx = prob.mu.size
+    row_ptr = np.zeros(nx + 1, dtype=np.int64)
+    cs, vs = [], []
+    for x in range(nx):
+        c, v = per_x.get(x, (np.zeros(0, np.int64), np.zeros(0)))
+        row_ptr[x + 1] = row_ptr[x] + c.size
+        cs.append(c)
+        vs.append(v)
+    return row_ptr, np.concatenate(cs), np.concatenate(vs)
+
+
+def kl_minus_mass(P, C, mu, nu, eps):
+    """KL(π|K) − ‖K‖ = Σ_{π>0} π·(log π − log K − 1), K = e^{−c/ε}·μ⊗ν
+    (Definition 2.1 with φ(s) = s log s − s + 1; ‖K‖ is the constant that the
+    paper subtracts in eq. RelPDGap)."""
+    m = P > 0
+    logK = -C / eps + np.log(mu)[:, None] + np.log(nu)[None, :]
+    return float((P[m] * (np.log(P[m]) - logK[m] - 1.0)).sum())
+
+
+def kernel_mass(C, mu, nu, eps):
+    """‖K‖ = Σ_{x,y} e^{−c(x,y)/ε} μ(x) ν(y)."""
+    return float((np.exp(-C / eps) * mu[:, None] * nu[None, :]).sum())
+
+
+def kl_div(P, Q):
+    """KL(P|Q) for non-negative arrays with supp P ⊂ supp Q (Definition 2.1)."""
+    m = P > 0
+    return float((P[m] * np.log(P[m] / Q[m])).sum() - P.sum() + Q.sum())
+
+
+def dual_objective(alpha, beta, mu_hat, nu_hat, C, mu, nu, eps):
+    """J(u,v) of eq. EntropicOTDualObjective with log u = α/ε, log v = β/ε:
+    ⟨μ̂, log u⟩ + ⟨ν̂, log v⟩ − Σ u⊗v·K + ‖K‖."""
+    K = np.exp(-C / eps) * mu[:, None] * nu[None, :]
+    uv = np.exp((alpha[:, None] + beta[None, :]) / eps)
+    return float(mu_hat @ (alpha / eps) + nu_hat @ (beta / eps) - (uv * K).sum() + K.sum())
+
+
+# ----------------------------------------------------------------------------
+# multi-scale: refinement of the basic marginals and of the duals (§6.4)
+# ----------------------------------------------------------------------------
+def refine_basic_marginals(coarse, fine, rows_c):
+    """Eq. FineBasicMarginals: ν_i⁰(y) = ν(y)·ν̂_{Pa(i)}(pa(y))/ν̂(pa(y))·μ(X_i)/μ̂(X̂_{Pa(i)}).
+
+    coarse, fine: GridProblem at two consecutive levels with the same b, so a
+    coarse basic cell (r, s) is the parent of fine cells (2r+{0,1}, 2s+{0,1})
+    and a coarse pixel (p, q) the parent of fine pixels (2p+{0,1}, 2q+{0,1}).
+    """
+    nc, nf = coarse.n, fine.n
+    nbc, nbf = coarse.nb, fine.nb
+    rows_f = [None] * (nbf * nbf)
+    for R in range(nbf):
+        for S in range(nbf):
+            i = R * nbf + S
+            j = (R // 2) * nbc + (S // 2)
+            cc, vc = rows_c[j]
+            pi, pj = np.divmod(cc, nc)
+            ys, ws = [], []
+            for di in (0, 1):
+                for dj in (0, 1):
+                    y = (2 * pi + di) * nf + (2 * pj + dj)
+                    ys.append(y)
+                    ws.append(fine.nu[y] * vc / coarse.nu[cc] * fine.basic_mass[i] / coarse.basic_mass[j])
+            y = np.concatenate(ys)
+            w = np.concatenate(ws)
+            o = np.argsort(y, kind="stable")
+            rows_f[i] = (y[o], w[o])
+    return rows_f
+
+
+def _fd(a, axis):
+    """Finite differences along one axis: central inside, one-sided at the
+    edges, zero when the extent is 1."""
+    k = a.shape[axis]
+    if k == 1:
+        return np.zeros_like(a)
+    d = np.empty_like(a)
+    a_ = np.moveaxis(a, axis, 0)
+    d_ = np.moveaxis(d, axis, 0)
+    d_[0] = a_[1] - a_[0]
+    d_[-1] = a_[-1] - a_[-2]
+    if k > 2:
+        d_[1:-1] = 0.5 * (a_[2:] - a_[:-2])
+    return d
+
+
+def refine_duals(coarse, fine, alpha_c, part):
+    """Dual initialisation at the next level (reading of §6.4, see module
+    docstring): per composite cell of `part` at the coarse level, the fine
+    children of a coarse pixel p get α(p) ± ¼·∂α(p) along each axis."""
+    nc, nf, b = coarse.n, fine.n, coarse.b
+    alpha_f = np.empty(nf * nf)
+    A2 = alpha_c.reshape(nc, nc)
+    for J in coarse.parts[part]:
+        rs = sorted({i // coarse.nb for i in J})
+        ss = sorted({i % coarse.nb for i in J})
+        r0, r1 = rs[0] * b, (rs[-1] + 1) * b
+        s0, s1 = ss[0] * b, (ss[-1] + 1) * b
+        blk = A2[r0:r1, s0:s1]
+        dr, ds = _fd(blk, 0), _fd(blk, 1)
+        for di, orr in ((0, -0.25), (1, 0.25)):
+            for dj, oss in ((0, -0.25), (1, 0.25)):
+                val = blk + orr * dr + oss * ds
+                R = 2 * np.arange(r0, r1) + di
+                S = 2 * np.arange(s0, s1) + dj
+                alpha_f[(R[:, None] * nf + S[None, :]).ravel()] = val.ravel()
+    return alpha_f
+
+
+# ----------------------------------------------------------------------------
+# the full coarse-to-fine run
+# ----------------------------------------------------------------------------
+@dataclass
+class RunResult:
+    prob: GridProblem
+    rows: list
+    alpha: dict
+    eps: float
+    last_part: str
+    history: list
+
+
+def run_schedule(mu_img, nu_img, b, levels, schedule, params, *, on_half_sweep=None):
+    """Algorithm 2 inside the multi-scale / ε-scaling driver (§6.4).
+
+    schedule: list of (eps, sweeps, level); level 0 is the coarsest image,
+    levels-1 the input resolution. One sweep = a half-sweep on A then on B.
+    The run starts at level 0 from the product coupling with α = 0.
+    """
+    mus, nus = pyramid(mu_img, levels), pyramid(nu_img, levels)
+    n = mu_img.shape[0]
+    lev = 0
+
+    def level_problem(l):
+        return GridProblem(mus[l], nus[l], b, 2.0 ** (levels - 1 - l) / n)
+
+    prob = level_problem(0)
+    rows = product_state(prob)
+    alpha = {"A": np.zeros(prob.mu.size), "B": np.zeros(prob.mu.size)}
+    history, eps, last = [], None, "B"
+    for eps_s, sweeps, L in schedule:
+        while lev < L:
+            fine = level_problem(lev + 1)
+            rows = refine_basic_marginals(prob, fine, rows)
+            a0 = refine_duals(prob, fine, alpha[last], last)
+            alpha = {"A": a0.copy(), "B": a0.copy()}
+            prob, lev = fine, lev + 1
+        eps = eps_s
+        for _ in range(sweeps):
+            for part in ("A", "B"):
+                rows, info = half_sweep(prob, part, rows, alpha[part], eps, params)
+                last = part
+                history.append((lev, eps, part, info))
+                if on_half_sweep is not None:
+                    on_half_sweep(prob, part, rows, alpha[part], eps, info)
+    return RunResult(prob, rows, alpha, eps, last, history)

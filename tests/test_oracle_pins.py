@@ -1,0 +1,376 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test names what it pins. None of them compares the oracle with itself:
+the references are an independent full-problem Sinkhorn (scaling form), an LP
+solver, the rate bound of Theorem 4.1, the odd-even transposition sort of §5,
+the identities of Lemmas 4.2/4.3, Proposition 2.5 and Proposition 6.1, and
+closed forms.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dd, referees
+from paper_2001_10986_gb300 import synthetic as syn
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _grid(n, b, blobs, seed):
+    mu = syn.gaussian_mixture(n, blobs, 2 * seed)
+    nu = syn.gaussian_mixture(n, blobs, 2 * seed + 1)
+    return dd.GridProblem(mu, nu, b, 1.0 / n)
+
+
+def _full_cost(prob):
+    return prob.cost(np.arange(prob.mu.size), np.arange(prob.nu.size))
+
+
+# --------------------------------------------------------------------------
+# cell solver: one composite cell covering X is plain Sinkhorn (textbook)
+# --------------------------------------------------------------------------
+def test_single_cell_is_plain_sinkhorn():
+    prob = _grid(8, 4, 2, 0)           # 2×2 basic cells: partition A = one cell
+    eps = 0.02
+    alpha = np.zeros(64)
+    rows, info = dd.half_sweep(prob, "A", dd.product_state(prob), alpha, eps,
+                               dd.Params(err=1e-12, trunc=0.0))
+    P = dd.partition_plan(prob, "A", rows, alpha, eps)
+    Pr, _, _ = referees.sinkhorn_scaling(prob.mu, prob.nu, _full_cost(prob), eps)
+    assert np.abs(P - Pr).sum() / Pr.sum() < 1e-9
+    # the stored marginals are the row sums of that plan over each basic cell
+    for i, X in enumerate(prob.basic):
+        c, v = rows[i]
+        np.testing.assert_allclose(v, Pr[X][:, c].sum(axis=0), rtol=1e-8, atol=1e-13)
+
+
+def test_sinkhorn_cell_ends_on_y_iteration():
+    rng = np.random.default_rng(3)
+    C = rng.uniform(0, 1, (5, 7))
+    mu = rng.uniform(0.5, 1, 5); mu /= mu.sum()
+    nu = rng.uniform(0.5, 1, 7); nu /= nu.sum()
+    f, g, P, it, ex = dd.sinkhorn_cell(C, mu, nu, np.zeros(5), 0.1, 1e-3, 3)
+    np.testing.assert_allclose(P.sum(axis=0), nu, rtol=1e-13)       # Y exact
+    assert ex == pytest.approx(np.abs(P.sum(axis=1) - mu).sum(), rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# global optimality: converged DD at fixed ε equals the full Sinkhorn solution
+# --------------------------------------------------------------------------
+def test_converged_dd_equals_global_sinkhorn():
+    prob = _grid(8, 2, 2, 1)            # 4×4 basic cells, 4 A cells, 9 B cells
+    eps = 0.03
+    Pr, _, _ = referees.sinkhorn_scaling(prob.mu, prob.nu, _full_cost(prob), eps)
+    rows = dd.product_state(prob)
+    alpha = {"A": np.zeros(64), "B": np.zeros(64)}
+    par = dd.Params(err=1e-12, trunc=0.0, max_iter=5000)
+    for _ in range(60):
+        for part in "AB":
+            rows, _ = dd.half_sweep(prob, part, rows, alpha[part], eps, par)
+    P = dd.partition_plan(prob, "B", rows, alpha["B"], eps)
+    assert np.abs(P - Pr).sum() / Pr.sum() < 1e-8
+
+
+# --------------------------------------------------------------------------
+# ε → 0: entropic cost is within ε·min(H(μ),H(ν)) above the LP optimum
+# --------------------------------------------------------------------------
+def test_small_eps_against_lp():
+    prob = _grid(8, 2, 2, 2)            # 64 pixels
+    C = _full_cost(prob)
+    lp_cost, _ = referees.lp_optimum(prob.mu, prob.nu, C)
+    H = min(-(prob.mu * np.log(prob.mu)).sum(), -(prob.nu * np.log(prob.nu)).sum())
+    rows = dd.product_state(prob)
+    alpha = {"A": np.zeros(64), "B": np.zeros(64)}
+    par = dd.Params(err=1e-10, trunc=0.0, max_iter=20000)
+    for eps, sweeps, _ in syn.halving_schedule(0.05, 0.05 / 16, 20):
+        for _ in range(sweeps):
+            for part in "AB":
+                rows, info = dd.half_sweep(prob, part, rows, alpha[part], eps, par)
+        cost = info.cost
+        # ⟨c, π_ε⟩ ≥ C* by feasibility; ⟨c, π_ε⟩ − C* ≤ ε·KL(π_0|μ⊗ν) ≤ ε·H
+        assert cost >= lp_cost - 1e-9
+        assert cost - lp_cost <= eps * H * (1 + 1e-6) + 1e-9
+
+
+# --------------------------------------------------------------------------
+# worst-case examples of §4.3 (golden setups from Fig. WorstCaseSetup)
+# --------------------------------------------------------------------------
+def _three_cell_deltas(eps, q, n_iter):
+    g = json.load(open(os.path.join(GOLDEN, "three_cell_worst_case.json")))
+    C = np.array(g["cost"], dtype=float)
+    p = (1 - q) / 2
+    mu = np.array([p, q, p]); nu = mu.copy()
+    prob = dd.matrix_problem(mu, nu, C, [[0], [1], [2]],
+                             {"A": [[0, 1], [2]], "B": [[0], [1, 2]]})
+    # π⁰ = p·δ(1,3) + q·δ(2,2) + p·δ(3,1)
+    rows = [(np.array([2]), np.array([p])), (np.array([1]), np.array([q])),
+            (np.array([0]), np.array([p]))]
+    alpha = {"A": np.zeros(3), "B": np.zeros(3)}
+    Pr, _, _ = referees.sinkhorn_scaling(mu, nu, C, eps, tol=1e-15)
+    kl_star = dd.kl_minus_mass(Pr, C, mu, nu, eps)
+    par = dd.Params(err=1e-14, trunc=0.0, max_iter=100000)
+    D = []
+    for l in range(n_iter):
+        part = "AB"[l % 2]
+        rows, _ = dd.half_sweep(prob, part, rows, alpha[part], eps, par)
+        P = dd.partition_plan(prob, part, rows, alpha[part], eps)
+        D.append(dd.kl_minus_mass(P, C, mu, nu, eps) - kl_star)
+    return np.array(D), float(g["cost_sup_norm"])
+
+
+@pytest.mark.parametrize("eps", [3.0, 5.0, 10.0, 20.0])
+def test_three_cell_rate_bound_eps(eps):
+    q = 0.3
+    D, cn = _three_cell_deltas(eps, q, 40)
+    bound = 1.0 / (1.0 + np.exp(-2 * cn / eps) * q / (1 - q))   # eq. LambdaBound
+    ok = D[:-1] > 1e-11
+    lam = D[1:][ok] / D[:-1][ok]
+    assert lam.size >= 3
+    assert np.all(D[1:][ok] >= -1e-12)
+    assert np.all(lam <= bound * (1 + 1e-9))
+
+
+@pytest.mark.parametrize("q", [0.1, 0.3, 0.5])
+def test_three_cell_rate_bound_q(q):
+    eps = 10.0                                                   # Example 4.11
+    D, cn = _three_cell_deltas(eps, q, 40)
+    ok = D[:-1] > 1e-11
+    lam = D[1:][ok] / D[:-1][ok]
+    # eq. LambdaBoundQ: λ(q)⁻¹ − 1 ≥ e^{−2‖c‖/ε}·q/(1−q)
+    assert np.all(1.0 / lam - 1.0 >= np.exp(-2 * cn / eps) * q / (1 - q) * (1 - 1e-9))
+
+
+def test_three_cell_rate_slows_with_smaller_eps():
+    lam = []
+    for eps in (2.0, 4.0, 8.0):
+        D, _ = _three_cell_deltas(eps, 0.3, 40)
+        ok = D[:-1] > 1e-11
+        lam.append(np.median(D[1:][ok] / D[:-1][ok]))
+    assert lam[0] > lam[1] > lam[2]
+
+
+def test_chain_rate_increases_with_n():
+    g = json.load(open(os.path.join(GOLDEN, "chain_worst_case.json")))
+    eps = g["eps"]
+    lams = []
+    for N in (4, 6, 8):
+        C = np.full((N, N), float(g["cost_other"]))
+        np.fill_diagonal(C, g["cost_diag"])
+        C[0, N - 1] = C[N - 1, 0] = g["cost_corner"]
+        mu = np.full(N, 1.0 / N); nu = mu.copy()
+        A = [[k, k + 1] for k in range(0, N, 2)]
+        B = [[0]] + [[k, k + 1] for k in range(1, N - 1, 2)] + [[N - 1]]
+        prob = dd.matrix_problem(mu, nu, C, [[k] for k in range(N)], {"A": A, "B": B})
+        sigma = list(range(N)); sigma[0], sigma[N - 1] = N - 1, 0
+        rows = [(np.array([sigma[k]]), np.array([1.0 / N])) for k in range(N)]
+        alpha = {"A": np.zeros(N), "B": np.zeros(N)}
+        Pr, _, _ = referees.sinkhorn_scaling(mu, nu, C, eps, tol=1e-15)
+        kls = dd.kl_minus_mass(Pr, C, mu, nu, eps)
+        par = dd.Params(err=1e-12, trunc=0.0, max_iter=2000)
+        D = []
+        for l in range(60):
+            part = "AB"[l % 2]
+            rows, _ = dd.half_sweep(prob, part, rows, alpha[part], eps, par)
+            P = dd.partition_plan(prob, part, rows, alpha[part], eps)
+            D.append(dd.kl_minus_mass(P, C, mu, nu, eps) - kls)
+        D = np.array(D)
+        ok = D[:-2] > 1e-10
+        lams.append(np.median((D[2:][ok] / D[:-2][ok])))   # per A+B sweep
+    assert lams[0] < lams[1] < lams[2] < 1.0
+
+
+# --------------------------------------------------------------------------
+# §5: small-ε DD with singleton cells and a Monge cost is odd-even sorting
+# --------------------------------------------------------------------------
+def test_odd_even_transposition_sort():
+    N = 8
+    x = np.arange(N, dtype=float)
+    C = (x[:, None] - x[None, :]) ** 2          # strictly Monge
+    mu = np.full(N, 1.0 / N); nu = mu.copy()
+    A = [[k, k + 1] for k in range(0, N, 2)]
+    B = [[0]] + [[k, k + 1] for k in range(1, N - 1, 2)] + [[N - 1]]
+    prob = dd.matrix_problem(mu, nu, C, [[k] for k in range(N)], {"A": A, "B": B})
+    perm = np.array([5, 2, 7, 0, 6, 1, 4, 3])
+    rows = [(np.array([perm[k]]), np.array([1.0 / N])) for k in range(N)]
+    alpha = {"A": np.zeros(N), "B": np.zeros(N)}
+    expect = referees.odd_even_transposition_sort_steps(perm, N)
+    par = dd.Params(err=1e-12, trunc=1e-15, max_iter=1000)
+    for step in range(N):
+        part = "AB"[step % 2]
+        rows, _ = dd.half_sweep(prob, part, rows, alpha[part], 0.05, par)
+        got = np.array([c[np.argmax(v)] for c, v in rows])
+        np.testing.assert_array_equal(got, expect[step])
+    np.testing.assert_array_equal(got, np.arange(N))
+
+
+# --------------------------------------------------------------------------
+# invariants: feasibility (Prop. 3.2), Balance, refinement (Prop. 6.1)
+# --------------------------------------------------------------------------
+def test_invariants_multiscale_run():
+    mu = syn.gaussian_mixture(16, 3, 4)
+    nu = syn.gaussian_mixture(16, 3, 5)
+    sched = syn.paper_schedule(16, 2, 3)
+    par = dd.Params(err=1e-8)
+    checks = []
+
+    def check(prob, part, rows, alpha, eps, info):
+        s = np.zeros(prob.nu.size)
+        for c, v in rows:
+            assert np.all(v > 0)
+            assert np.all(np.diff(c) > 0)
+            np.add.at(s, c, v)
+        # Σ_i ν_i = ν up to rounding and the mass dropped by Truncate
+        assert np.abs(s - prob.nu).sum() <= info.truncated_mass + 1e-12
+        m = np.array([v.sum() for _, v in rows])
+        assert np.abs(m - prob.basic_mass).max() <= info.truncated_mass + 1e-13
+        checks.append(info.err_x)
+
+    res = dd.run_schedule(mu, nu, 2, 2, sched, par, on_half_sweep=check)
+    assert len(checks) == 2 * sum(s for _, s, _ in sched)
+    assert res.prob.n == 16
+
+
+def test_balance_measures_invariants():
+    rng = np.random.default_rng(0)
+    parts = [rng.uniform(0, 1, 20) for _ in range(4)]
+    total = sum(parts)
+    targets = np.array([p.sum() for p in parts]) + np.array([0.3, -0.1, -0.25, 0.05])
+    out = dd.balance_measures([p.copy() for p in parts], targets)
+    np.testing.assert_allclose(sum(out), total, rtol=1e-14)
+    np.testing.assert_allclose([p.sum() for p in out], targets, rtol=1e-13)
+    assert all(np.all(p >= 0) for p in out)
+    # no-op when masses already match
+    out2 = dd.balance_measures([p.copy() for p in parts], [p.sum() for p in parts])
+    for a, b in zip(out2, parts):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_refined_marginals_are_feasible():
+    mus = dd.pyramid(syn.gaussian_mixture(16, 3, 6), 2)
+    nus = dd.pyramid(syn.gaussian_mixture(16, 3, 7), 2)
+    coarse = dd.GridProblem(mus[0], nus[0], 2, 1 / 8)
+    fine = dd.GridProblem(mus[1], nus[1], 2, 1 / 16)
+    rows = dd.product_state(coarse)
+    alpha = {"A": np.zeros(64), "B": np.zeros(64)}
+    par = dd.Params(err=1e-8)
+    for part in "AB":
+        rows, _ = dd.half_sweep(coarse, part, rows, alpha[part], 0.05, par)
+    rows_f = dd.refine_basic_marginals(coarse, fine, rows)
+    s = np.zeros(256)
+    for c, v in rows_f:
+        np.add.at(s, c, v)
+    np.testing.assert_allclose(s, fine.nu, rtol=1e-12, atol=1e-17)       # Σ_i ν_i⁰ = ν
+    np.testing.assert_allclose([v.sum() for _, v in rows_f], fine.basic_mass, rtol=1e-12)
+
+
+def test_pyramid_is_push_forward():
+    img = syn.gaussian_mixture(16, 2, 9)
+    p = dd.pyramid(img, 3)
+    assert [a.shape[0] for a in p] == [4, 8, 16]
+    assert p[0][1, 2] == pytest.approx(img[4:8, 8:12].sum(), rel=1e-14)
+
+
+def test_refined_duals_reproduce_linear_and_quadratic_terms():
+    # α linear in the pixel position must be refined exactly (first order),
+    # whatever the cell; positions in coarse pixel units, fine pixels at ±¼.
+    mus = dd.pyramid(syn.gaussian_mixture(16, 2, 10), 2)
+    coarse = dd.GridProblem(mus[0], mus[0], 2, 1 / 8)
+    fine = dd.GridProblem(mus[1], mus[1], 2, 1 / 16)
+    pi, pj = np.divmod(np.arange(64), 8)
+    a_c = 0.7 * pi - 1.3 * pj + 0.25
+    for part in "AB":
+        a_f = dd.refine_duals(coarse, fine, a_c, part)
+        fi, fj = np.divmod(np.arange(256), 16)
+        expect = 0.7 * ((fi + 0.5) / 2 - 0.5) - 1.3 * ((fj + 0.5) / 2 - 0.5) + 0.25
+        np.testing.assert_allclose(a_f, expect, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# objective: monotone decrease and the decrement identity (Lemma 4.3),
+# the scaling formula (Lemma 4.2), weak duality (Prop. 2.5)
+# --------------------------------------------------------------------------
+def test_kl_monotone_and_decrement_identity():
+    prob = _grid(8, 2, 2, 11)
+    eps = 0.04
+    C = _full_cost(prob)
+    rows = dd.product_state(prob)
+    alpha = {"A": np.zeros(64), "B": np.zeros(64)}
+    par = dd.Params(err=1e-13, trunc=0.0, max_iter=20000)
+    prev, prev_kl = None, None
+    for l in range(8):
+        part = "AB"[l % 2]
+        rows, _ = dd.half_sweep(prob, part, rows, alpha[part], eps, par)
+        P = dd.partition_plan(prob, part, rows, alpha[part], eps)
+        kl = dd.kl_minus_mass(P, C, prob.mu, prob.nu, eps)
+        if prev is not None:
+            assert kl <= prev_kl + 1e-12
+            dec = dd.kl_div(prev, P)
+            assert prev_kl - kl == pytest.approx(dec, rel=1e-6, abs=1e-12)
+        prev, prev_kl = P, kl
+
+
+def test_lemma_4_2_scaling_formula():
+    prob = _grid(8, 2, 2, 12)
+    eps = 0.05
+    C = _full_cost(prob)
+    rows = dd.product_state(prob)
+    alpha = {"A": np.zeros(64), "B": np.zeros(64)}
+    plans = {}
+    par = dd.Params(err=1e-12, trunc=0.0)
+    rows, _ = dd.half_sweep(prob, "A", rows, alpha["A"], eps, par)
+    rows, _ = dd.half_sweep(prob, "B", rows, alpha["B"], eps, par, plans=plans)
+    P = np.zeros((64, 64))
+    lhs_sum = 0.0
+    for X, cols, Pc in plans.values():
+        P[np.ix_(X, cols)] = Pc
+        # dπ_J/dK = u(x)·v(y); log u = α/ε; log v from the cell's Y-iteration
+        f = alpha["B"][X] + eps * np.log(prob.mu[X])
+        Cc = C[np.ix_(X, cols)]
+        nu_c = Pc.sum(axis=0)
+        g = eps * np.log(nu_c) - eps * dd.logsumexp((f[:, None] - Cc) / eps, axis=0)
+        logu = alpha["B"][X] / eps
+        logv = (g - eps * np.log(prob.nu[cols])) / eps
+        lhs_sum += Pc.sum(axis=1) @ logu + Pc.sum(axis=0) @ logv
+    K = dd.kernel_mass(C, prob.mu, prob.nu, eps)
+    direct = dd.kl_minus_mass(P, C, prob.mu, prob.nu, eps) + K
+    lemma = lhs_sum - P.sum() + K
+    assert direct == pytest.approx(lemma, rel=1e-10)
+
+
+def test_weak_duality_and_zero_gap_at_optimum():
+    prob = _grid(8, 4, 2, 13)
+    eps = 0.05
+    C = _full_cost(prob)
+    Pr, u, v = referees.sinkhorn_scaling(prob.mu, prob.nu, C, eps, tol=1e-15)
+    K = dd.kernel_mass(C, prob.mu, prob.nu, eps)
+    primal = dd.kl_minus_mass(Pr, C, prob.mu, prob.nu, eps) + K
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        a = rng.normal(0, eps, 64); b = rng.normal(0, eps, 64)
+        assert dd.dual_objective(a, b, prob.mu, prob.nu, C, prob.mu, prob.nu, eps) <= primal + 1e-12
+    J = dd.dual_objective(eps * np.log(u), eps * np.log(v), prob.mu, prob.nu, C, prob.mu, prob.nu, eps)
+    assert J == pytest.approx(primal, rel=1e-10)
+
+
+def test_partitions_cover_and_graph_connected():
+    nb = 6
+    parts = dd.grid_partitions(nb)
+    for name in "AB":
+        flat = sorted(i for J in parts[name] for i in J)
+        assert flat == list(range(nb * nb))
+    assert len(parts["A"]) == 9 and len(parts["B"]) == 16
+    assert sum(len(J) == 1 for J in parts["B"]) == 4
+    # partition graph (Def. 4.5): basic cells joined when they share a cell
+    adj = {i: set() for i in range(nb * nb)}
+    for name in "AB":
+        for J in parts[name]:
+            for i in J:
+                adj[i].update(J)
+    seen, todo = {0}, [0]
+    while todo:
+        k = todo.pop()
+        for m in adj[k] - seen:
+            seen.add(m); todo.append(m)
+    assert len(seen) == nb * nb
