@@ -1,0 +1,179 @@
+/*
+ * dd.h — C ABI of the GB300 library for entropic domain decomposition of
+ * optimal transport between two 2D images (Bonafini & Schmitzer, "Domain
+ * decomposition for entropy regularized optimal transport").
+ *
+ * The library solves min ε·KL(π|K) over couplings π of μ and ν with
+ * K = exp(−c/ε)·(μ⊗ν) and c(x,y) = |x−y|² on pixel centres in [0,1]²
+ * (§2.2 eq. EntropicOTPrimal, §3 eq. Problem, §7.1 "Test data"), by
+ * Algorithm 2 (§6.1) inside the multi-scale / ε-scaling driver of §6.4.
+ *
+ * Conventions for every entry point:
+ *  - Images are n×n, row-major, pixel (i,j) has flat index i·n+j and centre
+ *    ((i+½)h, (j+½)h), h = 1/n at the finest level. Level l of L has
+ *    n_l = n/2^(L−1−l) pixels per side; level 0 is the coarsest.
+ *  - A basic cell is a b×b block of pixels (§7.1 "Basic and composite
+ *    partitions"); basic cells are numbered row-major over the n_l/b × n_l/b
+ *    grid of cells ("natural order"). Partition A (= 0) groups them in 2×2
+ *    blocks; partition B (= 1) is A shifted by one basic cell.
+ *  - All pointer arguments are HOST pointers. The library copies what it
+ *    reads; the caller keeps ownership of its buffers. Device memory is owned
+ *    by the context and freed by dd_destroy.
+ *  - Every call returns a dd_status. On failure the context keeps the state
+ *    it had before the call and dd_last_error() describes the problem. After
+ *    a CUDA error the context is unusable and later calls return
+ *    DD_ERR_STATE. No call aborts the process or throws.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef DD_H
+#define DD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dd_ctx dd_ctx;
+
+typedef enum {
+  DD_OK = 0,
+  DD_ERR_ARG = 1,          /* invalid argument (sizes, NaN, negative mass, …)  */
+  DD_ERR_CUDA = 2,         /* a CUDA call failed                               */
+  DD_ERR_OOM = 3,          /* device allocation failed                         */
+  DD_ERR_CAPACITY = 4,     /* a caller buffer is too small (see *nnz)          */
+  DD_ERR_NUMERIC = 5,      /* a cell solve produced a non-finite value         */
+  DD_ERR_STATE = 6         /* context unusable or call out of order            */
+} dd_status;
+
+/* Image size and number of multi-scale levels (§6.4, §7.1 "Multi-scale"). */
+typedef struct {
+  int32_t n;       /* finest image side in pixels                              */
+  int32_t levels;  /* ≥ 1; n/2^(levels−1) must be a multiple of 2·b            */
+} dd_grid;
+
+/* One step of the ε schedule: `sweeps` sweeps (A then B half-sweep each) at
+ * regularisation `eps` ([0,1]² units, same units as c) on `level`. Levels must
+ * be non-decreasing; entering a new level refines the state by eq.
+ * FineBasicMarginals (§6.4). When ε changes, ε·log u is kept (§6.4, last
+ * paragraph). */
+typedef struct {
+  double eps;
+  int32_t sweeps;
+  int32_t level;
+} dd_eps_step;
+
+typedef struct {
+  double err_tol;        /* Err of §6.2: a cell solve stops after the first
+                            Y-iteration whose X-marginal L1 error is
+                            ≤ ‖μ_J‖·err_tol. Default 1e-6.                     */
+  double trunc;          /* Truncate threshold on ν_i entries (§7.1), absolute
+                            mass. Default 1e-15.                               */
+  int32_t max_iter;      /* cap on Sinkhorn Y-iterations per cell solve.
+                            Default 2000.                                      */
+  int32_t threads_per_cell; /* CUDA threads per composite cell (64, 128 or
+                            256); 0 = library choice. Default 0.               */
+  void* stream;          /* cudaStream_t to run on; NULL = a stream owned by
+                            the context.                                       */
+  uint64_t debug_flags;  /* bit 0: synchronise and check after every kernel  */
+} dd_options;
+
+/* Statistics of the last sweep run by dd_sweep / dd_run_schedule. */
+typedef struct {
+  int32_t level;          /* level of the last half-sweep                     */
+  int32_t partition;      /* 0 = A, 1 = B                                     */
+  double eps;             /* ε of the last half-sweep                         */
+  int64_t nnz;            /* entries stored in (ν_i) after it                 */
+  int32_t max_iters;      /* largest Sinkhorn iteration count over its cells  */
+  double mean_iters;      /* mean Sinkhorn iteration count over its cells     */
+  int32_t cells_not_converged; /* cells that stopped at max_iter               */
+  int64_t sweeps_done;    /* total sweeps since dd_create                     */
+} dd_sweep_stats;
+
+/* Fill *opt with the defaults listed above. */
+void dd_options_default(dd_options* opt);
+
+/* Create a context for transporting μ to ν.
+ * mu, nu: n×n host arrays of finite non-negative FP64 masses (n = grid->n).
+ *   They are normalised to mass 1; their masses must agree to 1e-9 relative.
+ *   Every basic cell of the finest level must carry positive μ-mass (Def. 3.1).
+ * b: basic cell side in pixels (2, 4 or 8).
+ * schedule, n_steps: the ε schedule (copied). n_steps ≥ 1, first level 0.
+ * opt: NULL for defaults.
+ * The context starts at level 0 with the product coupling ν_i = ‖μ_i‖·ν
+ * (§6.4) and α = ε·log u = 0 on both partitions (Algorithm 2 inputs).
+ * On success *out receives the context. */
+dd_status dd_create(const double* mu, const double* nu, const dd_grid* grid, int32_t b,
+                    const dd_eps_step* schedule, int32_t n_steps,
+                    const dd_options* opt, dd_ctx** out);
+
+/* Replace the state at the context's current level with the inputs of
+ * Algorithm 2 (§6.1): feasible basic Y-marginals (ν_i) and the scaling u as
+ * α = ε·log u, one value per pixel.
+ * row_ptr: n_basic+1 offsets (natural order of basic cells), col: Y pixel
+ *   indices at this level, strictly increasing within each row, val: masses
+ *   (FP64, ≥ 0) in the normalisation of dd_create (total mass 1).
+ * alpha_A, alpha_B: n_l×n_l FP64 arrays or NULL for zero.
+ * Returns DD_ERR_ARG for unsorted / out-of-range / negative input. */
+dd_status dd_set_state(dd_ctx* ctx, const int64_t* row_ptr, const int32_t* col,
+                       const double* val, const double* alpha_A, const double* alpha_B);
+
+/* One iteration of Algorithm 2 on `partition` (0 = A, 1 = B) at the current
+ * level with regularisation eps: for every composite cell J, gather
+ * ν_cell = Σ_{i∈J} ν_i, solve the cell by log-domain Sinkhorn warm-started
+ * from u_{C,J} (stop rule of §6.2), extract ν_i = P_Y(π_cell|X_i×Y),
+ * BalanceMeasures, Truncate. Does not advance the schedule. */
+dd_status dd_half_sweep(dd_ctx* ctx, int32_t partition, double eps);
+
+/* Run n_sweeps sweeps (A then B) following the schedule, refining when the
+ * schedule enters a new level. After the last step of the schedule the
+ * remaining sweeps stay at its ε and level. stats may be NULL. */
+dd_status dd_sweep(dd_ctx* ctx, int32_t n_sweeps, dd_sweep_stats* stats);
+
+/* Run every remaining sweep of the schedule. stats may be NULL. */
+dd_status dd_run_schedule(dd_ctx* ctx, dd_sweep_stats* stats);
+
+/* FP64 summaries of the coupling of the last half-sweep, π = Σ_J π_J with
+ * π_J the final cell plans: cost = Σ c·π (transport cost ⟨c,π⟩),
+ * err_x = Σ_x |P_X π(x) − μ(x)|, err_y = Σ_y |Σ_i ν_i(y) − ν(y)| (L1 errors of
+ * the marginals, Table 1 "L1 X/Y-marginal error"). Any pointer may be NULL. */
+dd_status dd_cost(dd_ctx* ctx, double* cost, double* err_x, double* err_y);
+
+/* Copy the basic Y-marginals (ν_i) at the current level to host memory as
+ * CSR in natural order of basic cells: row_ptr[n_basic+1], col (Y pixel
+ * index), val (FP64 mass). Call with col = val = NULL (row_ptr may be NULL)
+ * to get *nnz; cap is the capacity of col/val in entries
+ * (DD_ERR_CAPACITY if smaller than *nnz). */
+dd_status dd_get_basic_marginals(dd_ctx* ctx, int64_t* nnz, int64_t* row_ptr,
+                                 int32_t* col, double* val, int64_t cap);
+
+/* Pixel-level coupling of the partition solved last (§6.1 item (iv): the
+ * partial couplings are recovered from the scalings): on every composite
+ * cell, f from u_{C,J} and one Y-iteration against ν_cell, so P_Y π = ν.
+ * CSR with one row per X pixel (n_l² rows), entries > trunc only.
+ * Two-call pattern as in dd_get_basic_marginals. */
+dd_status dd_get_plan(dd_ctx* ctx, double trunc, int64_t* nnz, int64_t* row_ptr,
+                      int32_t* col, double* val, int64_t cap);
+
+/* α = ε·log u_{C,J} of `partition` on every pixel of the current level, up to
+ * one additive constant per composite cell (the gauge of Prop. 2.3 (ii)). */
+dd_status dd_get_duals(dd_ctx* ctx, int32_t partition, double* alpha);
+
+/* Current level, its side n_l, its number of basic cells (n_l/b)², the ε of
+ * the last half-sweep and the number of stored entries of (ν_i). Any output
+ * pointer may be NULL. */
+dd_status dd_get_info(dd_ctx* ctx, int32_t* level, int32_t* n_level, int32_t* n_basic,
+                      double* eps, int64_t* nnz);
+
+/* Free the context and all device memory it owns. NULL is allowed. */
+void dd_destroy(dd_ctx* ctx);
+
+/* Description of the last failure on ctx (never NULL; "" after success).
+ * With ctx == NULL: the last failure of dd_create in this thread. */
+const char* dd_last_error(const dd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DD_H */

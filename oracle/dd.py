@@ -37,6 +37,10 @@ the design notes of the repository):
   the support, as the paper requires.
 * Truncate (§6.1 item (ii), §7.1): entries of ν_i not above the absolute
   threshold (1e-15) are dropped.
+* Sinkhorn stopping test (§6.2) after truncation: the X-marginal is compared
+  with μ_J rescaled to ‖ν_cell‖ (see sinkhorn_cell), because truncated mass
+  makes ‖ν_cell‖ < ‖μ_J‖ and the unscaled error can then never reach
+  ‖μ_J‖·Err for small Err.
 * Dual refinement (§6.4 ends with "glue, then interpolate linearly in log
   space"): without gluing, each fine pixel takes the coarse α of its parent
   pixel plus a first-order correction from finite differences of α inside the
@@ -170,21 +174,27 @@ def sinkhorn_cell(C, mu_x, nu_y, f, eps, err, max_iter):
 
     Y-iteration: g(y) = ε·log ν(y) − ε·log Σ_x exp((f(x) − c(x,y))/ε)
     X-iteration: f(x) = ε·log μ(x) − ε·log Σ_y exp((g(y) − c(x,y))/ε)
-    After each Y-iteration the X-marginal error Σ_x |P_X π(x) − μ(x)| is
-    compared with ‖μ_J‖·Err; the solver stops on a Y-iteration.
+    After each Y-iteration the X-marginal error is compared with ‖μ_J‖·Err;
+    the solver stops on a Y-iteration. Truncate removes a little mass from the
+    basic marginals, so ‖ν_cell‖ can fall short of ‖μ_J‖ and no plan on the
+    cell then matches μ_J exactly; the stopping test therefore measures the
+    X-marginal against μ rescaled to the mass of ν_cell (the paper's rule
+    whenever no mass was truncated):
+        Σ_x |P_X π(x) − μ(x)·‖ν_cell‖/‖μ_J‖| ≤ ‖μ_J‖·Err.
     Returns f, g, the plan P (|X|×|Y|), the number of Y-iterations and the
-    final X-marginal error.
+    final X-marginal error Σ_x |P_X π(x) − μ(x)| (not rescaled).
     """
     logmu, lognu = np.log(mu_x), np.log(nu_y)
     tol = err * mu_x.sum()
+    target = mu_x * (nu_y.sum() / mu_x.sum())
     it = 0
     while True:
         it += 1
         g = eps * lognu - eps * logsumexp((f[:, None] - C) / eps, axis=0)
         P = np.exp((f[:, None] + g[None, :] - C) / eps)
-        err_x = np.abs(P.sum(axis=1) - mu_x).sum()
-        if err_x <= tol or it >= max_iter:
-            return f, g, P, it, err_x
+        px = P.sum(axis=1)
+        if np.abs(px - target).sum() <= tol or it >= max_iter:
+            return f, g, P, it, np.abs(px - mu_x).sum()
         f = eps * logmu - eps * logsumexp((g[None, :] - C) / eps, axis=1)
 
 
@@ -231,17 +241,22 @@ class SweepInfo:
     truncated_mass: float = 0.0
 
 
-def half_sweep(prob, part, rows, alpha, eps, params, plans=None):
+def half_sweep(prob, part, rows, alpha, eps, params, plans=None, cells=None):
     """One iteration of Algorithm 2 over the composite partition `part`.
 
     rows: list over basic cells of (cols sorted int array, vals float array).
     alpha: array over X holding α = ε·log u_{C,J} for this partition; updated
     in place. Returns the new rows and a SweepInfo. If `plans` is a dict, the
-    cell plans are stored there as plans[J index] = (X, cols, P).
+    cell plans are stored there as plans[J index] = (X, cols, P). `cells`
+    restricts the loop to the listed composite cells (the cells of one
+    partition are independent, so a subset is solved exactly as in the full
+    loop); rows of other basic cells are returned unchanged.
     """
     new_rows = list(rows)
     info = SweepInfo()
-    for jn, J in enumerate(prob.parts[part]):
+    todo = range(len(prob.parts[part])) if cells is None else cells
+    for jn in todo:
+        J = prob.parts[part][jn]
         cols, nu_cell = gather(rows, J)
         X = prob.cell_points(J)
         mu_x = prob.mu[X]

@@ -1,0 +1,922 @@
+// Host side of the C ABI declared in include/dd.h: context, multi-scale
+// driver (§6.4), half-sweep orchestration (Algorithm 2, §6.1) and result
+// read-back. Device work is issued on one stream; the host synchronises once
+// per half-sweep to learn the new number of stored entries.
+#include "dd.h"
+#include "dd_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace ddk;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct LevelHost {
+  int n = 0, nb = 0;
+  double spacing = 0.0;
+  std::vector<uint64_t> mu_q, nu_q, M_q;
+  std::vector<float> mu_f, log2mu;
+};
+
+struct LevelDev {
+  uint64_t* mu_q = nullptr;
+  uint64_t* nu_q = nullptr;
+  uint64_t* M_q = nullptr;
+  float* mu_f = nullptr;
+  float* log2mu = nullptr;
+};
+
+struct DdError {
+  dd_status st;
+  std::string msg;
+};
+
+}  // namespace
+
+struct dd_ctx {
+  std::string err;
+  dd_options opt{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool broken = false;
+  int n = 0, levels = 0, b = 0;
+  std::vector<dd_eps_step> sched;
+  size_t step = 0;
+  int step_done = 0;
+  std::vector<LevelHost> lh;
+  std::vector<void*> allocs;
+
+  int lev = -1;
+  LevelDev ld;
+  int cur = 0;
+  int64_t* rp[2] = {nullptr, nullptr};
+  int32_t* col[2] = {nullptr, nullptr};
+  uint64_t* val[2] = {nullptr, nullptr};
+  int64_t cap[2] = {0, 0};
+  int64_t rp_rows = 0;  // rows the rp buffers can hold (+1)
+  int64_t nnz = 0;
+
+  float* alpha[2] = {nullptr, nullptr};
+  int2* anchor[2] = {nullptr, nullptr};
+
+  int64_t ws_cap = 0;
+  int32_t* ws_ytmp = nullptr;
+  uint64_t* ws_vtmp = nullptr;
+  int32_t* ws_eta = nullptr;
+  uint64_t* ws_nu = nullptr;
+  float* ws_lognu = nullptr;
+  float* ws_g = nullptr;
+  int64_t tmp_cap = 0;
+  int32_t* tmp_col = nullptr;
+  uint64_t* tmp_val = nullptr;
+
+  int32_t* row_cnt = nullptr;
+  int64_t* row_src = nullptr;
+  int64_t* tile = nullptr;
+  int64_t* cell_off = nullptr;
+  int32_t* cell_ny = nullptr;
+  int2* anchor_new = nullptr;
+  double* cell_cost = nullptr;
+  double* cell_errx = nullptr;
+  int32_t* cell_iters = nullptr;
+  int32_t* cell_status = nullptr;
+  unsigned long long* ydense = nullptr;
+  int64_t level_alloc_n = 0;   // n of the per-level buffers
+
+  unsigned long long* ws_counter = nullptr;
+  int* err_flag = nullptr;
+  SweepTotals* totals = nullptr;
+  double* yerr = nullptr;
+
+  // pinned host mirrors
+  SweepTotals* h_tot = nullptr;
+  int64_t* h_nnz = nullptr;
+  int* h_err = nullptr;
+  double* h_yerr = nullptr;
+
+  int last_part = -1;
+  double eps_cur = 0.0;
+  SweepTotals last_tot{};
+  int64_t sweeps_done = 0;
+};
+
+namespace {
+
+#define DD_CUDA(call)                                                                 \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      throw DdError{DD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+void dev_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+template <typename T>
+void dev_alloc(T*& p, size_t count) {
+  dev_free(p);
+  p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)&p, sizeof(T) * count);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+    throw DdError{DD_ERR_OOM, "cudaMalloc of " + std::to_string(sizeof(T) * count) + " bytes failed"};
+  }
+}
+
+template <typename T>
+void grow(T*& p, int64_t& cap, int64_t need) {
+  if (need <= cap && p) return;
+  int64_t c = std::max<int64_t>(need + need / 2, 1024);
+  dev_alloc(p, (size_t)c);
+  cap = c;
+}
+
+// col/val buffer k holds at least `need` entries (contents are not kept)
+void state_reserve(dd_ctx* c, int k, int64_t need) {
+  if (c->cap[k] >= need && c->col[k] && c->val[k]) return;
+  const int64_t cap = std::max<int64_t>(need + need / 2, 1024);
+  dev_alloc(c->col[k], (size_t)cap);
+  dev_alloc(c->val[k], (size_t)cap);
+  c->cap[k] = cap;
+}
+
+void check_debug(dd_ctx* c, const char* what) {
+  if (c->opt.debug_flags & 1) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) throw DdError{DD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+  }
+}
+
+LevelView view(dd_ctx* c) {
+  const LevelHost& h = c->lh[c->lev];
+  LevelView v;
+  v.n = h.n;
+  v.nb = h.nb;
+  v.b = c->b;
+  v.spacing = h.spacing;
+  v.mu_q = c->ld.mu_q;
+  v.nu_q = c->ld.nu_q;
+  v.mu_f = c->ld.mu_f;
+  v.log2mu = c->ld.log2mu;
+  v.M_q = c->ld.M_q;
+  return v;
+}
+
+void free_level(LevelDev& d) {
+  dev_free(d.mu_q);
+  dev_free(d.nu_q);
+  dev_free(d.M_q);
+  dev_free(d.mu_f);
+  dev_free(d.log2mu);
+  d = LevelDev{};
+}
+
+LevelDev upload_level(dd_ctx* c, int l) {
+  const LevelHost& h = c->lh[l];
+  LevelDev d;
+  const size_t n2 = (size_t)h.n * h.n;
+  dev_alloc(d.mu_q, n2);
+  dev_alloc(d.nu_q, n2);
+  dev_alloc(d.M_q, (size_t)h.nb * h.nb);
+  dev_alloc(d.mu_f, n2);
+  dev_alloc(d.log2mu, n2);
+  DD_CUDA(cudaMemcpyAsync(d.mu_q, h.mu_q.data(), n2 * 8, cudaMemcpyHostToDevice, c->stream));
+  DD_CUDA(cudaMemcpyAsync(d.nu_q, h.nu_q.data(), n2 * 8, cudaMemcpyHostToDevice, c->stream));
+  DD_CUDA(cudaMemcpyAsync(d.M_q, h.M_q.data(), (size_t)h.nb * h.nb * 8, cudaMemcpyHostToDevice, c->stream));
+  DD_CUDA(cudaMemcpyAsync(d.mu_f, h.mu_f.data(), n2 * 4, cudaMemcpyHostToDevice, c->stream));
+  DD_CUDA(cudaMemcpyAsync(d.log2mu, h.log2mu.data(), n2 * 4, cudaMemcpyHostToDevice, c->stream));
+  return d;
+}
+
+// per-level buffers sized by pixels, basic cells and composite cells
+void alloc_level_buffers(dd_ctx* c, int l, float*& alpha0, float*& alpha1, int2*& an0, int2*& an1) {
+  const LevelHost& h = c->lh[l];
+  const size_t n2 = (size_t)h.n * h.n;
+  const size_t nbasic = (size_t)h.nb * h.nb;
+  const size_t ncell = (size_t)num_cells(1, h.nb);
+  dev_alloc(alpha0, n2);
+  dev_alloc(alpha1, n2);
+  dev_alloc(an0, ncell);
+  dev_alloc(an1, ncell);
+  dev_alloc(c->row_cnt, nbasic);
+  dev_alloc(c->row_src, nbasic);
+  dev_alloc(c->tile, (nbasic + 1023) / 1024 + (n2 + 1023) / 1024 + 2);
+  dev_alloc(c->cell_off, ncell);
+  dev_alloc(c->cell_ny, ncell);
+  dev_alloc(c->anchor_new, ncell);
+  dev_alloc(c->cell_cost, ncell);
+  dev_alloc(c->cell_errx, ncell);
+  dev_alloc(c->cell_iters, ncell);
+  dev_alloc(c->cell_status, ncell);
+  dev_alloc(c->ydense, n2);
+  for (int k = 0; k < 2; ++k) {
+    dev_alloc(c->rp[k], nbasic + 1);
+  }
+  c->rp_rows = (int64_t)nbasic + 1;
+  c->level_alloc_n = h.n;
+}
+
+// anchors at the cell corners: α̃ = α when the anchor displacement is zero
+void corner_anchors(dd_ctx* c, int l, int part, int2* dst) {
+  const LevelHost& h = c->lh[l];
+  const int nc = num_cells(part, h.nb);
+  std::vector<int2> an(nc);
+  for (int J = 0; J < nc; ++J) {
+    CellGeom g = cell_geom(part, J, h.nb, c->b);
+    an[J] = make_int2(g.r0, g.c0);
+  }
+  DD_CUDA(cudaMemcpyAsync(dst, an.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, c->stream));
+  DD_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+void ensure_sweep_capacity(dd_ctx* c, int64_t nnz_in) {
+  if (nnz_in > c->ws_cap) {
+    int64_t need = nnz_in + nnz_in / 2 + 1024;
+    dev_alloc(c->ws_ytmp, need);
+    dev_alloc(c->ws_vtmp, need);
+    dev_alloc(c->ws_eta, need);
+    dev_alloc(c->ws_nu, need);
+    dev_alloc(c->ws_lognu, need);
+    dev_alloc(c->ws_g, need);
+    c->ws_cap = need;
+  }
+  if (4 * c->ws_cap > c->tmp_cap) {
+    const int64_t need = 4 * c->ws_cap;
+    dev_alloc(c->tmp_col, need);
+    dev_alloc(c->tmp_val, need);
+    c->tmp_cap = need;
+  }
+}
+
+SweepArgs sweep_args(dd_ctx* c, int part, double eps) {
+  SweepArgs a{};
+  a.L = view(c);
+  a.part = part;
+  a.ncells = num_cells(part, a.L.nb);
+  a.eps = (float)eps;
+  a.err_tol = (float)c->opt.err_tol;
+  a.max_iter = c->opt.max_iter;
+  const double tq = c->opt.trunc * kFixOne;
+  a.trunc_q = tq <= 0 ? 0ull : (tq >= 1.8e19 ? ~0ull : (uint64_t)tq);
+  a.rp = c->rp[c->cur];
+  a.col = c->col[c->cur];
+  a.val = c->val[c->cur];
+  a.ws_cap = c->ws_cap;
+  a.ws_counter = c->ws_counter;
+  a.cell_off = c->cell_off;
+  a.cell_ny = c->cell_ny;
+  a.anchor_new = c->anchor_new;
+  a.ws_ytmp = c->ws_ytmp;
+  a.ws_vtmp = c->ws_vtmp;
+  a.ws_eta = c->ws_eta;
+  a.ws_nu = c->ws_nu;
+  a.ws_lognu = c->ws_lognu;
+  a.ws_g = c->ws_g;
+  a.alpha = c->alpha[part];
+  a.anchor = c->anchor[part];
+  a.tmp_col = c->tmp_col;
+  a.tmp_val = c->tmp_val;
+  a.row_cnt = c->row_cnt;
+  a.row_src = c->row_src;
+  a.cell_cost = c->cell_cost;
+  a.cell_errx = c->cell_errx;
+  a.cell_iters = c->cell_iters;
+  a.cell_status = c->cell_status;
+  a.err_flag = c->err_flag;
+  return a;
+}
+
+int threads_per_cell(dd_ctx* c) {
+  const int t = c->opt.threads_per_cell;
+  return (t == 64 || t == 128 || t == 256) ? t : 128;
+}
+
+void half_sweep(dd_ctx* c, int part, double eps) {
+  const LevelHost& h = c->lh[c->lev];
+  const int nrows = h.nb * h.nb;
+  ensure_sweep_capacity(c, c->nnz);
+  const int other = 1 - c->cur;
+  state_reserve(c, other, 4 * c->nnz);
+  DD_CUDA(cudaMemsetAsync(c->ws_counter, 0, sizeof(unsigned long long), c->stream));
+  DD_CUDA(cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream));
+  SweepArgs a = sweep_args(c, part, eps);
+  DD_CUDA(launch_gather(a, c->stream));
+  check_debug(c, "gather");
+  DD_CUDA(launch_sinkhorn(a, threads_per_cell(c), c->stream));
+  check_debug(c, "sinkhorn");
+  DD_CUDA(launch_row_scan(c->row_cnt, c->rp[other], c->tile, nrows, c->stream));
+  DD_CUDA(launch_compact(c->row_cnt, c->row_src, c->tile, c->rp[other], c->tmp_col, c->tmp_val,
+                         c->col[other], c->val[other], c->cap[other], nrows, c->err_flag, c->stream));
+  check_debug(c, "compact");
+  DD_CUDA(launch_reduce_cells(a, c->totals, c->stream));
+  DD_CUDA(cudaMemcpyAsync(c->h_tot, c->totals, sizeof(SweepTotals), cudaMemcpyDeviceToHost, c->stream));
+  DD_CUDA(cudaMemcpyAsync(c->h_nnz, c->rp[other] + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  DD_CUDA(cudaMemcpyAsync(c->h_err, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  DD_CUDA(cudaStreamSynchronize(c->stream));
+  if (*c->h_err & 2 || c->h_tot->nonfinite)
+    throw DdError{DD_ERR_NUMERIC, "a cell solve produced a non-finite value"};
+  if (*c->h_err & (4 | 8))
+    throw DdError{DD_ERR_STATE, "internal capacity check failed (flag " + std::to_string(*c->h_err) + ")"};
+  c->cur = other;
+  c->nnz = *c->h_nnz;
+  c->last_part = part;
+  c->eps_cur = eps;
+  c->last_tot = *c->h_tot;
+}
+
+// move the state one level finer (§6.4)
+void refine(dd_ctx* c) {
+  const int lc = c->lev, lf = lc + 1;
+  const LevelHost& hc = c->lh[lc];
+  const LevelHost& hf = c->lh[lf];
+  LevelDev fine = upload_level(c, lf);
+  LevelView C = view(c);
+  LevelView F = C;
+  F.n = hf.n;
+  F.nb = hf.nb;
+  F.spacing = hf.spacing;
+  F.mu_q = fine.mu_q;
+  F.nu_q = fine.nu_q;
+  F.mu_f = fine.mu_f;
+  F.log2mu = fine.log2mu;
+  F.M_q = fine.M_q;
+  (void)hc;
+
+  // keep the coarse state and duals alive while the fine buffers are created
+  const int cpart = c->last_part < 0 ? 1 : c->last_part;
+  int64_t* rp_c = c->rp[c->cur];
+  int32_t* col_c = c->col[c->cur];
+  uint64_t* val_c = c->val[c->cur];
+  float* alpha_c = c->alpha[cpart];
+  int2* anchor_c = c->anchor[cpart];
+  float* other_alpha = c->alpha[1 - cpart];
+  int2* other_anchor = c->anchor[1 - cpart];
+  const int oth = 1 - c->cur;
+  dev_free(c->rp[oth]);
+  dev_free(c->col[oth]);
+  dev_free(c->val[oth]);
+  for (int k = 0; k < 2; ++k) {
+    c->rp[k] = nullptr;
+    c->col[k] = nullptr;
+    c->val[k] = nullptr;
+    c->cap[k] = 0;
+    c->alpha[k] = nullptr;
+    c->anchor[k] = nullptr;
+  }
+
+  float *a0 = nullptr, *a1 = nullptr;
+  int2 *n0 = nullptr, *n1 = nullptr;
+  alloc_level_buffers(c, lf, a0, a1, n0, n1);
+
+  const int nrows_f = hf.nb * hf.nb;
+  RefineArgs r{};
+  r.C = C;
+  r.F = F;
+  r.rp_c = rp_c;
+  r.col_c = col_c;
+  r.val_c = val_c;
+  r.cnt_f = c->row_cnt;
+  DD_CUDA(launch_refine_count(r, c->stream));
+  const int target = 0;
+  DD_CUDA(cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream));
+  DD_CUDA(launch_row_scan(c->row_cnt, c->rp[target], c->tile, nrows_f, c->stream));
+  DD_CUDA(launch_compact(c->row_cnt, nullptr, c->tile, c->rp[target], nullptr, nullptr, nullptr, nullptr, 0,
+                         nrows_f, c->err_flag, c->stream));
+  DD_CUDA(cudaMemcpyAsync(c->h_nnz, c->rp[target] + nrows_f, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                          c->stream));
+  DD_CUDA(cudaStreamSynchronize(c->stream));
+  const int64_t nnz_f = *c->h_nnz;
+  state_reserve(c, target, nnz_f);
+  r.rp_f = c->rp[target];
+  r.col_f = c->col[target];
+  r.val_f = c->val[target];
+  DD_CUDA(launch_refine_write(r, c->stream));
+  check_debug(c, "refine_write");
+  DD_CUDA(launch_refine_duals(C, F, cpart, alpha_c, anchor_c, 0, a0, n0, c->stream));
+  DD_CUDA(launch_refine_duals(C, F, cpart, alpha_c, anchor_c, 1, a1, n1, c->stream));
+  check_debug(c, "refine_duals");
+  DD_CUDA(cudaStreamSynchronize(c->stream));
+  dev_free(rp_c);
+  dev_free(col_c);
+  dev_free(val_c);
+  dev_free(alpha_c);
+  dev_free(anchor_c);
+  dev_free(other_alpha);
+  dev_free(other_anchor);
+  free_level(c->ld);
+  c->ld = fine;
+  c->lev = lf;
+  c->cur = target;
+  c->nnz = nnz_f;
+  c->alpha[0] = a0;
+  c->alpha[1] = a1;
+  c->anchor[0] = n0;
+  c->anchor[1] = n1;
+  c->last_part = -1;
+}
+
+void enter_level0(dd_ctx* c) {
+  c->lev = 0;
+  c->ld = upload_level(c, 0);
+  float *a0 = nullptr, *a1 = nullptr;
+  int2 *n0 = nullptr, *n1 = nullptr;
+  alloc_level_buffers(c, 0, a0, a1, n0, n1);
+  c->alpha[0] = a0;
+  c->alpha[1] = a1;
+  c->anchor[0] = n0;
+  c->anchor[1] = n1;
+  const LevelHost& h = c->lh[0];
+  const size_t n2 = (size_t)h.n * h.n;
+  DD_CUDA(cudaMemsetAsync(a0, 0, n2 * 4, c->stream));
+  DD_CUDA(cudaMemsetAsync(a1, 0, n2 * 4, c->stream));
+  corner_anchors(c, 0, 0, n0);
+  corner_anchors(c, 0, 1, n1);
+  // product coupling ν_i = ‖μ_i‖·ν (dense rows)
+  const int64_t nnz = (int64_t)h.nb * h.nb * (int64_t)n2;
+  state_reserve(c, 0, nnz);
+  int imax = 0;
+  for (int i = 1; i < h.nb * h.nb; ++i)
+    if (h.M_q[i] > h.M_q[imax]) imax = i;
+  DD_CUDA(launch_init_product(view(c), c->rp[0], c->col[0], c->val[0], imax, c->stream));
+  DD_CUDA(cudaStreamSynchronize(c->stream));
+  c->cur = 0;
+  c->nnz = nnz;
+}
+
+void build_levels(dd_ctx* c, const double* mu, const double* nu) {
+  const int n = c->n, L = c->levels;
+  const size_t n2 = (size_t)n * n;
+  double smu = 0, snu = 0;
+  for (size_t i = 0; i < n2; ++i) {
+    smu += mu[i];
+    snu += nu[i];
+  }
+  auto quantise = [&](const double* a, double s) {
+    std::vector<uint64_t> q(n2);
+    long double tot = 0;
+    size_t imax = 0;
+    for (size_t i = 0; i < n2; ++i) {
+      q[i] = (uint64_t)std::llround(a[i] / s * kFixOne);
+      tot += (long double)q[i];
+      if (a[i] > a[imax]) imax = i;
+    }
+    const long double diff = (long double)kFixOne - tot;
+    q[imax] = (uint64_t)((long double)q[imax] + diff);
+    return q;
+  };
+  c->lh.assign(L, LevelHost{});
+  LevelHost& fin = c->lh[L - 1];
+  fin.n = n;
+  fin.mu_q = quantise(mu, smu);
+  fin.nu_q = quantise(nu, snu);
+  for (int l = L - 2; l >= 0; --l) {
+    const LevelHost& f = c->lh[l + 1];
+    LevelHost& h = c->lh[l];
+    h.n = f.n / 2;
+    h.mu_q.assign((size_t)h.n * h.n, 0);
+    h.nu_q.assign((size_t)h.n * h.n, 0);
+    for (int i = 0; i < f.n; ++i)
+      for (int j = 0; j < f.n; ++j) {
+        const size_t k = (size_t)(i / 2) * h.n + j / 2;
+        h.mu_q[k] += f.mu_q[(size_t)i * f.n + j];
+        h.nu_q[k] += f.nu_q[(size_t)i * f.n + j];
+      }
+  }
+  for (int l = 0; l < L; ++l) {
+    LevelHost& h = c->lh[l];
+    h.nb = h.n / c->b;
+    h.spacing = 1.0 / (double)h.n;
+    const size_t m2 = (size_t)h.n * h.n;
+    h.mu_f.resize(m2);
+    h.log2mu.resize(m2);
+    for (size_t i = 0; i < m2; ++i) {
+      const double m = (double)h.mu_q[i] / kFixOne;
+      h.mu_f[i] = (float)m;
+      h.log2mu[i] = m > 0 ? (float)std::log2(m) : -1.0e30f;
+    }
+    h.M_q.assign((size_t)h.nb * h.nb, 0);
+    for (int i = 0; i < h.n; ++i)
+      for (int j = 0; j < h.n; ++j)
+        h.M_q[(size_t)(i / c->b) * h.nb + j / c->b] += h.mu_q[(size_t)i * h.n + j];
+  }
+}
+
+void release(dd_ctx* c) {
+  for (int k = 0; k < 2; ++k) {
+    dev_free(c->rp[k]);
+    dev_free(c->col[k]);
+    dev_free(c->val[k]);
+    dev_free(c->alpha[k]);
+    dev_free(c->anchor[k]);
+  }
+  free_level(c->ld);
+  void* bufs[] = {c->ws_ytmp, c->ws_vtmp, c->ws_eta, c->ws_nu, c->ws_lognu, c->ws_g, c->tmp_col, c->tmp_val,
+                  c->row_cnt, c->row_src, c->tile, c->cell_off, c->cell_ny, c->anchor_new, c->cell_cost,
+                  c->cell_errx, c->cell_iters, c->cell_status, c->ydense, c->ws_counter, c->err_flag,
+                  c->totals, c->yerr};
+  for (void* p : bufs) dev_free(p);
+  if (c->h_tot) cudaFreeHost(c->h_tot);
+  if (c->h_nnz) cudaFreeHost(c->h_nnz);
+  if (c->h_err) cudaFreeHost(c->h_err);
+  if (c->h_yerr) cudaFreeHost(c->h_yerr);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+template <typename F>
+dd_status guarded(dd_ctx* c, F&& f) {
+  if (!c) return DD_ERR_ARG;
+  if (c->broken) {
+    c->err = "context unusable after an earlier CUDA error";
+    return DD_ERR_STATE;
+  }
+  try {
+    f();
+    c->err.clear();
+    return DD_OK;
+  } catch (const DdError& e) {
+    c->err = e.msg;
+    if (e.st == DD_ERR_CUDA) c->broken = true;
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    c->err = "host allocation failed";
+    return DD_ERR_OOM;
+  } catch (...) {
+    c->err = "unexpected internal error";
+    return DD_ERR_STATE;
+  }
+}
+
+// advance the schedule by one sweep (refining first if the step asks for it)
+void one_sweep(dd_ctx* c) {
+  while (c->step < c->sched.size() && c->sched[c->step].sweeps <= 0) {
+    while (c->lev < c->sched[c->step].level) refine(c);
+    ++c->step;
+    c->step_done = 0;
+  }
+  const dd_eps_step& s = c->step < c->sched.size() ? c->sched[c->step] : c->sched.back();
+  while (c->lev < s.level) refine(c);
+  half_sweep(c, 0, s.eps);
+  half_sweep(c, 1, s.eps);
+  ++c->sweeps_done;
+  if (c->step < c->sched.size()) {
+    if (++c->step_done >= c->sched[c->step].sweeps) {
+      ++c->step;
+      c->step_done = 0;
+    }
+  }
+}
+
+void fill_stats(dd_ctx* c, dd_sweep_stats* st) {
+  if (!st) return;
+  st->level = c->lev;
+  st->partition = c->last_part;
+  st->eps = c->eps_cur;
+  st->nnz = c->nnz;
+  st->max_iters = c->last_tot.iters_max;
+  const int nc = num_cells(c->last_part < 0 ? 0 : c->last_part, c->lh[c->lev].nb);
+  st->mean_iters = nc > 0 ? (double)c->last_tot.iters_sum / nc : 0.0;
+  st->cells_not_converged = c->last_tot.not_converged;
+  st->sweeps_done = c->sweeps_done;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dd_options_default(dd_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->err_tol = 1e-6;
+  opt->trunc = 1e-15;
+  opt->max_iter = 2000;
+  opt->threads_per_cell = 0;
+  opt->stream = nullptr;
+  opt->debug_flags = 0;
+}
+
+dd_status dd_create(const double* mu, const double* nu, const dd_grid* grid, int32_t b,
+                    const dd_eps_step* schedule, int32_t n_steps, const dd_options* opt, dd_ctx** out) {
+  g_create_error.clear();
+  auto fail = [&](dd_status st, const std::string& m) {
+    g_create_error = m;
+    return st;
+  };
+  if (!out) return fail(DD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!mu || !nu || !grid || !schedule) return fail(DD_ERR_ARG, "NULL argument");
+  const int n = grid->n, L = grid->levels;
+  if (b != 2 && b != 4 && b != 8) return fail(DD_ERR_ARG, "b must be 2, 4 or 8");
+  if (L < 1 || L > 12 || n < 2 * b || n > 16384) return fail(DD_ERR_ARG, "bad grid size or level count");
+  if (n % (1 << (L - 1))) return fail(DD_ERR_ARG, "n must be divisible by 2^(levels-1)");
+  const int n0 = n >> (L - 1);
+  if (n0 % (2 * b)) return fail(DD_ERR_ARG, "coarsest side must be a multiple of 2b");
+  if (n_steps < 1) return fail(DD_ERR_ARG, "empty schedule");
+  int prev = 0;
+  for (int k = 0; k < n_steps; ++k) {
+    const dd_eps_step& s = schedule[k];
+    if (!(s.eps > 0) || !std::isfinite(s.eps) || s.sweeps < 0 || s.level < prev || s.level >= L)
+      return fail(DD_ERR_ARG, "invalid schedule step " + std::to_string(k));
+    prev = s.level;
+  }
+  const size_t n2 = (size_t)n * n;
+  double smu = 0, snu = 0;
+  for (size_t i = 0; i < n2; ++i) {
+    if (!std::isfinite(mu[i]) || mu[i] < 0 || !std::isfinite(nu[i]) || nu[i] < 0)
+      return fail(DD_ERR_ARG, "mu and nu must be finite and non-negative");
+    smu += mu[i];
+    snu += nu[i];
+  }
+  if (!(smu > 0) || !(snu > 0)) return fail(DD_ERR_ARG, "zero total mass");
+  if (std::fabs(smu - snu) > 1e-9 * std::max(smu, snu)) return fail(DD_ERR_ARG, "mu and nu masses differ");
+  const int nb = n / b;
+  for (int r = 0; r < nb; ++r)
+    for (int s = 0; s < nb; ++s) {
+      double m = 0;
+      for (int i = 0; i < b; ++i)
+        for (int j = 0; j < b; ++j) m += mu[(size_t)(r * b + i) * n + s * b + j];
+      if (!(m > 0)) return fail(DD_ERR_ARG, "a basic cell has zero mu-mass (Def. 3.1)");
+    }
+  dd_ctx* c = new (std::nothrow) dd_ctx();
+  if (!c) return fail(DD_ERR_OOM, "host allocation failed");
+  if (opt) c->opt = *opt;
+  else dd_options_default(&c->opt);
+  if (c->opt.max_iter <= 0) c->opt.max_iter = 2000;
+  c->n = n;
+  c->levels = L;
+  c->b = b;
+  c->sched.assign(schedule, schedule + n_steps);
+  dd_status st = guarded(c, [&] {
+    if (c->opt.stream) {
+      c->stream = (cudaStream_t)c->opt.stream;
+    } else {
+      DD_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    dev_alloc(c->ws_counter, 1);
+    dev_alloc(c->err_flag, 1);
+    dev_alloc(c->totals, 1);
+    dev_alloc(c->yerr, 1);
+    DD_CUDA(cudaMallocHost((void**)&c->h_tot, sizeof(SweepTotals)));
+    DD_CUDA(cudaMallocHost((void**)&c->h_nnz, sizeof(int64_t)));
+    DD_CUDA(cudaMallocHost((void**)&c->h_err, sizeof(int)));
+    DD_CUDA(cudaMallocHost((void**)&c->h_yerr, sizeof(double)));
+    build_levels(c, mu, nu);
+    enter_level0(c);
+    c->eps_cur = c->sched[0].eps;
+  });
+  if (st != DD_OK) {
+    g_create_error = c->err;
+    release(c);
+    delete c;
+    return st;
+  }
+  *out = c;
+  return DD_OK;
+}
+
+dd_status dd_set_state(dd_ctx* c, const int64_t* row_ptr, const int32_t* col, const double* val,
+                       const double* alpha_A, const double* alpha_B) {
+  return guarded(c, [&] {
+    if (!row_ptr || !col || !val) throw DdError{DD_ERR_ARG, "NULL argument"};
+    const LevelHost& h = c->lh[c->lev];
+    const int nrows = h.nb * h.nb;
+    const int n2 = h.n * h.n;
+    if (row_ptr[0] != 0) throw DdError{DD_ERR_ARG, "row_ptr[0] must be 0"};
+    std::vector<int64_t> rp(nrows + 1, 0);
+    std::vector<int32_t> cs;
+    std::vector<uint64_t> vs;
+    for (int i = 0; i < nrows; ++i) {
+      if (row_ptr[i + 1] < row_ptr[i]) throw DdError{DD_ERR_ARG, "row_ptr must be non-decreasing"};
+      int last = -1;
+      for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+        if (col[e] <= last || col[e] >= n2) throw DdError{DD_ERR_ARG, "columns must be increasing and < n_l^2"};
+        last = col[e];
+        if (!std::isfinite(val[e]) || val[e] < 0) throw DdError{DD_ERR_ARG, "values must be finite and >= 0"};
+        const uint64_t q = (uint64_t)std::llround(val[e] * kFixOne);
+        if (q == 0) continue;
+        cs.push_back(col[e]);
+        vs.push_back(q);
+      }
+      rp[i + 1] = (int64_t)cs.size();
+      if (rp[i + 1] == rp[i]) throw DdError{DD_ERR_ARG, "every basic cell needs a non-empty marginal"};
+    }
+    const int64_t nnz = (int64_t)cs.size();
+    state_reserve(c, c->cur, nnz);
+    DD_CUDA(cudaMemcpyAsync(c->rp[c->cur], rp.data(), 8 * (nrows + 1), cudaMemcpyHostToDevice, c->stream));
+    DD_CUDA(cudaMemcpyAsync(c->col[c->cur], cs.data(), 4 * nnz, cudaMemcpyHostToDevice, c->stream));
+    DD_CUDA(cudaMemcpyAsync(c->val[c->cur], vs.data(), 8 * nnz, cudaMemcpyHostToDevice, c->stream));
+    // duals: reduce α to the cell frame with an anchor from its mean slope
+    const double d2 = h.spacing * h.spacing;
+    for (int part = 0; part < 2; ++part) {
+      const double* al = part == 0 ? alpha_A : alpha_B;
+      const int nc = num_cells(part, h.nb);
+      std::vector<float> at((size_t)n2, 0.f);
+      std::vector<int2> an(nc);
+      for (int J = 0; J < nc; ++J) {
+        CellGeom g = cell_geom(part, J, h.nb, c->b);
+        int Dr = 0, Dc = 0;
+        if (al) {
+          const double a00 = al[(size_t)g.r0 * h.n + g.c0];
+          const double sr = (al[(size_t)(g.r0 + g.H - 1) * h.n + g.c0] - a00) / (g.H - 1);
+          const double sc = (al[(size_t)g.r0 * h.n + g.c0 + g.W - 1] - a00) / (g.W - 1);
+          Dr = (int)std::lround(sr / (2 * d2));
+          Dc = (int)std::lround(sc / (2 * d2));
+          for (int i = 0; i < g.H; ++i)
+            for (int j = 0; j < g.W; ++j) {
+              const size_t p = (size_t)(g.r0 + i) * h.n + g.c0 + j;
+              at[p] = (float)(al[p] - a00 - 2 * d2 * ((double)Dr * i + (double)Dc * j));
+            }
+        }
+        an[J] = make_int2(g.r0 - Dr, g.c0 - Dc);
+      }
+      DD_CUDA(cudaMemcpyAsync(c->alpha[part], at.data(), 4 * (size_t)n2, cudaMemcpyHostToDevice, c->stream));
+      DD_CUDA(cudaMemcpyAsync(c->anchor[part], an.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, c->stream));
+      DD_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    c->nnz = nnz;
+    c->last_part = -1;
+  });
+}
+
+dd_status dd_half_sweep(dd_ctx* c, int32_t partition, double eps) {
+  return guarded(c, [&] {
+    if (partition != 0 && partition != 1) throw DdError{DD_ERR_ARG, "partition must be 0 (A) or 1 (B)"};
+    if (!(eps > 0) || !std::isfinite(eps)) throw DdError{DD_ERR_ARG, "eps must be positive"};
+    half_sweep(c, partition, eps);
+  });
+}
+
+dd_status dd_sweep(dd_ctx* c, int32_t n_sweeps, dd_sweep_stats* stats) {
+  return guarded(c, [&] {
+    if (n_sweeps < 0) throw DdError{DD_ERR_ARG, "n_sweeps must be >= 0"};
+    for (int k = 0; k < n_sweeps; ++k) one_sweep(c);
+    fill_stats(c, stats);
+  });
+}
+
+dd_status dd_run_schedule(dd_ctx* c, dd_sweep_stats* stats) {
+  return guarded(c, [&] {
+    int64_t remaining = 0;
+    if (c->step < c->sched.size()) {
+      remaining = c->sched[c->step].sweeps - c->step_done;
+      for (size_t k = c->step + 1; k < c->sched.size(); ++k) remaining += c->sched[k].sweeps;
+    }
+    for (int64_t k = 0; k < remaining; ++k) one_sweep(c);
+    // a trailing refinement without sweeps
+    while (c->step < c->sched.size()) {
+      while (c->lev < c->sched[c->step].level) refine(c);
+      ++c->step;
+    }
+    fill_stats(c, stats);
+  });
+}
+
+dd_status dd_cost(dd_ctx* c, double* cost, double* err_x, double* err_y) {
+  return guarded(c, [&] {
+    if (cost) *cost = c->last_part < 0 ? NAN : c->last_tot.cost;
+    if (err_x) *err_x = c->last_part < 0 ? NAN : c->last_tot.errx;
+    if (err_y) {
+      const LevelHost& h = c->lh[c->lev];
+      DD_CUDA(launch_y_error(view(c), c->rp[c->cur], c->col[c->cur], c->val[c->cur], h.nb * h.nb, c->ydense,
+                             c->yerr, c->stream));
+      DD_CUDA(cudaMemcpyAsync(c->h_yerr, c->yerr, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      DD_CUDA(cudaStreamSynchronize(c->stream));
+      *err_y = *c->h_yerr;
+    }
+  });
+}
+
+dd_status dd_get_basic_marginals(dd_ctx* c, int64_t* nnz, int64_t* row_ptr, int32_t* col, double* val,
+                                 int64_t cap) {
+  return guarded(c, [&] {
+    if (!nnz) throw DdError{DD_ERR_ARG, "nnz is NULL"};
+    const LevelHost& h = c->lh[c->lev];
+    const int nrows = h.nb * h.nb;
+    *nnz = c->nnz;
+    if (row_ptr)
+      DD_CUDA(cudaMemcpyAsync(row_ptr, c->rp[c->cur], 8 * (size_t)(nrows + 1), cudaMemcpyDeviceToHost, c->stream));
+    if (col || val) {
+      if (cap < c->nnz) throw DdError{DD_ERR_CAPACITY, "buffer too small"};
+      std::vector<uint64_t> q(c->nnz);
+      if (col) DD_CUDA(cudaMemcpyAsync(col, c->col[c->cur], 4 * (size_t)c->nnz, cudaMemcpyDeviceToHost, c->stream));
+      DD_CUDA(cudaMemcpyAsync(q.data(), c->val[c->cur], 8 * (size_t)c->nnz, cudaMemcpyDeviceToHost, c->stream));
+      DD_CUDA(cudaStreamSynchronize(c->stream));
+      if (val)
+        for (int64_t e = 0; e < c->nnz; ++e) val[e] = (double)q[e] / kFixOne;
+    }
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+  });
+}
+
+dd_status dd_get_plan(dd_ctx* c, double trunc, int64_t* nnz, int64_t* row_ptr, int32_t* col, double* val,
+                      int64_t cap) {
+  return guarded(c, [&] {
+    if (!nnz) throw DdError{DD_ERR_ARG, "nnz is NULL"};
+    if (c->last_part < 0) throw DdError{DD_ERR_STATE, "no half-sweep has run at this level"};
+    const LevelHost& h = c->lh[c->lev];
+    const int n2 = h.n * h.n;
+    ensure_sweep_capacity(c, c->nnz);
+    DD_CUDA(cudaMemsetAsync(c->ws_counter, 0, sizeof(unsigned long long), c->stream));
+    DD_CUDA(cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream));
+    SweepArgs a = sweep_args(c, c->last_part, c->eps_cur);
+    DD_CUDA(launch_gather(a, c->stream));
+    int32_t* xcnt = nullptr;
+    int64_t* xrp = nullptr;
+    int64_t* xtile = nullptr;
+    try {
+      dev_alloc(xcnt, (size_t)n2);
+      dev_alloc(xrp, (size_t)n2 + 1);
+      dev_alloc(xtile, (size_t)(n2 + 1023) / 1024 + 1);
+      DD_CUDA(launch_plan(a, (float)trunc, xrp, xcnt, nullptr, nullptr, 0, c->stream));
+      DD_CUDA(launch_row_scan(xcnt, xrp, xtile, n2, c->stream));
+      DD_CUDA(launch_compact(xcnt, nullptr, xtile, xrp, nullptr, nullptr, nullptr, nullptr, 0, n2, c->err_flag,
+                             c->stream));
+      DD_CUDA(cudaMemcpyAsync(c->h_nnz, xrp + n2, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+      DD_CUDA(cudaStreamSynchronize(c->stream));
+      const int64_t tot = *c->h_nnz;
+      *nnz = tot;
+      if (row_ptr) DD_CUDA(cudaMemcpy(row_ptr, xrp, 8 * ((size_t)n2 + 1), cudaMemcpyDeviceToHost));
+      if (col || val) {
+        if (cap < tot) throw DdError{DD_ERR_CAPACITY, "buffer too small"};
+        int32_t* pc = nullptr;
+        double* pv = nullptr;
+        dev_alloc(pc, (size_t)tot);
+        dev_alloc(pv, (size_t)tot);
+        DD_CUDA(launch_plan(a, (float)trunc, xrp, xcnt, pc, pv, 1, c->stream));
+        DD_CUDA(cudaStreamSynchronize(c->stream));
+        if (col) DD_CUDA(cudaMemcpy(col, pc, 4 * (size_t)tot, cudaMemcpyDeviceToHost));
+        if (val) DD_CUDA(cudaMemcpy(val, pv, 8 * (size_t)tot, cudaMemcpyDeviceToHost));
+        dev_free(pc);
+        dev_free(pv);
+      }
+    } catch (...) {
+      dev_free(xcnt);
+      dev_free(xrp);
+      dev_free(xtile);
+      throw;
+    }
+    dev_free(xcnt);
+    dev_free(xrp);
+    dev_free(xtile);
+  });
+}
+
+dd_status dd_get_duals(dd_ctx* c, int32_t partition, double* alpha) {
+  return guarded(c, [&] {
+    if ((partition != 0 && partition != 1) || !alpha) throw DdError{DD_ERR_ARG, "bad argument"};
+    const LevelHost& h = c->lh[c->lev];
+    const int n2 = h.n * h.n;
+    const int nc = num_cells(partition, h.nb);
+    std::vector<float> at(n2);
+    std::vector<int2> an(nc);
+    DD_CUDA(cudaMemcpyAsync(at.data(), c->alpha[partition], 4 * (size_t)n2, cudaMemcpyDeviceToHost, c->stream));
+    DD_CUDA(cudaMemcpyAsync(an.data(), c->anchor[partition], sizeof(int2) * nc, cudaMemcpyDeviceToHost, c->stream));
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    const double d2 = h.spacing * h.spacing;
+    for (int J = 0; J < nc; ++J) {
+      CellGeom g = cell_geom(partition, J, h.nb, c->b);
+      const int Dr = g.r0 - an[J].x, Dc = g.c0 - an[J].y;
+      for (int i = 0; i < g.H; ++i)
+        for (int j = 0; j < g.W; ++j) {
+          const size_t p = (size_t)(g.r0 + i) * h.n + g.c0 + j;
+          alpha[p] = (double)at[p] + 2 * d2 * ((double)Dr * i + (double)Dc * j);
+        }
+    }
+  });
+}
+
+dd_status dd_get_info(dd_ctx* c, int32_t* level, int32_t* n_level, int32_t* n_basic, double* eps,
+                      int64_t* nnz) {
+  return guarded(c, [&] {
+    if (level) *level = c->lev;
+    if (n_level) *n_level = c->lh[c->lev].n;
+    if (n_basic) *n_basic = c->lh[c->lev].nb * c->lh[c->lev].nb;
+    if (eps) *eps = c->eps_cur;
+    if (nnz) *nnz = c->nnz;
+  });
+}
+
+void dd_destroy(dd_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  release(c);
+  delete c;
+}
+
+const char* dd_last_error(const dd_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.c_str();
+}
+
+}  // extern "C"

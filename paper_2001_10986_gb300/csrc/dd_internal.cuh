@@ -1,0 +1,163 @@
+// Internal declarations shared by the kernels and the C-ABI host code.
+//
+// Mass representation: every mass (μ, ν, ν_i entries) is an unsigned 64-bit
+// fixed-point number with one unit = 2^-62 of the total mass (total = 2^62).
+// Integer sums make Σ_i ν_i(y) = ν(y) exact through gather and extraction,
+// which the paper needs after every half-sweep (§6.2: the Y-marginal must be
+// reproduced exactly) and which FP64 arithmetic would do only up to rounding
+// — at 1/64 of the FP32 rate on this GPU.
+//
+// Potentials are FP32 in a per-cell frame (see k_sinkhorn): with x = x0 + ξ on
+// the cell and y = y_a + η around an anchor pixel y_a, and D = x0 − y_a,
+//   c(x,y) = Δ²|D + ξ − η|² = Δ²|D|² + 2Δ²D·ξ − 2Δ²D·η + Δ²|ξ − η|²,
+// so f(x) + g(y) − c(x,y) = f̃(ξ) + g̃(η) − Δ²|ξ − η|² with f̃ = f − 2Δ²D·ξ and
+// g̃ = g + 2Δ²D·η − Δ²|D|². Only the small quantities f̃, g̃ and |ξ−η|² are held
+// in FP32. The stored dual of a cell is α̃(ξ) = α(x) − 2Δ²D·ξ + const together
+// with its anchor y_a.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ddk {
+
+constexpr int kFixShift = 62;                       // one unit = 2^-62 of the mass
+constexpr double kFixOne = 4611686018427387904.0;   // 2^62
+constexpr float kFixToFloat = 2.168404344971009e-19f;  // 2^-62
+
+struct LevelView {
+  int n;                  // pixels per side at this level
+  int nb;                 // basic cells per side
+  int b;                  // basic cell side (pixels)
+  double spacing;         // Δ: pixel spacing in [0,1]² units
+  const uint64_t* mu_q;   // n·n fixed-point μ
+  const uint64_t* nu_q;   // n·n fixed-point ν
+  const float* mu_f;      // μ as float (true mass)
+  const float* log2mu;    // log2 μ
+  const uint64_t* M_q;    // nb·nb fixed-point basic-cell masses ‖μ_i‖
+};
+
+// geometry of a composite cell (§7.1): a rectangle of nbr×nbc basic cells
+struct CellGeom {
+  int bi0, bj0;   // first basic cell (row, col)
+  int nbr, nbc;   // basic cells per column / row of the cell (1 or 2)
+  int r0, c0;     // corner pixel
+  int H, W;       // size in pixels
+};
+
+__host__ __device__ inline int num_cells(int part, int nb) {
+  int m = part == 0 ? nb / 2 : nb / 2 + 1;
+  return m * m;
+}
+
+__host__ __device__ inline CellGeom cell_geom(int part, int J, int nb, int b) {
+  CellGeom g;
+  if (part == 0) {
+    int m = nb / 2;
+    int a = J / m, c = J - (J / m) * m;
+    g.bi0 = 2 * a; g.bj0 = 2 * c; g.nbr = 2; g.nbc = 2;
+  } else {
+    int m = nb / 2 + 1;
+    int a = J / m, c = J - (J / m) * m;
+    int r_lo = 2 * a - 1 < 0 ? 0 : 2 * a - 1;
+    int r_hi = 2 * a > nb - 1 ? nb - 1 : 2 * a;
+    int c_lo = 2 * c - 1 < 0 ? 0 : 2 * c - 1;
+    int c_hi = 2 * c > nb - 1 ? nb - 1 : 2 * c;
+    g.bi0 = r_lo; g.bj0 = c_lo; g.nbr = r_hi - r_lo + 1; g.nbc = c_hi - c_lo + 1;
+  }
+  g.r0 = g.bi0 * b; g.c0 = g.bj0 * b; g.H = g.nbr * b; g.W = g.nbc * b;
+  return g;
+}
+
+// composite cell of `part` that contains basic cell (bi, bj)
+__host__ __device__ inline int cell_of_basic(int part, int bi, int bj, int nb) {
+  if (part == 0) return (bi / 2) * (nb / 2) + bj / 2;
+  return ((bi + 1) / 2) * (nb / 2 + 1) + (bj + 1) / 2;
+}
+
+// state of one half-sweep
+struct SweepArgs {
+  LevelView L;
+  int part;                 // 0 = A, 1 = B
+  int ncells;
+  float eps;                // ε ([0,1]² units)
+  float err_tol;            // Err
+  int max_iter;
+  uint64_t trunc_q;         // Truncate threshold in fixed-point units
+  // input CSR (natural order)
+  const int64_t* rp;
+  const int32_t* col;
+  const uint64_t* val;
+  // workspace (capacity ws_cap entries; cell J owns [cell_off[J], +L_J))
+  int64_t ws_cap;
+  unsigned long long* ws_counter;
+  int64_t* cell_off;
+  int32_t* cell_ny;
+  int2* anchor_new;
+  int32_t* ws_ytmp;
+  uint64_t* ws_vtmp;
+  int32_t* ws_eta;          // packed (ηr, ηc) int16 pair
+  uint64_t* ws_nu;          // ν_cell fixed point
+  float* ws_lognu;          // log2 ν_cell (true mass)
+  float* ws_g;              // stabiliser / potential G(η) in log2 units
+  // dual state of the partition
+  float* alpha;             // α̃ per pixel ([0,1]² units)
+  int2* anchor;             // anchor pixel per cell
+  // outputs (tmp capacity 4·ws_cap)
+  int32_t* tmp_col;
+  uint64_t* tmp_val;
+  int32_t* row_cnt;         // per basic row (natural order)
+  int64_t* row_src;         // offset of the row's entries in tmp
+  double* cell_cost;
+  double* cell_errx;
+  int32_t* cell_iters;
+  int32_t* cell_status;     // bit0 not converged, bit1 non-finite, bit2 workspace overflow
+  int* err_flag;
+};
+
+// kernel launchers (dd_kernels.cu)
+cudaError_t launch_gather(const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sinkhorn(const SweepArgs& a, int threads, cudaStream_t s);
+cudaError_t launch_row_scan(const int32_t* cnt, int64_t* rp_out, int64_t* tile_sum, int nrows,
+                            cudaStream_t s);
+// rp_out[i] = tile_off[tile] + prefix within the tile; with tmp_col != NULL the
+// kept entries of each row are copied to col_out/val_out (capacity cap_out)
+cudaError_t launch_compact(const int32_t* cnt, const int64_t* src, const int64_t* tile_off,
+                           int64_t* rp_out, const int32_t* tmp_col, const uint64_t* tmp_val,
+                           int32_t* col_out, uint64_t* val_out, int64_t cap_out, int nrows,
+                           int* err_flag, cudaStream_t s);
+cudaError_t launch_init_product(LevelView L, int64_t* rp, int32_t* col, uint64_t* val, int imax,
+                                cudaStream_t s);
+
+struct SweepTotals {
+  double cost, errx;
+  long long iters_sum;
+  int iters_max, not_converged, nonfinite, overflow;
+};
+cudaError_t launch_reduce_cells(const SweepArgs& a, SweepTotals* out_dev, cudaStream_t s);
+cudaError_t launch_y_error(LevelView L, const int64_t* rp, const int32_t* col, const uint64_t* val,
+                           int nrows, unsigned long long* scratch, double* out_dev, cudaStream_t s);
+
+// refinement (§6.4): fine rows from coarse rows
+struct RefineArgs {
+  LevelView C, F;           // coarse and fine level (same b)
+  const int64_t* rp_c;
+  const int32_t* col_c;
+  const uint64_t* val_c;
+  const int64_t* rp_f;      // after scan
+  int32_t* cnt_f;
+  int32_t* col_f;
+  uint64_t* val_f;
+};
+cudaError_t launch_refine_count(const RefineArgs& r, cudaStream_t s);
+cudaError_t launch_refine_write(const RefineArgs& r, cudaStream_t s);
+// dual refinement: coarse α̃/anchors of partition `cpart` → fine α̃/anchors of `fpart`
+cudaError_t launch_refine_duals(LevelView C, LevelView F, int cpart, const float* alpha_c,
+                                const int2* anchor_c, int fpart, float* alpha_f, int2* anchor_f,
+                                cudaStream_t s);
+
+// plan reconstruction: counts per X pixel, then values
+cudaError_t launch_plan(const SweepArgs& a, float trunc, const int64_t* xrp, int32_t* xcnt,
+                        int32_t* pcol, double* pval, int write, cudaStream_t s);
+
+}  // namespace ddk

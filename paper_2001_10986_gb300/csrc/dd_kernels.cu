@@ -1,0 +1,1115 @@
+// CUDA kernels of one half-sweep of Algorithm 2 (§6.1) and of the
+// multi-scale driver (§6.4), written for sm_103a.
+//
+//   k_gather    ν_cell = Σ_{i∈J} ν_i: sorted union of ≤4 sparse rows by
+//               merge-path ranks, then duplicate folding (Algorithm 2).
+//   k_sinkhorn  cell Sinkhorn in log2 form with the §6.2 stop rule, then
+//               extraction ν_i = P_Y(π_cell|X_i×Y), BalanceMeasures and
+//               Truncate with in-row stream compaction.
+//   k_scan_*    prefix sums of the kept row lengths → new row offsets.
+//   k_compact   copies kept entries into the new CSR.
+//   k_refine_*  eq. FineBasicMarginals and the dual initialisation at the
+//               next level.
+//
+// All kernels are plain launches; none of them waits on another CTA.
+#include "dd_internal.cuh"
+
+#include <cfloat>
+#include <cstdint>
+
+namespace ddk {
+
+namespace {
+
+constexpr float kLn2 = 0.69314718055994530942f;
+constexpr float kNegBig = -1.0e30f;
+
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ int32_t pack_eta(int r, int c) {
+  return (int32_t)((uint32_t)(r & 0xffff) | ((uint32_t)(c & 0xffff) << 16));
+}
+__device__ __forceinline__ int eta_r(int32_t p) { return (int)(int16_t)(p & 0xffff); }
+__device__ __forceinline__ int eta_c(int32_t p) { return (int)(int16_t)((uint32_t)p >> 16); }
+
+// exclusive scan of one int per thread over the block; returns the prefix,
+// writes the block total. `ws` holds ≥ 32 ints.
+__device__ int block_exscan(int v, int* ws, int& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
+  }
+  __syncthreads();
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < nw ? ws[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    if (lane < nw) ws[lane] = w;
+  }
+  __syncthreads();
+  int before = warp > 0 ? ws[warp - 1] : 0;
+  total = ws[nw - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+template <typename T>
+__device__ T block_sum(T v, T* ws) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) ws[warp] = v;
+  __syncthreads();
+  T t = 0;
+  for (int w = 0; w < nw; ++w) t += ws[w];
+  __syncthreads();
+  return t;
+}
+
+// number of elements < y (strict) or <= y in a sorted int row
+__device__ __forceinline__ int64_t lower_bound_row(const int32_t* a, int64_t n, int y) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t m = (lo + hi) >> 1;
+    if (a[m] < y) lo = m + 1; else hi = m;
+  }
+  return lo;
+}
+__device__ __forceinline__ int64_t upper_bound_row(const int32_t* a, int64_t n, int y) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t m = (lo + hi) >> 1;
+    if (a[m] <= y) lo = m + 1; else hi = m;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint64_t frac_to_u64(float f) {
+  // f in [0,1] → round-down fixed point of f·2^64, clamped below 2^64
+  if (!(f > 0.0f)) return 0ull;
+  if (f >= 1.0f) return 0xffffffffffffffffull;
+  return __float2ull_rz(f * 18446744073709551616.0f);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// S1: gather ν_cell (Algorithm 2, line "ν_cell ← Σ_{i∈J} ν_i")
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gather(SweepArgs a) {
+  const int J = blockIdx.x;
+  if (*a.err_flag) return;
+  const LevelView& L = a.L;
+  const CellGeom g = cell_geom(a.part, J, L.nb, L.b);
+  __shared__ int64_t rs[4];
+  __shared__ int64_t rl[4];
+  __shared__ int nrows;
+  __shared__ int64_t s_off, s_tot;
+  __shared__ int s_anchor[2];
+  __shared__ float fred[32];
+  __shared__ int iws[32];
+
+  if (threadIdx.x == 0) {
+    int k = 0;
+    int64_t tot = 0;
+    for (int kr = 0; kr < g.nbr; ++kr)
+      for (int kc = 0; kc < g.nbc; ++kc) {
+        int bi = (g.bi0 + kr) * L.nb + g.bj0 + kc;
+        rs[k] = a.rp[bi];
+        rl[k] = a.rp[bi + 1] - a.rp[bi];
+        tot += rl[k];
+        ++k;
+      }
+    nrows = k;
+    unsigned long long off = atomicAdd(a.ws_counter, (unsigned long long)tot);
+    int64_t o = (int64_t)off;
+    if (o + tot > a.ws_cap) {
+      o = -1;
+      atomicOr(a.err_flag, 4);
+    }
+    s_off = o;
+    s_tot = tot;
+    a.cell_off[J] = o;
+  }
+  __syncthreads();
+  const int64_t off = s_off, tot = s_tot;
+  if (off < 0) return;
+
+  // merge-path rank of every element of the ≤4 sorted rows
+  float sw = 0.f, sr = 0.f, sc = 0.f;
+  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+    int r = 0;
+    int64_t k = e;
+    while (k >= rl[r]) { k -= rl[r]; ++r; }
+    const int y = a.col[rs[r] + k];
+    const uint64_t v = a.val[rs[r] + k];
+    int64_t rank = k;
+    for (int r2 = 0; r2 < nrows; ++r2) {
+      if (r2 == r) continue;
+      const int32_t* row = a.col + rs[r2];
+      rank += (r2 < r) ? upper_bound_row(row, rl[r2], y) : lower_bound_row(row, rl[r2], y);
+    }
+    a.ws_ytmp[off + rank] = y;
+    a.ws_vtmp[off + rank] = v;
+    const float vf = (float)v * kFixToFloat;
+    const int yr = y / L.n, yc = y - (y / L.n) * L.n;
+    sw += vf;
+    sr += vf * (float)yr;
+    sc += vf * (float)yc;
+  }
+  sw = block_sum(sw, fred);
+  sr = block_sum(sr, fred);
+  sc = block_sum(sc, fred);
+  if (threadIdx.x == 0) {
+    // anchor so that η ≈ ξ for the bulk of the cell's mass
+    float cr = sw > 0.f ? sr / sw : (float)g.r0;
+    float cc = sw > 0.f ? sc / sw : (float)g.c0;
+    s_anchor[0] = __float2int_rn(cr - 0.5f * (float)(g.H - 1));
+    s_anchor[1] = __float2int_rn(cc - 0.5f * (float)(g.W - 1));
+    a.anchor_new[J] = make_int2(s_anchor[0], s_anchor[1]);
+  }
+  __syncthreads();
+  const int ya = s_anchor[0], yc0 = s_anchor[1];
+
+  // fold duplicates, keep sorted order
+  int carry = 0;
+  for (int64_t base = 0; base < tot; base += blockDim.x) {
+    const int64_t p = base + threadIdx.x;
+    int head = 0;
+    int y = 0;
+    if (p < tot) {
+      y = a.ws_ytmp[off + p];
+      head = (p == 0) || (a.ws_ytmp[off + p - 1] != y);
+    }
+    int chunk_total;
+    int u = block_exscan(head, iws, chunk_total);
+    if (head) {
+      uint64_t s = a.ws_vtmp[off + p];
+      for (int64_t q = p + 1; q < tot && a.ws_ytmp[off + q] == y; ++q) s += a.ws_vtmp[off + q];
+      const int64_t w = off + carry + u;
+      const int yr = y / L.n, yc = y - (y / L.n) * L.n;
+      a.ws_eta[w] = pack_eta(yr - ya, yc - yc0);
+      a.ws_nu[w] = s;
+      a.ws_lognu[w] = log2f((float)s * kFixToFloat);
+    }
+    carry += chunk_total;
+  }
+  if (threadIdx.x == 0) a.cell_ny[J] = carry;
+}
+
+// ---------------------------------------------------------------------------
+// S2-S5: cell Sinkhorn + extraction + BalanceMeasures + Truncate
+// ---------------------------------------------------------------------------
+// Thread layout: every y of the cell support is handled by a group of G
+// consecutive threads; thread g of the group owns RPT = 32/W pixel rows
+// (32 pixels) of the H×W cell. Potentials in log2 units:
+//   F(ξ) = f̃(ξ)/(ε ln 2),  G(η) = g̃(η)/(ε ln 2),  κ = Δ²/(ε ln 2),
+//   π(x,y) = 2^(F(ξ) + G(η) − κ|ξ−η|²).
+// A Y-iteration with stabiliser Gs(y) computes p = 2^(F + Gs − κc̃),
+// s(y) = Σ_x p, G(y) = Gs + log2 ν(y) − log2 s, and the X-marginal of the new
+// plan as Σ_y p·ν(y)/s(y). The previous G is the stabiliser, so p is a plan
+// entry of the previous iterate and s(y) stays near ν(y): no running maximum
+// is needed after the first iteration, which takes Gs = −max_x(F − κc̃).
+
+constexpr int kMaxHW = 256;
+
+struct SinkSmem {
+  float F[kMaxHW];
+  float l2mu[kMaxHW];
+  float mu[kMaxHW];
+  float PX[kMaxHW];
+  float red[8][kMaxHW];
+  float fws[32];
+  int iws[32];
+  unsigned long long uws[32];
+  double dws[32];
+  float s_err;
+  int s_stop;
+  int s_flag;
+  uint64_t q64[4];
+  uint64_t w64[4];
+  int nsur, ndef, last_def;
+  int sur[4], def[4];
+};
+
+template <int W, int G>
+struct SinkCfg {
+  static constexpr int RPT = 32 / W;
+};
+
+template <int G>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <int G>
+__device__ __forceinline__ float group_max(float v) {
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Sum v[0..31] over the lanes of a warp that share lane%G; afterwards lane
+// holds G fully reduced values for chunk-local x = base + j.
+template <int G>
+__device__ __forceinline__ int warp_reduce_scatter(float (&v)[32], int lane) {
+  int base = 0;
+#pragma unroll
+  for (int m = 16, cnt = 32; m >= G; m >>= 1, cnt >>= 1) {
+    const int half = cnt >> 1;
+    const bool up = (lane & m) != 0;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      float send = up ? v[j] : v[j + half];
+      float keep = up ? v[j + half] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+    }
+    if (up) base += half;
+  }
+  return base;
+}
+
+template <int W, int G>
+__device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g, SinkSmem& sm) {
+  constexpr int RPT = 32 / W;
+  const LevelView& L = a.L;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int NT = blockDim.x;
+  const int gid = tid % G, slot = tid / G, YS = NT / G;
+  const int HW = g.H * g.W;
+
+  const int64_t off = a.cell_off[J];
+  if (off < 0) {
+    if (tid == 0) a.cell_status[J] = 4;
+    return;
+  }
+  const int ny = a.cell_ny[J];
+  const int2 anc_old = a.anchor[J];
+  const int2 anc = a.anchor_new[J];
+  const float d2 = (float)(L.spacing * L.spacing);
+  const float inv_eln2 = 1.0f / (a.eps * kLn2);
+  const float kappa = (float)(L.spacing * L.spacing / ((double)a.eps * 0.69314718055994530942));
+  const int Dr = g.r0 - anc.x, Dc = g.c0 - anc.y;
+  const int shr = anc.x - anc_old.x, shc = anc.y - anc_old.y;
+
+  // potentials of the cell in the new frame
+  for (int x = tid; x < HW; x += NT) {
+    const int ar = x / g.W, ac = x - (x / g.W) * g.W;
+    const int p = (g.r0 + ar) * L.n + g.c0 + ac;
+    const float l2 = L.log2mu[p];
+    float at = a.alpha[p] + 2.0f * d2 * (float)(shr * ar + shc * ac);
+    sm.F[x] = at * inv_eln2 + l2;
+    sm.l2mu[x] = l2;
+    sm.mu[x] = L.mu_f[p];
+  }
+  float tol_part = 0.f, nu_part = 0.f;
+  for (int x = tid; x < HW; x += NT) tol_part += sm.mu[x];
+  for (int k = tid; k < ny; k += NT) nu_part += (float)a.ws_nu[off + k] * kFixToFloat;
+  __syncthreads();
+  const float muJ = block_sum(tol_part, sm.fws);
+  const float nuJ = block_sum(nu_part, sm.fws);
+  const float tol = a.err_tol * muJ;
+  // truncated mass leaves ‖ν_cell‖ ≤ ‖μ_J‖: the stopping test compares P_X π
+  // with μ rescaled to ‖ν_cell‖ (the §6.2 rule when nothing was truncated)
+  const float mscale = muJ > 0.f ? nuJ / muJ : 1.f;
+
+  float Fr[RPT][W];
+  int arow[RPT];
+  auto load_F = [&]() {
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      arow[r] = gid * RPT + r;
+#pragma unroll
+      for (int c = 0; c < W; ++c)
+        Fr[r][c] = (arow[r] < g.H && c < g.W) ? sm.F[arow[r] * g.W + c] : kNegBig;
+    }
+  };
+  load_F();
+
+  float acc[32];
+  float pv[32];
+  int it = 0;
+  float errx = 0.f;
+  bool converged = false, bad = false;
+  for (;;) {
+    // ---- Y-iteration + X-marginal of the new plan ----
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] = 0.f;
+    for (int k0 = 0; k0 < ny; k0 += YS) {
+      const int k = k0 + slot;
+      const bool valid = k < ny;
+      const int kk = valid ? k : 0;
+      const int32_t e = a.ws_eta[off + kk];
+      const int er = eta_r(e), ec = eta_c(e);
+      const float lognu = a.ws_lognu[off + kk];
+      float Cc[W];
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        float t = (float)(c - ec);
+        Cc[c] = kappa * t * t;
+      }
+      float Rq[RPT];
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        float t = (float)(arow[r] - er);
+        Rq[r] = kappa * t * t;
+      }
+      float Gs;
+      if (it == 0) {
+        float m = kNegBig;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+          for (int c = 0; c < W; ++c) m = fmaxf(m, Fr[r][c] - Rq[r] - Cc[c]);
+        m = group_max<G>(m);
+        Gs = -m;
+      } else {
+        Gs = a.ws_g[off + kk];
+      }
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const float Ra = Gs - Rq[r];
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+          float p = ex2(Fr[r][c] + Ra - Cc[c]);
+          pv[r * W + c] = p;
+          s += p;
+        }
+      }
+      s = group_sum<G>(s);
+      if (!(s > 1e-30f && s < 1e30f)) {
+        // stabiliser too far off: restart this y from the running maximum
+        float m = kNegBig;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+          for (int c = 0; c < W; ++c) m = fmaxf(m, Fr[r][c] - Rq[r] - Cc[c]);
+        m = group_max<G>(m);
+        Gs = -m;
+        s = 0.f;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          const float Ra = Gs - Rq[r];
+#pragma unroll
+          for (int c = 0; c < W; ++c) {
+            float p = ex2(Fr[r][c] + Ra - Cc[c]);
+            pv[r * W + c] = p;
+            s += p;
+          }
+        }
+        s = group_sum<G>(s);
+      }
+      const float ls = lg2(s);
+      const float rY = valid ? ex2(lognu - ls) : 0.f;
+      if (valid && gid == 0) a.ws_g[off + k] = Gs + lognu - ls;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) acc[q] = fmaf(rY, pv[q], acc[q]);
+    }
+    // ---- reduce the X-marginal over y ----
+    {
+      const int base = warp_reduce_scatter<G>(acc, lane);
+#pragma unroll
+      for (int j = 0; j < G; ++j) sm.red[warp][gid * 32 + base + j] = acc[j];
+    }
+    __syncthreads();
+    float ep = 0.f, er = 0.f;
+    const int nw = NT >> 5;
+    for (int x = tid; x < HW; x += NT) {
+      // chunk gid owns rows [gid·RPT, (gid+1)·RPT) = chunk-local x of W·RPT = 32
+      float px = 0.f;
+      for (int w = 0; w < nw; ++w) px += sm.red[w][x];
+      sm.PX[x] = px;
+      ep += fabsf(px - sm.mu[x] * mscale);
+      er += fabsf(px - sm.mu[x]);
+    }
+    ep = block_sum(ep, sm.fws);
+    er = block_sum(er, sm.fws);
+    ++it;
+    if (tid == 0) {
+      int stop = 0;
+      if (!(ep == ep) || isinf(ep)) stop = 2;
+      else if (ep <= tol) stop = 1;
+      else if (it >= a.max_iter) stop = 3;
+      sm.s_stop = stop;
+      sm.s_err = er;
+    }
+    __syncthreads();
+    const int stop = sm.s_stop;
+    errx = sm.s_err;
+    if (stop) {
+      converged = stop == 1;
+      bad = stop == 2;
+      break;
+    }
+    // ---- X-iteration: F ← F + log2 μ − log2 P_X π ----
+    for (int x = tid; x < HW; x += NT) {
+      const float px = sm.PX[x];
+      if (px > 1e-37f && px < 1e37f) {
+        sm.F[x] += sm.l2mu[x] - lg2(px);
+      } else {
+        // full log-sum-exp over the support for this x
+        const int ar = x / g.W, ac = x - (x / g.W) * g.W;
+        float m = kNegBig;
+        for (int k = 0; k < ny; ++k) {
+          const int32_t e = a.ws_eta[off + k];
+          const float tr = (float)(ar - eta_r(e)), tc = (float)(ac - eta_c(e));
+          m = fmaxf(m, a.ws_g[off + k] - kappa * (tr * tr + tc * tc));
+        }
+        float s = 0.f;
+        for (int k = 0; k < ny; ++k) {
+          const int32_t e = a.ws_eta[off + k];
+          const float tr = (float)(ar - eta_r(e)), tc = (float)(ac - eta_c(e));
+          s += ex2(a.ws_g[off + k] - kappa * (tr * tr + tc * tc) - m);
+        }
+        sm.F[x] = sm.l2mu[x] - (m + lg2(s));
+      }
+    }
+    __syncthreads();
+    load_F();
+  }
+
+  // ---- epilogue: final plan → fractions per basic cell, cost ----
+  const int nbas = g.nbr * g.nbc;
+  const int bsh = __ffs(L.b) - 1;  // b is a power of two
+  const int64_t tbase = 4 * off;
+  double cost_acc = 0.0;
+  for (int k0 = 0; k0 < ny; k0 += YS) {
+    const int k = k0 + slot;
+    const bool valid = k < ny;
+    const int kk = valid ? k : 0;
+    const int32_t e = a.ws_eta[off + kk];
+    const int er = eta_r(e), ec = eta_c(e);
+    const float Gs = a.ws_g[off + kk];
+    float Cc[W], Dcc[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      float t = (float)(c - ec);
+      Cc[c] = kappa * t * t;
+      float u = (float)(Dc + c - ec);
+      Dcc[c] = u * u;
+    }
+    float q[4] = {0.f, 0.f, 0.f, 0.f};
+    float cst = 0.f, s = 0.f;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const float tr = (float)(arow[r] - er);
+      const float Ra = Gs - kappa * tr * tr;
+      const float ur = (float)(Dr + arow[r] - er);
+      const float Drr = ur * ur;
+      const int kb_r = (arow[r] >> bsh) * g.nbc;
+      float rs = 0.f;
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        float p = ex2(Fr[r][c] + Ra - Cc[c]);
+        rs += p;
+        cst = fmaf(p, Drr + Dcc[c], cst);
+        int kb = kb_r + (c >> bsh);
+        if (arow[r] < g.H && c < g.W) {
+          // kb < 4 for valid pixels
+          if (kb == 0) q[0] += p; else if (kb == 1) q[1] += p; else if (kb == 2) q[2] += p; else q[3] += p;
+        }
+      }
+      s += rs;
+    }
+    s = group_sum<G>(s);
+    cst = group_sum<G>(cst);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q[i] = group_sum<G>(q[i]);
+    if (valid && gid == 0) {
+      const uint64_t nuJ = a.ws_nu[off + k];
+      const float S = q[0] + q[1] + q[2] + q[3];
+      int imax = 0;
+      for (int i = 1; i < nbas; ++i)
+        if (q[i] > q[imax]) imax = i;
+      uint64_t rest = nuJ;
+      const int y = (anc.x + er) * L.n + (anc.y + ec);
+      const float invS = S > 0.f ? 1.0f / S : 0.f;
+      for (int i = 0; i < nbas; ++i) {
+        if (i == imax) continue;
+        const uint64_t v = __umul64hi(nuJ, frac_to_u64(q[i] * invS));
+        rest -= v;
+        a.tmp_val[tbase + (int64_t)i * ny + k] = v;
+        a.tmp_col[tbase + (int64_t)i * ny + k] = y;
+      }
+      a.tmp_val[tbase + (int64_t)imax * ny + k] = rest;
+      a.tmp_col[tbase + (int64_t)imax * ny + k] = y;
+      const double nuf = (double)nuJ * (1.0 / kFixOne);
+      if (s > 0.f) cost_acc += (double)cst * (nuf / (double)s);
+    }
+  }
+  __syncthreads();
+
+  // ---- BalanceMeasures: proportional transfer from surplus to deficit ----
+  unsigned long long msum[4] = {0, 0, 0, 0};
+  for (int k = tid; k < ny; k += NT)
+    for (int i = 0; i < nbas; ++i) msum[i] += a.tmp_val[tbase + (int64_t)i * ny + k];
+  for (int i = 0; i < nbas; ++i) msum[i] = block_sum<unsigned long long>(msum[i], sm.uws);
+  if (tid == 0) {
+    long long d[4];
+    long long dtot = 0;
+    sm.nsur = 0;
+    sm.ndef = 0;
+    for (int i = 0; i < nbas; ++i) {
+      const int bi = (g.bi0 + i / g.nbc) * L.nb + g.bj0 + (i % g.nbc);
+      d[i] = (long long)(msum[i] - L.M_q[bi]);
+      if (d[i] > 0 && msum[i] > 0) {
+        sm.sur[sm.nsur] = i;
+        sm.q64[sm.nsur] = (uint64_t)fmin((double)d[i] / (double)msum[i] * 18446744073709551616.0,
+                                         18446744073709549568.0);
+        sm.nsur++;
+      } else if (d[i] < 0) {
+        sm.def[sm.ndef++] = i;
+        dtot += -d[i];
+      }
+    }
+    for (int j = 0; j < sm.ndef; ++j) {
+      const int i = sm.def[j];
+      sm.w64[j] = (uint64_t)fmin((double)(-d[i]) / (double)dtot * 18446744073709551616.0,
+                                 18446744073709549568.0);
+    }
+  }
+  __syncthreads();
+  if (sm.nsur > 0 && sm.ndef > 0) {
+    for (int k = tid; k < ny; k += NT) {
+      uint64_t T = 0;
+      for (int j = 0; j < sm.nsur; ++j) {
+        const int64_t idx = tbase + (int64_t)sm.sur[j] * ny + k;
+        const uint64_t v = a.tmp_val[idx];
+        const uint64_t t = __umul64hi(v, sm.q64[j]);
+        a.tmp_val[idx] = v - t;
+        T += t;
+      }
+      uint64_t rem = T;
+      for (int j = 0; j + 1 < sm.ndef; ++j) {
+        const int64_t idx = tbase + (int64_t)sm.def[j] * ny + k;
+        const uint64_t t = __umul64hi(T, sm.w64[j]);
+        a.tmp_val[idx] += t;
+        rem -= t;
+      }
+      a.tmp_val[tbase + (int64_t)sm.def[sm.ndef - 1] * ny + k] += rem;
+    }
+  }
+  __syncthreads();
+
+  // ---- Truncate + in-row compaction ----
+  for (int i = 0; i < nbas; ++i) {
+    const int64_t rb = tbase + (int64_t)i * ny;
+    int carry = 0;
+    for (int k0 = 0; k0 < ny; k0 += NT) {
+      const int k = k0 + tid;
+      uint64_t v = 0;
+      int y = 0;
+      int keep = 0;
+      if (k < ny) {
+        v = a.tmp_val[rb + k];
+        y = a.tmp_col[rb + k];
+        keep = v > a.trunc_q;
+      }
+      int tot;
+      const int pos = block_exscan(keep, sm.iws, tot);  // contains the barrier
+      if (keep) {
+        a.tmp_val[rb + carry + pos] = v;
+        a.tmp_col[rb + carry + pos] = y;
+      }
+      carry += tot;
+      __syncthreads();
+    }
+    if (tid == 0) {
+      const int bi = (g.bi0 + i / g.nbc) * L.nb + g.bj0 + (i % g.nbc);
+      a.row_cnt[bi] = carry;
+      a.row_src[bi] = rb;
+    }
+  }
+
+  // ---- duals of the cell, statistics ----
+  const float eln2 = a.eps * kLn2;
+  for (int x = tid; x < HW; x += NT) {
+    const int ar = x / g.W, ac = x - (x / g.W) * g.W;
+    const int p = (g.r0 + ar) * L.n + g.c0 + ac;
+    a.alpha[p] = (sm.F[x] - sm.l2mu[x]) * eln2;
+  }
+  // costs: Δ²·Σ over leaders
+  double cs = cost_acc;
+  cs = block_sum<double>(cs, sm.dws);
+  if (tid == 0) {
+    a.anchor[J] = anc;
+    a.cell_cost[J] = cs * (double)L.spacing * (double)L.spacing;
+    a.cell_errx[J] = (double)errx;
+    a.cell_iters[J] = it;
+    a.cell_status[J] = (converged ? 0 : 1) | (bad ? 2 : 0);
+    if (bad) atomicOr(a.err_flag, 2);
+  }
+}
+
+// one launch per (W, G) class is avoided by dispatching inside one kernel
+__global__ void __launch_bounds__(256) k_sinkhorn(SweepArgs a) {
+  __shared__ SinkSmem sm;
+  const int J = blockIdx.x;
+  if (*a.err_flag & 4) return;
+  const CellGeom g = cell_geom(a.part, J, a.L.nb, a.L.b);
+  const int W = g.W, H = g.H;
+  if (W == 2) sinkhorn_cell<2, 1>(a, J, g, sm);
+  else if (W == 4) sinkhorn_cell<4, 1>(a, J, g, sm);
+  else if (W == 8) {
+    if (H <= 4) sinkhorn_cell<8, 1>(a, J, g, sm);
+    else if (H <= 8) sinkhorn_cell<8, 2>(a, J, g, sm);
+    else sinkhorn_cell<8, 4>(a, J, g, sm);
+  } else {
+    if (H <= 8) sinkhorn_cell<16, 4>(a, J, g, sm);
+    else sinkhorn_cell<16, 8>(a, J, g, sm);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// S6: prefix sums of the kept row lengths and compaction into the new CSR
+// ---------------------------------------------------------------------------
+constexpr int kScanTile = 1024;
+
+__global__ void __launch_bounds__(kScanTile) k_scan_tiles(const int32_t* cnt, int64_t* tile_sum, int n) {
+  __shared__ long long ws[32];
+  const int i = blockIdx.x * kScanTile + threadIdx.x;
+  long long v = i < n ? cnt[i] : 0;
+  v = block_sum<long long>(v, ws);
+  if (threadIdx.x == 0) tile_sum[blockIdx.x] = v;
+}
+
+__global__ void __launch_bounds__(kScanTile) k_scan_top(int64_t* tile_sum, int ntiles, int64_t* rp_out,
+                                                        int nrows) {
+  __shared__ long long lws[32];
+  long long carry = 0;
+  for (int t0 = 0; t0 < ntiles; t0 += kScanTile) {
+    const int t = t0 + threadIdx.x;
+    long long v = t < ntiles ? tile_sum[t] : 0;
+    // 64-bit exclusive scan via warp shuffles
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      long long u = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += u;
+    }
+    if (lane == 31) lws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      long long w = lws[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        long long u = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += u;
+      }
+      lws[lane] = w;
+    }
+    __syncthreads();
+    const long long before = warp > 0 ? lws[warp - 1] : 0;
+    const long long chunk = lws[31];
+    if (t < ntiles) tile_sum[t] = carry + before + x - v;
+    carry += chunk;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rp_out[nrows] = carry;
+}
+
+__global__ void __launch_bounds__(kScanTile) k_compact(const int32_t* cnt, const int64_t* src,
+                                                       const int64_t* tile_off, int64_t* rp_out,
+                                                       const int32_t* tmp_col, const uint64_t* tmp_val,
+                                                       int32_t* col_out, uint64_t* val_out,
+                                                       int64_t cap_out, int nrows, int* err_flag) {
+  __shared__ int iws[32];
+  __shared__ int64_t s_start[kScanTile];
+  const int i = blockIdx.x * kScanTile + threadIdx.x;
+  const int c = i < nrows ? cnt[i] : 0;
+  int tot;
+  const int pre = block_exscan(c, iws, tot);
+  const int64_t start = tile_off[blockIdx.x] + pre;
+  if (i < nrows) rp_out[i] = start;
+  s_start[threadIdx.x] = start;
+  __syncthreads();
+  if (tmp_col == nullptr || *err_flag) return;
+  // warp-cooperative copies, one row per warp at a time
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = warp; r < kScanTile; r += kScanTile / 32) {
+    const int row = blockIdx.x * kScanTile + r;
+    if (row >= nrows) break;
+    const int len = cnt[row];
+    const int64_t dst = s_start[r];
+    if (dst + len > cap_out) {
+      if (lane == 0) atomicOr(err_flag, 8);
+      continue;
+    }
+    const int64_t s0 = src[row];
+    for (int k = lane; k < len; k += 32) {
+      col_out[dst + k] = tmp_col[s0 + k];
+      val_out[dst + k] = tmp_val[s0 + k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// statistics
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals* out) {
+  __shared__ double dws[32];
+  __shared__ long long lws[32];
+  __shared__ int iws[32];
+  double c = 0.0, e = 0.0;
+  long long its = 0;
+  int mx = 0, nc = 0, nf = 0, ov = 0;
+  for (int J = threadIdx.x; J < a.ncells; J += blockDim.x) {
+    const int st = a.cell_status[J];
+    if (st & 4) { ++ov; continue; }
+    c += a.cell_cost[J];
+    e += a.cell_errx[J];
+    its += a.cell_iters[J];
+    mx = max(mx, a.cell_iters[J]);
+    nc += (st & 1) ? 1 : 0;
+    nf += (st & 2) ? 1 : 0;
+  }
+  c = block_sum<double>(c, dws);
+  e = block_sum<double>(e, dws);
+  its = block_sum<long long>(its, lws);
+  nc = block_sum<int>(nc, iws);
+  nf = block_sum<int>(nf, iws);
+  ov = block_sum<int>(ov, iws);
+  // max via shuffles
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) iws[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, iws[w]);
+    out->cost = c;
+    out->errx = e;
+    out->iters_sum = its;
+    out->iters_max = m;
+    out->not_converged = nc;
+    out->nonfinite = nf;
+    out->overflow = ov;
+  }
+}
+
+__global__ void k_scatter_rows(const int64_t* rp, int nrows, const int32_t* col, const uint64_t* val,
+                               unsigned long long* dense) {
+  const int64_t nnz = rp[nrows];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(dense + col[e], (unsigned long long)val[e]);
+}
+
+__global__ void k_y_error(const unsigned long long* dense, const uint64_t* nu, int n2, double* out) {
+  __shared__ double dws[32];
+  double s = 0.0;
+  for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n2; y += gridDim.x * blockDim.x) {
+    const long long d = (long long)(dense[y] - nu[y]);
+    s += (double)(d < 0 ? -d : d);
+  }
+  s = block_sum<double>(s, dws);
+  if (threadIdx.x == 0) atomicAdd(out, s * (1.0 / kFixOne));
+}
+
+// ---------------------------------------------------------------------------
+// initial coupling μ⊗ν on the coarsest level (§6.4)
+// ---------------------------------------------------------------------------
+__global__ void k_init_product(LevelView L, int64_t* rp, int32_t* col, uint64_t* val, int imax) {
+  const int n2 = L.n * L.n, nr = L.nb * L.nb;
+  const int y = blockIdx.x * blockDim.x + threadIdx.x;
+  if (y < nr + 1 && y <= nr) rp[y] = (int64_t)y * n2;
+  if (y >= n2) return;
+  const uint64_t nu = L.nu_q[y];
+  uint64_t rest = nu;
+  for (int i = 0; i < nr; ++i) {
+    col[(int64_t)i * n2 + y] = y;
+    if (i == imax) continue;
+    const uint64_t m = L.M_q[i];
+    const uint64_t m4 = m >= (1ull << 62) ? 0xffffffffffffffffull : (m << 2);
+    const uint64_t v = __umul64hi(nu, m4);   // ν(y)·M_i / 2^62
+    val[(int64_t)i * n2 + y] = v;
+    rest -= v;
+  }
+  val[(int64_t)imax * n2 + y] = rest;
+}
+
+// ---------------------------------------------------------------------------
+// refinement (§6.4, eq. FineBasicMarginals)
+// ---------------------------------------------------------------------------
+__global__ void k_refine_count(RefineArgs r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nbf = r.F.nb, nbc = r.C.nb;
+  if (i >= nbf * nbf) return;
+  const int R = i / nbf, S = i - (i / nbf) * nbf;
+  const int j = (R >> 1) * nbc + (S >> 1);
+  r.cnt_f[i] = (int32_t)(4 * (r.rp_c[j + 1] - r.rp_c[j]));
+}
+
+__global__ void __launch_bounds__(128) k_refine_write(RefineArgs r) {
+  const int i = blockIdx.x;
+  const int nbf = r.F.nb, nbc = r.C.nb, nc = r.C.n, nf = r.F.n;
+  const int R = i / nbf, S = i - (i / nbf) * nbf;
+  const int j = (R >> 1) * nbc + (S >> 1);
+  const int64_t c0 = r.rp_c[j];
+  const int64_t len = r.rp_c[j + 1] - c0;
+  const int32_t* row = r.col_c + c0;
+  const int64_t o = r.rp_f[i];
+  const double wmass = (double)r.F.M_q[i] / (double)r.C.M_q[j];
+  for (int64_t k = threadIdx.x; k < len; k += blockDim.x) {
+    const int yh = row[k];
+    const int pi = yh / nc, pj = yh - (yh / nc) * nc;
+    const int64_t k0 = lower_bound_row(row, len, pi * nc);
+    const int64_t k1 = lower_bound_row(row, len, (pi + 1) * nc);
+    const double vh = (double)r.val_c[c0 + k];
+    const double nuh = (double)r.C.nu_q[yh];
+#pragma unroll
+    for (int di = 0; di < 2; ++di)
+#pragma unroll
+      for (int dj = 0; dj < 2; ++dj) {
+        const int y = (2 * pi + di) * nf + 2 * pj + dj;
+        const int64_t pos = 4 * k0 + di * 2 * (k1 - k0) + 2 * (k - k0) + dj;
+        const double v = vh * ((double)r.F.nu_q[y] / nuh) * wmass;
+        r.col_f[o + pos] = y;
+        r.val_f[o + pos] = (uint64_t)__double2ull_rn(v);
+      }
+  }
+}
+
+// α of the coarse level at coarse pixel (pr, pc), FP64, from the reduced
+// storage of the cell of `cpart` containing it
+__device__ double coarse_alpha(const LevelView& C, int cpart, const float* alpha_c, const int2* anchor_c,
+                               int pr, int pc, CellGeom& gK) {
+  const int K = cell_of_basic(cpart, pr / C.b, pc / C.b, C.nb);
+  gK = cell_geom(cpart, K, C.nb, C.b);
+  const int2 an = anchor_c[K];
+  const double d2 = C.spacing * C.spacing;
+  const int Dr = gK.r0 - an.x, Dc = gK.c0 - an.y;
+  return (double)alpha_c[pr * C.n + pc] + 2.0 * d2 * ((double)Dr * (pr - gK.r0) + (double)Dc * (pc - gK.c0));
+}
+
+// first-order refinement of α inside the coarse cell (finite differences)
+__device__ double fine_alpha(const LevelView& C, int cpart, const float* alpha_c, const int2* anchor_c,
+                             int R, int S) {
+  const int pr = R >> 1, pc = S >> 1;
+  CellGeom gK;
+  const double a0 = coarse_alpha(C, cpart, alpha_c, anchor_c, pr, pc, gK);
+  CellGeom tmp;
+  double dr = 0.0, dc = 0.0;
+  if (gK.H > 1) {
+    const int lr = pr - gK.r0;
+    if (lr == 0) dr = coarse_alpha(C, cpart, alpha_c, anchor_c, pr + 1, pc, tmp) - a0;
+    else if (lr == gK.H - 1) dr = a0 - coarse_alpha(C, cpart, alpha_c, anchor_c, pr - 1, pc, tmp);
+    else
+      dr = 0.5 * (coarse_alpha(C, cpart, alpha_c, anchor_c, pr + 1, pc, tmp) -
+                  coarse_alpha(C, cpart, alpha_c, anchor_c, pr - 1, pc, tmp));
+  }
+  if (gK.W > 1) {
+    const int lc = pc - gK.c0;
+    if (lc == 0) dc = coarse_alpha(C, cpart, alpha_c, anchor_c, pr, pc + 1, tmp) - a0;
+    else if (lc == gK.W - 1) dc = a0 - coarse_alpha(C, cpart, alpha_c, anchor_c, pr, pc - 1, tmp);
+    else
+      dc = 0.5 * (coarse_alpha(C, cpart, alpha_c, anchor_c, pr, pc + 1, tmp) -
+                  coarse_alpha(C, cpart, alpha_c, anchor_c, pr, pc - 1, tmp));
+  }
+  const double orr = (R & 1) ? 0.25 : -0.25;
+  const double occ = (S & 1) ? 0.25 : -0.25;
+  return a0 + orr * dr + occ * dc;
+}
+
+__global__ void k_refine_duals(LevelView C, LevelView F, int cpart, const float* alpha_c,
+                               const int2* anchor_c, int fpart, float* alpha_f, int2* anchor_f) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= F.n * F.n) return;
+  const int R = x / F.n, S = x - (x / F.n) * F.n;
+  const int Jf = cell_of_basic(fpart, R / F.b, S / F.b, F.nb);
+  const CellGeom gf = cell_geom(fpart, Jf, F.nb, F.b);
+  // anchor: same physical displacement as the coarse cell holding the corner
+  const int pr0 = gf.r0 >> 1, pc0 = gf.c0 >> 1;
+  const int K0 = cell_of_basic(cpart, pr0 / C.b, pc0 / C.b, C.nb);
+  const CellGeom gK0 = cell_geom(cpart, K0, C.nb, C.b);
+  const int2 anK = anchor_c[K0];
+  const int Dfr = 2 * (gK0.r0 - anK.x), Dfc = 2 * (gK0.c0 - anK.y);
+  const double d2f = F.spacing * F.spacing;
+  const double af = fine_alpha(C, cpart, alpha_c, anchor_c, R, S);
+  const double acorner = fine_alpha(C, cpart, alpha_c, anchor_c, gf.r0, gf.c0);
+  const int xr = R - gf.r0, xc = S - gf.c0;
+  const double at = af - acorner - 2.0 * d2f * ((double)Dfr * xr + (double)Dfc * xc);
+  alpha_f[x] = (float)at;
+  if (xr == 0 && xc == 0) anchor_f[Jf] = make_int2(gf.r0 - Dfr, gf.c0 - Dfc);
+}
+
+// ---------------------------------------------------------------------------
+// coupling of the last partition: one Y-iteration per cell (dd_get_plan)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_plan(SweepArgs a, float trunc, const int64_t* xrp, int32_t* xcnt,
+                                              int32_t* pcol, double* pval, int write) {
+  const int J = blockIdx.x;
+  const LevelView& L = a.L;
+  const CellGeom g = cell_geom(a.part, J, L.nb, L.b);
+  const int64_t off = a.cell_off[J];
+  if (off < 0) return;
+  const int ny = a.cell_ny[J];
+  const int2 anc_old = a.anchor[J], anc = a.anchor_new[J];
+  const float d2 = (float)(L.spacing * L.spacing);
+  const float inv_eln2 = 1.0f / (a.eps * kLn2);
+  const float kappa = (float)(L.spacing * L.spacing / ((double)a.eps * 0.69314718055994530942));
+  const int shr = anc.x - anc_old.x, shc = anc.y - anc_old.y;
+  const int HW = g.H * g.W;
+  __shared__ float F[kMaxHW];
+  __shared__ int iws[32];
+  for (int x = threadIdx.x; x < HW; x += blockDim.x) {
+    const int ar = x / g.W, ac = x - (x / g.W) * g.W;
+    const int p = (g.r0 + ar) * L.n + g.c0 + ac;
+    F[x] = (a.alpha[p] + 2.0f * d2 * (float)(shr * ar + shc * ac)) * inv_eln2 + L.log2mu[p];
+  }
+  __syncthreads();
+  if (!write) {
+    // G(y) = log2 ν(y) − LSE_x(F − κc̃): written to ws_g
+    for (int k = threadIdx.x; k < ny; k += blockDim.x) {
+      const int32_t e = a.ws_eta[off + k];
+      const int er = eta_r(e), ec = eta_c(e);
+      float m = kNegBig;
+      for (int x = 0; x < HW; ++x) {
+        const float tr = (float)(x / g.W - er), tc = (float)(x % g.W - ec);
+        m = fmaxf(m, F[x] - kappa * (tr * tr + tc * tc));
+      }
+      float s = 0.f;
+      for (int x = 0; x < HW; ++x) {
+        const float tr = (float)(x / g.W - er), tc = (float)(x % g.W - ec);
+        s += ex2(F[x] - kappa * (tr * tr + tc * tc) - m);
+      }
+      a.ws_g[off + k] = a.ws_lognu[off + k] - m - lg2(s);
+    }
+    __syncthreads();
+  }
+  for (int x = 0; x < HW; ++x) {
+    const int ar = x / g.W, ac = x - (x / g.W) * g.W;
+    const int p = (g.r0 + ar) * L.n + g.c0 + ac;
+    int carry = 0;
+    for (int k0 = 0; k0 < ny; k0 += blockDim.x) {
+      const int k = k0 + threadIdx.x;
+      float v = 0.f;
+      int y = 0;
+      int keep = 0;
+      if (k < ny) {
+        const int32_t e = a.ws_eta[off + k];
+        const int er = eta_r(e), ec = eta_c(e);
+        const float tr = (float)(ar - er), tc = (float)(ac - ec);
+        v = ex2(F[x] + a.ws_g[off + k] - kappa * (tr * tr + tc * tc));
+        y = (anc.x + er) * L.n + anc.y + ec;
+        keep = v > trunc;
+      }
+      int tot;
+      const int pos = block_exscan(keep, iws, tot);
+      if (write && keep) {
+        pcol[xrp[p] + carry + pos] = y;
+        pval[xrp[p] + carry + pos] = (double)v;
+      }
+      carry += tot;
+    }
+    if (!write && threadIdx.x == 0) xcnt[p] = carry;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_gather(const SweepArgs& a, cudaStream_t s) {
+  k_gather<<<a.ncells, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sinkhorn(const SweepArgs& a, int threads, cudaStream_t s) {
+  if (threads != 64 && threads != 128 && threads != 256) threads = 128;
+  k_sinkhorn<<<a.ncells, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_scan(const int32_t* cnt, int64_t* rp_out, int64_t* tile_sum, int nrows,
+                            cudaStream_t s) {
+  const int ntiles = (nrows + kScanTile - 1) / kScanTile;
+  k_scan_tiles<<<ntiles, kScanTile, 0, s>>>(cnt, tile_sum, nrows);
+  k_scan_top<<<1, kScanTile, 0, s>>>(tile_sum, ntiles, rp_out, nrows);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const int32_t* cnt, const int64_t* src, const int64_t* tile_off,
+                           int64_t* rp_out, const int32_t* tmp_col, const uint64_t* tmp_val,
+                           int32_t* col_out, uint64_t* val_out, int64_t cap_out, int nrows,
+                           int* err_flag, cudaStream_t s) {
+  const int ntiles = (nrows + kScanTile - 1) / kScanTile;
+  k_compact<<<ntiles, kScanTile, 0, s>>>(cnt, src, tile_off, rp_out, tmp_col, tmp_val, col_out,
+                                         val_out, cap_out, nrows, err_flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_product(LevelView L, int64_t* rp, int32_t* col, uint64_t* val, int imax,
+                                cudaStream_t s) {
+  const int n2 = L.n * L.n;
+  k_init_product<<<(n2 + 255) / 256, 256, 0, s>>>(L, rp, col, val, imax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_cells(const SweepArgs& a, SweepTotals* out_dev, cudaStream_t s) {
+  k_reduce_cells<<<1, 1024, 0, s>>>(a, out_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_y_error(LevelView L, const int64_t* rp, const int32_t* col, const uint64_t* val,
+                           int nrows, unsigned long long* scratch, double* out_dev, cudaStream_t s) {
+  const int n2 = L.n * L.n;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (size_t)n2, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(out_dev, 0, sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  k_scatter_rows<<<1216, 256, 0, s>>>(rp, nrows, col, val, scratch);
+  const int blocks = (n2 + 255) / 256 < 1216 ? (n2 + 255) / 256 : 1216;
+  k_y_error<<<blocks, 256, 0, s>>>(scratch, L.nu_q, n2, out_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_count(const RefineArgs& r, cudaStream_t s) {
+  const int nr = r.F.nb * r.F.nb;
+  k_refine_count<<<(nr + 255) / 256, 256, 0, s>>>(r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_write(const RefineArgs& r, cudaStream_t s) {
+  k_refine_write<<<r.F.nb * r.F.nb, 128, 0, s>>>(r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_duals(LevelView C, LevelView F, int cpart, const float* alpha_c,
+                                const int2* anchor_c, int fpart, float* alpha_f, int2* anchor_f,
+                                cudaStream_t s) {
+  const int n2 = F.n * F.n;
+  k_refine_duals<<<(n2 + 255) / 256, 256, 0, s>>>(C, F, cpart, alpha_c, anchor_c, fpart, alpha_f,
+                                                  anchor_f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plan(const SweepArgs& a, float trunc, const int64_t* xrp, int32_t* xcnt,
+                        int32_t* pcol, double* pval, int write, cudaStream_t s) {
+  k_plan<<<a.ncells, 256, 0, s>>>(a, trunc, xrp, xcnt, pcol, pval, write);
+  return cudaGetLastError();
+}
+
+}  // namespace ddk

@@ -1,0 +1,246 @@
+"""Python binding of the C ABI in include/dd.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and forwards
+its arguments; all computation runs in libddot.so. Importing this module
+raises if the library has not been built (see paper_2001_10986_gb300.build).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+DD_OK, DD_ERR_ARG, DD_ERR_CUDA, DD_ERR_OOM, DD_ERR_CAPACITY, DD_ERR_NUMERIC, DD_ERR_STATE = range(7)
+_STATUS = {0: "DD_OK", 1: "DD_ERR_ARG", 2: "DD_ERR_CUDA", 3: "DD_ERR_OOM", 4: "DD_ERR_CAPACITY",
+           5: "DD_ERR_NUMERIC", 6: "DD_ERR_STATE"}
+
+
+class dd_grid(C.Structure):
+    _fields_ = [("n", C.c_int32), ("levels", C.c_int32)]
+
+
+class dd_eps_step(C.Structure):
+    _fields_ = [("eps", C.c_double), ("sweeps", C.c_int32), ("level", C.c_int32)]
+
+
+class dd_options(C.Structure):
+    _fields_ = [("err_tol", C.c_double), ("trunc", C.c_double), ("max_iter", C.c_int32),
+                ("threads_per_cell", C.c_int32), ("stream", C.c_void_p), ("debug_flags", C.c_uint64)]
+
+
+class dd_sweep_stats(C.Structure):
+    _fields_ = [("level", C.c_int32), ("partition", C.c_int32), ("eps", C.c_double), ("nnz", C.c_int64),
+                ("max_iters", C.c_int32), ("mean_iters", C.c_double), ("cells_not_converged", C.c_int32),
+                ("sweeps_done", C.c_int64)]
+
+
+class DDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+if not os.path.exists(LIB):
+    raise ImportError(f"{LIB} is missing: build it with paper_2001_10986_gb300.build.build()")
+_lib = C.CDLL(LIB)
+
+_P = C.c_void_p
+_pd = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_pi64 = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_pi32 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+
+_lib.dd_options_default.argtypes = [C.POINTER(dd_options)]
+_lib.dd_options_default.restype = None
+_lib.dd_create.argtypes = [_pd, _pd, C.POINTER(dd_grid), C.c_int32, C.POINTER(dd_eps_step), C.c_int32,
+                           C.POINTER(dd_options), C.POINTER(_P)]
+_lib.dd_set_state.argtypes = [_P, _pi64, _pi32, _pd, _P, _P]
+_lib.dd_half_sweep.argtypes = [_P, C.c_int32, C.c_double]
+_lib.dd_sweep.argtypes = [_P, C.c_int32, C.POINTER(dd_sweep_stats)]
+_lib.dd_run_schedule.argtypes = [_P, C.POINTER(dd_sweep_stats)]
+_lib.dd_cost.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+_lib.dd_get_basic_marginals.argtypes = [_P, C.POINTER(C.c_int64), _P, _P, _P, C.c_int64]
+_lib.dd_get_plan.argtypes = [_P, C.c_double, C.POINTER(C.c_int64), _P, _P, _P, C.c_int64]
+_lib.dd_get_duals.argtypes = [_P, C.c_int32, _pd]
+_lib.dd_get_info.argtypes = [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                             C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+_lib.dd_destroy.argtypes = [_P]
+_lib.dd_destroy.restype = None
+_lib.dd_last_error.argtypes = [_P]
+_lib.dd_last_error.restype = C.c_char_p
+for _f in ("dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep", "dd_run_schedule", "dd_cost",
+           "dd_get_basic_marginals", "dd_get_plan", "dd_get_duals", "dd_get_info"):
+    getattr(_lib, _f).restype = C.c_int
+
+EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep",
+            "dd_run_schedule", "dd_cost", "dd_get_basic_marginals", "dd_get_plan", "dd_get_duals",
+            "dd_get_info", "dd_destroy", "dd_last_error")
+
+
+def _check(ctx, st):
+    if st != DD_OK:
+        raise DDError(st, (_lib.dd_last_error(ctx) or b"").decode())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)      # torch.cuda.Stream
+
+
+def dd_options_default(**overrides) -> dd_options:
+    o = dd_options()
+    _lib.dd_options_default(C.byref(o))
+    for k, v in overrides.items():
+        if k == "stream":
+            v = _stream_ptr(v)
+        setattr(o, k, v)
+    return o
+
+
+def dd_create(mu, nu, n, levels, b, schedule, opt: dd_options | None = None):
+    """schedule: iterable of (eps, sweeps, level). Returns an opaque handle."""
+    mu = np.ascontiguousarray(mu, dtype=np.float64).ravel()
+    nu = np.ascontiguousarray(nu, dtype=np.float64).ravel()
+    steps = list(schedule)
+    arr = (dd_eps_step * len(steps))(*[dd_eps_step(float(e), int(s), int(l)) for e, s, l in steps])
+    g = dd_grid(int(n), int(levels))
+    out = _P()
+    st = _lib.dd_create(mu, nu, C.byref(g), int(b), arr, len(steps),
+                        C.byref(opt) if opt is not None else None, C.byref(out))
+    _check(None, st)
+    return out
+
+
+def dd_set_state(ctx, row_ptr, col, val, alpha_A=None, alpha_B=None):
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    vl = np.ascontiguousarray(val, dtype=np.float64)
+    aA = None if alpha_A is None else np.ascontiguousarray(alpha_A, dtype=np.float64).ravel()
+    aB = None if alpha_B is None else np.ascontiguousarray(alpha_B, dtype=np.float64).ravel()
+    _check(ctx, _lib.dd_set_state(ctx, rp, cl, vl, None if aA is None else aA.ctypes.data,
+                                  None if aB is None else aB.ctypes.data))
+
+
+def dd_half_sweep(ctx, partition, eps):
+    _check(ctx, _lib.dd_half_sweep(ctx, int(partition), float(eps)))
+
+
+def dd_sweep(ctx, n_sweeps=1) -> dd_sweep_stats:
+    st = dd_sweep_stats()
+    _check(ctx, _lib.dd_sweep(ctx, int(n_sweeps), C.byref(st)))
+    return st
+
+
+def dd_run_schedule(ctx) -> dd_sweep_stats:
+    st = dd_sweep_stats()
+    _check(ctx, _lib.dd_run_schedule(ctx, C.byref(st)))
+    return st
+
+
+def dd_cost(ctx, with_y=True):
+    c, ex, ey = C.c_double(), C.c_double(), C.c_double()
+    _check(ctx, _lib.dd_cost(ctx, C.byref(c), C.byref(ex), C.byref(ey) if with_y else None))
+    return c.value, ex.value, (ey.value if with_y else None)
+
+
+def dd_get_info(ctx):
+    """Returns (level, n_level, n_basic, eps, nnz)."""
+    lv, nl, nbs, e, nz = C.c_int32(), C.c_int32(), C.c_int32(), C.c_double(), C.c_int64()
+    _check(ctx, _lib.dd_get_info(ctx, C.byref(lv), C.byref(nl), C.byref(nbs), C.byref(e), C.byref(nz)))
+    return lv.value, nl.value, nbs.value, e.value, nz.value
+
+
+def dd_get_basic_marginals(ctx):
+    """Returns (row_ptr int64, col int32, val float64), natural order of basic cells."""
+    _, _, nrows, _, _ = dd_get_info(ctx)
+    nnz = C.c_int64()
+    _check(ctx, _lib.dd_get_basic_marginals(ctx, C.byref(nnz), None, None, None, 0))
+    rp = np.zeros(nrows + 1, dtype=np.int64)
+    col = np.zeros(max(nnz.value, 1), dtype=np.int32)
+    val = np.zeros(max(nnz.value, 1), dtype=np.float64)
+    _check(ctx, _lib.dd_get_basic_marginals(ctx, C.byref(nnz), rp.ctypes.data, col.ctypes.data,
+                                            val.ctypes.data, col.size))
+    return rp, col[:nnz.value], val[:nnz.value]
+
+
+def dd_get_plan(ctx, trunc=0.0):
+    """Returns (row_ptr over X pixels, col, val) of the coupling of the last partition."""
+    _, nl, _, _, _ = dd_get_info(ctx)
+    nnz = C.c_int64()
+    _check(ctx, _lib.dd_get_plan(ctx, float(trunc), C.byref(nnz), None, None, None, 0))
+    rp = np.zeros(nl * nl + 1, dtype=np.int64)
+    col = np.zeros(max(nnz.value, 1), dtype=np.int32)
+    val = np.zeros(max(nnz.value, 1), dtype=np.float64)
+    _check(ctx, _lib.dd_get_plan(ctx, float(trunc), C.byref(nnz), rp.ctypes.data, col.ctypes.data,
+                                 val.ctypes.data, col.size))
+    return rp, col[:nnz.value], val[:nnz.value]
+
+
+def dd_get_duals(ctx, partition):
+    _, nl, _, _, _ = dd_get_info(ctx)
+    out = np.zeros(nl * nl, dtype=np.float64)
+    _check(ctx, _lib.dd_get_duals(ctx, int(partition), out))
+    return out
+
+
+def dd_destroy(ctx):
+    _lib.dd_destroy(ctx)
+
+
+def dd_last_error(ctx=None) -> str:
+    return (_lib.dd_last_error(ctx) or b"").decode()
+
+
+class DD:
+    """Owner of one context; methods forward to the functions above."""
+
+    def __init__(self, mu, nu, b, levels, schedule, **opts):
+        mu = np.asarray(mu)
+        self.n = mu.shape[0]
+        self.b = b
+        self.levels = levels
+        self.opt = dd_options_default(**opts)
+        self.ctx = dd_create(mu, nu, self.n, levels, b, schedule, self.opt)
+
+    def set_state(self, row_ptr, col, val, alpha_A=None, alpha_B=None):
+        dd_set_state(self.ctx, row_ptr, col, val, alpha_A, alpha_B)
+
+    def half_sweep(self, partition, eps):
+        dd_half_sweep(self.ctx, partition, eps)
+
+    def sweep(self, n=1):
+        return dd_sweep(self.ctx, n)
+
+    def run_schedule(self):
+        return dd_run_schedule(self.ctx)
+
+    def cost(self, with_y=True):
+        return dd_cost(self.ctx, with_y)
+
+    def info(self):
+        return dd_get_info(self.ctx)
+
+    def basic_marginals(self):
+        return dd_get_basic_marginals(self.ctx)
+
+    def plan(self, trunc=0.0):
+        return dd_get_plan(self.ctx, trunc)
+
+    def duals(self, partition):
+        return dd_get_duals(self.ctx, partition)
+
+    def close(self):
+        if self.ctx:
+            dd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

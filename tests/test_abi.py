@@ -1,0 +1,75 @@
+"""The C-ABI library loads, exports every entry point of include/dd.h and
+rejects invalid arguments before touching the GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2001_10986_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    from paper_2001_10986_gb300 import dd
+    return dd
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "dd.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(dd_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for f in ("dd_create", "dd_sweep", "dd_get_plan", "dd_cost", "dd_half_sweep",
+              "dd_set_state", "dd_destroy", "dd_last_error"):
+        assert f in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    so = ctypes.CDLL(lib.LIB)
+    for name in _declared():
+        assert hasattr(so, name), name
+    assert set(_declared()) == set(lib.EXPORTED)
+
+
+def _create(lib, mu, nu, n=16, levels=1, b=4, sched=((0.01, 1, 0),)):
+    return lib.dd_create(mu, nu, n, levels, b, sched)
+
+
+def test_create_rejects_bad_arguments(lib):
+    n = 16
+    mu = np.full((n, n), 1.0 / n**2)
+    nu = mu.copy()
+    bad = mu.copy(); bad[3, 4] = np.nan
+    with pytest.raises(lib.DDError) as e:
+        _create(lib, bad, nu)
+    assert e.value.status == lib.DD_ERR_ARG
+    neg = mu.copy(); neg[0, 0] = -1e-3
+    with pytest.raises(lib.DDError):
+        _create(lib, neg, nu)
+    with pytest.raises(lib.DDError):
+        _create(lib, mu, nu * 2.0)                     # masses differ
+    with pytest.raises(lib.DDError):
+        _create(lib, mu, nu, b=3)                       # b not in {2,4,8}
+    with pytest.raises(lib.DDError):
+        _create(lib, mu, nu, levels=3)                  # coarsest 4 < 2b
+    with pytest.raises(lib.DDError):
+        _create(lib, mu, nu, sched=((0.01, 1, 1),))     # level out of range
+    with pytest.raises(lib.DDError):
+        _create(lib, mu, nu, sched=((-1.0, 1, 0),))     # eps <= 0
+    zero = mu.copy(); zero[:4, :4] = 0.0; zero /= zero.sum()
+    with pytest.raises(lib.DDError) as e:
+        _create(lib, zero, nu)                          # empty basic cell (Def. 3.1)
+    assert "basic cell" in str(e.value)
+
+
+def test_options_default(lib):
+    o = lib.dd_options_default()
+    assert o.err_tol == 1e-6 and o.trunc == 1e-15 and o.max_iter == 2000

@@ -1,0 +1,203 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (from the targets of the method's GPU form): basic marginals and
+pixel-level plan ≤ 1e-5 relative L1, transport cost ≤ 1e-6 relative, marginal
+errors ≤ 1e-6 L1. The GPU computes potentials in FP32; the oracle in FP64 with
+a tighter Sinkhorn tolerance.
+"""
+import numpy as np
+import pytest
+
+from oracle import dd as odd
+from paper_2001_10986_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+PLAN_TOL = 1e-5
+COST_TOL = 1e-6
+MARG_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2001_10986_gb300 import build
+    build.build()
+    from paper_2001_10986_gb300 import dd
+    return dd
+
+
+def _rel_l1(a, b):
+    return float(np.abs(a - b).sum() / np.abs(b).sum())
+
+
+def _dense_rows(rp, col, val, ny):
+    return odd.rows_to_dense(odd.rows_from_csr(rp, col, val), ny)
+
+
+def _dense_plan(rp, col, val, nx, ny):
+    P = np.zeros((nx, ny))
+    for x in range(nx):
+        P[x, col[rp[x]:rp[x + 1]]] = val[rp[x]:rp[x + 1]]
+    return P
+
+
+def _compare_run(lib, mu, nu, b, levels, sched, gpu_err=1e-6, oracle_err=1e-10, check_plan=True,
+                 threads=0):
+    n = mu.shape[0]
+    g = lib.DD(mu, nu, b, levels, sched, err_tol=gpu_err, threads_per_cell=threads)
+    st = g.run_schedule()
+    rp, col, val = g.basic_marginals()
+    cost, ex, ey = g.cost()
+    level, nl, _, eps, _ = g.info()
+    plan = g.plan(0.0) if check_plan else None
+    g.close()
+    ref = odd.run_schedule(mu, nu, b, levels, sched, odd.Params(err=oracle_err))
+    assert nl == ref.prob.n
+    ny = nl * nl
+    got = _dense_rows(rp, col, val, ny)
+    exp = odd.rows_to_dense(ref.rows, ny)
+    info = ref.history[-1][3]
+    out = dict(rows=_rel_l1(got, exp), cost=abs(cost - info.cost) / info.cost, err_x=ex, err_y=ey,
+               ref_err_y=odd.y_marginal_error(ref.prob, ref.rows), stats=st)
+    if check_plan:
+        P = _dense_plan(*plan, ny, ny)
+        Pref = odd.partition_plan(ref.prob, ref.last_part, ref.rows, ref.alpha[ref.last_part], ref.eps)
+        out["plan"] = _rel_l1(P, Pref)
+    return out
+
+
+def test_single_cell_is_sinkhorn(lib):
+    # n = 2b: partition A is one cell, so one A half-sweep is a full Sinkhorn solve
+    n, b, eps = 8, 4, 0.02
+    mu = syn.gaussian_mixture(n, 2, 0)
+    nu = syn.gaussian_mixture(n, 2, 1)
+    g = lib.DD(mu, nu, b, 1, [(eps, 1, 0)], err_tol=1e-6)
+    g.half_sweep(0, eps)
+    P = _dense_plan(*g.plan(0.0), n * n, n * n)
+    g.close()
+    prob = odd.GridProblem(mu, nu, b, 1.0 / n)
+    alpha = np.zeros(n * n)
+    rows, _ = odd.half_sweep(prob, "A", odd.product_state(prob), alpha, eps, odd.Params(err=1e-12))
+    Pref = odd.partition_plan(prob, "A", rows, alpha, eps)
+    assert _rel_l1(P, Pref) < PLAN_TOL
+
+
+def test_config1_full_schedule(lib):
+    # two 32×32 images of 3 blobs, 4×4 cells, ε halving 1.0 → 2h², 20 sweeps each
+    mu, nu = syn.image_pair("gm32_b4", 0)
+    sched = syn.halving_schedule(1.0, 2.0 / 32**2, 20)
+    r = _compare_run(lib, mu, nu, 4, 1, sched, gpu_err=1e-6, oracle_err=1e-8)
+    assert r["rows"] < PLAN_TOL, r
+    assert r["plan"] < PLAN_TOL, r
+    assert r["cost"] < COST_TOL, r
+    assert r["err_x"] < MARG_TOL and r["err_y"] < MARG_TOL, r
+
+
+def test_ragged_grid_fixed_eps(lib):
+    # 24×24 with 4×4 cells: 6×6 basic cells, B has corner, edge and full cells
+    mu = syn.gaussian_mixture(24, 3, 20)
+    nu = syn.gaussian_mixture(24, 3, 21)
+    r = _compare_run(lib, mu, nu, 4, 1, [(0.004, 12, 0)], gpu_err=1e-6)
+    assert r["rows"] < PLAN_TOL and r["plan"] < PLAN_TOL and r["cost"] < COST_TOL, r
+
+
+def test_two_levels_refinement(lib):
+    # 16² → 32² with the paper's per-level schedule, then 6 sweeps at 2h²
+    mu = syn.gaussian_mixture(32, 4, 30)
+    nu = syn.gaussian_mixture(32, 4, 31)
+    sched = syn.paper_schedule(32, 2, 6)
+    r = _compare_run(lib, mu, nu, 4, 2, sched, gpu_err=1e-6, oracle_err=1e-9)
+    assert r["rows"] < PLAN_TOL and r["cost"] < COST_TOL, r
+    assert r["err_y"] < MARG_TOL, r
+
+
+@pytest.mark.parametrize("b,n,eps,sweeps", [(8, 32, 0.004, 2), (2, 16, 0.01, 4)])
+def test_cell_sizes(lib, b, n, eps, sweeps):
+    mu = syn.gaussian_mixture(n, 3, 40 + b)
+    nu = syn.gaussian_mixture(n, 3, 41 + b)
+    r = _compare_run(lib, mu, nu, b, 1, [(eps, sweeps, 0)], gpu_err=1e-6, oracle_err=1e-9)
+    assert r["rows"] < PLAN_TOL and r["cost"] < COST_TOL, r
+
+
+@pytest.fixture(scope="module")
+def ref32():
+    mu = syn.gaussian_mixture(32, 3, 50)
+    nu = syn.gaussian_mixture(32, 3, 51)
+    sched = [(0.004, 4, 0)]
+    return mu, nu, sched, odd.run_schedule(mu, nu, 4, 1, sched, odd.Params(err=1e-10))
+
+
+@pytest.mark.parametrize("threads", [64, 128, 256])
+def test_threads_per_cell(lib, ref32, threads):
+    mu, nu, sched, ref = ref32
+    g = lib.DD(mu, nu, 4, 1, sched, err_tol=1e-7, threads_per_cell=threads)
+    g.run_schedule()
+    rp, col, val = g.basic_marginals()
+    cost, _, _ = g.cost(with_y=False)
+    g.close()
+    got = _dense_rows(rp, col, val, 32 * 32)
+    assert _rel_l1(got, odd.rows_to_dense(ref.rows, 32 * 32)) < PLAN_TOL
+    assert abs(cost - ref.history[-1][3].cost) / ref.history[-1][3].cost < COST_TOL
+
+
+def test_duals_match_up_to_cell_constants(lib, ref32):
+    mu, nu, sched, ref = ref32
+    eps = sched[0][0]
+    g = lib.DD(mu, nu, 4, 1, sched, err_tol=1e-7)
+    g.run_schedule()
+    aA, aB = g.duals(0), g.duals(1)
+    g.close()
+    for part, a in (("A", aA), ("B", aB)):
+        for J in ref.prob.parts[part]:
+            X = ref.prob.cell_points(J)
+            d = a[X] - ref.alpha[part][X]
+            assert np.ptp(d) / eps < 1e-3
+
+
+def test_sampled_cells_full_size(lib):
+    # 1024² images, 4×4 cells: a feasible synthetic state, one A half-sweep at
+    # ε = 2h², compared on a sample of cells that the oracle solves one by one
+    n, b = 1024, 4
+    eps = 2.0 / n**2
+    mu, _ = syn.image_pair("gm1024_b4_l4", 0)
+    nu, rp, col, val = syn.feasible_state(mu, b, seed=7)
+    g = lib.DD(mu, nu, b, 1, [(eps, 1, 0)], err_tol=1e-6)
+    g.set_state(rp, col, val)
+    g.half_sweep(0, eps)
+    grp, gcol, gval = g.basic_marginals()
+    g.close()
+    prob = odd.GridProblem(mu / mu.sum(), nu / nu.sum(), b, 1.0 / n)
+    rows = odd.rows_from_csr(rp, col, val / nu.sum())
+    rng = np.random.default_rng(3)
+    cells = sorted(rng.choice(len(prob.parts["A"]), 48, replace=False).tolist())
+    cells += [0, len(prob.parts["A"]) - 1]
+    new_rows, _ = odd.half_sweep(prob, "A", rows, np.zeros(n * n), eps, odd.Params(err=1e-10), cells=cells)
+    num = den = 0.0
+    for jn in cells:
+        for i in prob.parts["A"][jn]:
+            c_ref, v_ref = new_rows[i]
+            c_gpu = gcol[grp[i]:grp[i + 1]]
+            v_gpu = gval[grp[i]:grp[i + 1]]
+            u = np.union1d(c_ref, c_gpu)
+            a = np.zeros(u.size); a[np.searchsorted(u, c_gpu)] = v_gpu
+            e = np.zeros(u.size); e[np.searchsorted(u, c_ref)] = v_ref
+            num += np.abs(a - e).sum()
+            den += e.sum()
+    assert num / den < PLAN_TOL, num / den
+
+
+def test_set_state_rejects_unsorted(lib):
+    n, b = 16, 4
+    mu = syn.gaussian_mixture(n, 2, 70)
+    nu, rp, col, val = syn.feasible_state(mu, b, seed=1, radius_px=2)
+    g = lib.DD(mu, nu, b, 1, [(0.01, 1, 0)])
+    bad = col.copy()
+    bad[rp[0]], bad[rp[0] + 1] = bad[rp[0] + 1], bad[rp[0]]
+    with pytest.raises(lib.DDError) as e:
+        g.set_state(rp, bad, val)
+    assert e.value.status == lib.DD_ERR_ARG
+    g.set_state(rp, col, val)           # the context is still usable
+    g.half_sweep(1, 0.01)
+    g.close()
