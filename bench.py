@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Throughput of the domain-decomposition half-sweep path on GB300.
+
+Metric: pixels·sweeps/s at the finest level of a coarse-to-fine run on
+1024×1024 Gaussian-mixture images (4×4 basic cells, layers 8²→1024², final
+ε = 2h²). One step = one sweep (half-sweep on partition A, then on B) over the
+whole image. The state (basic marginals, duals, workspace) stays resident in
+HBM between steps and is larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank solves its own image
+pair (pair index = rank): the problems are independent, so the scaling is weak
+and no collective touches the data path; only the timing uses a barrier and a
+max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pixels·sweeps/s at 1024², plain DD"
+UNIT = "px·sweeps/s"
+# ex2 units per SM per clock, measured on this GPU (see the design notes)
+EX2_PER_CLK_PER_SM = 32
+NUM_SM = 152
+SM_MAX_MHZ = 2070.0
+# DRAM bytes per launch of the cell-solve kernel from the last ncu capture of
+# the current kernel (profiles/k_sinkhorn_gm1024_b4.md); None if not captured
+SOLVE_TRAFFIC_BYTES = None
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    p.add_argument("--workload", default="gm1024_b4")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-cells", type=int, default=160)
+    p.add_argument("--err", type=float, default=1e-6)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+class OracleSample:
+    """The FP64 oracle on a bounded sample of the same workload: one half-sweep
+    over a set of A-cells of the finest level, started from a feasible
+    synthetic state with zero duals; the time per cell is extrapolated to whole
+    sweeps."""
+
+    def __init__(self, workload):
+        import numpy as np
+        from oracle import dd as odd
+        from paper_2001_10986_gb300 import synthetic as syn
+        self.np, self.odd = np, odd
+        w = syn.WORKLOADS[workload]
+        self.n, self.b = w.n, w.b
+        mu, _ = syn.image_pair(w, 0)
+        nu, rp, col, val = syn.feasible_state(mu, self.b, seed=7)
+        self.prob = odd.GridProblem(mu, nu, self.b, 1.0 / self.n)
+        self.rows = odd.rows_from_csr(rp, col, val)
+        self.eps = 2.0 / self.n ** 2
+        self.rng = np.random.default_rng(0)
+        self.cells_per_sweep = len(self.prob.parts["A"]) + len(self.prob.parts["B"])
+
+    def run(self, n_cells):
+        cells = self.rng.choice(len(self.prob.parts["A"]), n_cells, replace=False).tolist()
+        alpha = self.np.zeros(self.n * self.n)
+        t = time.perf_counter()
+        _, info = self.odd.half_sweep(self.prob, "A", self.rows, alpha, self.eps,
+                                      self.odd.Params(err=1e-6), cells=cells)
+        dt = time.perf_counter() - t
+        per_cell = dt / n_cells
+        return self.n * self.n / (per_cell * self.cells_per_sweep), per_cell, dt, float(self.np.mean(info.iters))
+
+
+def cpu_baseline(workload, n_cells):
+    s = OracleSample(workload)
+    v, per_cell, dt, iters = s.run(n_cells)
+    sample = (f"oracle (numpy FP64, 1 thread) on {n_cells} random A-cells of one half-sweep at "
+              f"{s.n}², eps=2h², from a feasible synthetic state with zero duals "
+              f"(mean {iters:.0f} Sinkhorn iterations per cell); {per_cell*1e3:.1f} ms per "
+              f"cell, extrapolated to {s.cells_per_sweep} cells per sweep; {dt:.1f} s of CPU work")
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2001_10986_gb300 import synthetic as syn
+    w = syn.WORKLOADS[args.workload]
+    s = OracleSample(args.workload)
+    vals = []
+    cells = 16
+    for k in range(args.warmup + args.steps):
+        v, _, _, _ = s.run(cells)
+        if k >= args.warmup:
+            vals.append(v)
+    v = statistics.median(vals)
+    ms = w.n * w.n / v * 1e3
+    cb = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+          "sample": f"each step: the FP64 oracle on {cells} random A-cells of a {w.n}² half-sweep "
+                    f"(feasible synthetic state, zero duals), extrapolated to a whole sweep"}
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "n": w.n, "b": w.b, "levels": w.levels,
+                      "eps_final": "2h^2"},
+           "impl": "reference", "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_cuda(args):
+    import numpy as np
+    import torch
+
+    from paper_2001_10986_gb300 import build as bld
+    if not os.path.exists(bld.LIB):
+        bld.build()
+    from paper_2001_10986_gb300 import dd, synthetic as syn
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        pg = tdist
+    w = syn.WORKLOADS[args.workload]
+    n, b, L = w.n, w.b, w.levels
+    mu, nu = syn.image_pair(w, rank)
+    sched = syn.paper_schedule(n, L, args.warmup)
+    stream = torch.cuda.current_stream()
+
+    # ---- setup (untimed): coarse levels, refinement, warm-up sweeps at 2h² ----
+    g = dd.DD(mu, nu, b, L, sched, err_tol=args.err, stream=stream, debug_flags=2)
+    g.run_schedule()
+    torch.cuda.synchronize()
+    g.reset_profile()
+    lvl, nl, _, eps, nnz0 = g.info()
+    assert nl == n, (nl, n)
+
+    # ---- timed region: K sweeps at the finest level ----
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            st = g.sweep(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms_total = e0.elapsed_time(e1)
+    prof = g.profile()
+    cost, ex, ey = g.cost()
+    g.close()
+    t_rank = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+    if pg:
+        pg.all_reduce(t_rank, op=pg.ReduceOp.MAX)
+    ms_max = float(t_rank.item())
+    value = world * n * n * args.steps / (ms_max * 1e-3)
+
+    # ---- roofline of the cell-solve kernel (exp evaluations) ----
+    solve_ms = prof.solve_ms / max(prof.solve_launches, 1)
+    evals = prof.kernel_evals / max(prof.solve_launches, 1)
+    achieved = evals / (solve_ms * 1e-3) / 1e9
+    peak = NUM_SM * EX2_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
+    roofline = {"bound": "alu", "kernel": "k_sinkhorn", "achieved": achieved, "peak": peak,
+                "unit": "Gexp/s", "frac": achieved / peak, "traffic": SOLVE_TRAFFIC_BYTES,
+                "peak_source": f"{NUM_SM} SMs x {EX2_PER_CLK_PER_SM} ex2/clk/SM x {SM_MAX_MHZ:.0f} MHz",
+                "evals_per_launch": evals, "ms_per_launch": solve_ms,
+                "solve_share": prof.solve_ms / ms_total if ms_total > 0 else None,
+                "gather_ms_per_launch": prof.gather_ms / max(prof.gather_launches, 1),
+                "mean_sinkhorn_iters": prof.sinkhorn_iters / max(prof.cells, 1)}
+
+    # ---- end to end through the C ABI from host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        sched_e2e = syn.paper_schedule(n, L, args.steps)
+        h = dd.DD(mu, nu, b, L, sched_e2e, err_tol=args.err, stream=stream)
+        h.run_schedule()
+        c2, ex2_, ey2 = h.cost()
+        rp, col, val = h.basic_marginals()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        h.close()
+        e2e = {"value": n * n * args.steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(2 * n * n * 8),
+               "d2h_bytes_per_step": int(rp.nbytes + col.nbytes + val.nbytes + 24),
+               "what": f"dd_create from host images + full schedule ({len(sched_e2e)} steps, "
+                       f"{args.steps} sweeps at {n}²) + dd_cost + basic marginals to host; "
+                       f"px·sweeps over the finest-level sweeps / wall time",
+               "seconds": dt}
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu and world == 1:
+        cpu = cpu_baseline(args.workload, args.cpu_cells)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": args.workload, "n": n, "b": b, "levels": L, "eps_final": eps,
+                      "err_tol": args.err, "nnz": nnz0, "l2": "working set larger than L2 (CSR + workspace)",
+                      "parallelism": f"replicas x{world} (independent image pairs)"},
+           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": int(prof.launches), "clocks": clk.summary(),
+           "quality": {"cost": cost, "err_x": ex, "err_y": ey, "max_iters_last": st.max_iters,
+                       "mean_iters_last": st.mean_iters, "cells_not_converged_last": st.cells_not_converged}}
+    print(json.dumps(out), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cuda(args)
+
+
+if __name__ == "__main__":
+    main()

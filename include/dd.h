@@ -75,8 +75,25 @@ typedef struct {
                             256); 0 = library choice. Default 0.               */
   void* stream;          /* cudaStream_t to run on; NULL = a stream owned by
                             the context.                                       */
-  uint64_t debug_flags;  /* bit 0: synchronise and check after every kernel  */
+  uint64_t debug_flags;  /* bit 0: synchronise and check after every kernel;
+                            bit 1: time the gather and cell-solve kernels with
+                            CUDA events (see dd_get_profile)                   */
 } dd_options;
+
+/* Counters of the work done by a context since creation or the last
+ * dd_reset_profile. Kernel times are filled only with debug_flags bit 1. */
+typedef struct {
+  int64_t launches;          /* CUDA kernels launched by the context            */
+  int64_t half_sweeps;       /* half-sweeps run                                 */
+  int64_t solve_launches;    /* launches of the cell-solve kernel               */
+  double solve_ms;           /* their summed duration (CUDA events)             */
+  int64_t gather_launches;   /* launches of the Y-marginal gather kernel        */
+  double gather_ms;          /* their summed duration (CUDA events)             */
+  double kernel_evals;       /* Σ over cell solves of |X_J|·N_y(J)·(iterations+1):
+                                kernel entries exp(…) evaluated                  */
+  double sinkhorn_iters;     /* Σ over cell solves of the Sinkhorn iterations   */
+  int64_t cells;             /* cell solves                                     */
+} dd_profile;
 
 /* Statistics of the last sweep run by dd_sweep / dd_run_schedule. */
 typedef struct {
@@ -164,6 +181,12 @@ dd_status dd_get_duals(dd_ctx* ctx, int32_t partition, double* alpha);
  * pointer may be NULL. */
 dd_status dd_get_info(dd_ctx* ctx, int32_t* level, int32_t* n_level, int32_t* n_basic,
                       double* eps, int64_t* nnz);
+
+/* Copy the context's counters to *out. */
+dd_status dd_get_profile(dd_ctx* ctx, dd_profile* out);
+
+/* Reset the context's counters to zero. */
+dd_status dd_reset_profile(dd_ctx* ctx);
 
 /* Free the context and all device memory it owns. NULL is allowed. */
 void dd_destroy(dd_ctx* ctx);

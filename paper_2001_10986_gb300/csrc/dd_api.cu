@@ -102,7 +102,10 @@ struct dd_ctx {
   int* h_err = nullptr;
   double* h_yerr = nullptr;
 
+  dd_profile prof{};
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   int last_part = -1;
+  bool need_init = false;  // level-0 product coupling not built yet
   double eps_cur = 0.0;
   SweepTotals last_tot{};
   int64_t sweeps_done = 0;
@@ -145,7 +148,7 @@ void grow(T*& p, int64_t& cap, int64_t need) {
 // col/val buffer k holds at least `need` entries (contents are not kept)
 void state_reserve(dd_ctx* c, int k, int64_t need) {
   if (c->cap[k] >= need && c->col[k] && c->val[k]) return;
-  const int64_t cap = std::max<int64_t>(need + need / 2, 1024);
+  const int64_t cap = std::max<int64_t>(need + need / 4, 1024);
   dev_alloc(c->col[k], (size_t)cap);
   dev_alloc(c->val[k], (size_t)cap);
   c->cap[k] = cap;
@@ -240,6 +243,8 @@ void corner_anchors(dd_ctx* c, int l, int part, int2* dst) {
   DD_CUDA(cudaStreamSynchronize(c->stream));
 }
 
+void ensure_state(dd_ctx* c);
+
 void ensure_sweep_capacity(dd_ctx* c, int64_t nnz_in) {
   if (nnz_in > c->ws_cap) {
     int64_t need = nnz_in + nnz_in / 2 + 1024;
@@ -305,25 +310,37 @@ int threads_per_cell(dd_ctx* c) {
 void half_sweep(dd_ctx* c, int part, double eps) {
   const LevelHost& h = c->lh[c->lev];
   const int nrows = h.nb * h.nb;
+  ensure_state(c);
   ensure_sweep_capacity(c, c->nnz);
   const int other = 1 - c->cur;
-  state_reserve(c, other, 4 * c->nnz);
   DD_CUDA(cudaMemsetAsync(c->ws_counter, 0, sizeof(unsigned long long), c->stream));
   DD_CUDA(cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream));
   SweepArgs a = sweep_args(c, part, eps);
+  const bool timing = (c->opt.debug_flags & 2) != 0;
+  if (timing) DD_CUDA(cudaEventRecord(c->ev[0], c->stream));
   DD_CUDA(launch_gather(a, c->stream));
   check_debug(c, "gather");
+  if (timing) DD_CUDA(cudaEventRecord(c->ev[1], c->stream));
   DD_CUDA(launch_sinkhorn(a, threads_per_cell(c), c->stream));
   check_debug(c, "sinkhorn");
+  if (timing) DD_CUDA(cudaEventRecord(c->ev[2], c->stream));
   DD_CUDA(launch_row_scan(c->row_cnt, c->rp[other], c->tile, nrows, c->stream));
-  DD_CUDA(launch_compact(c->row_cnt, c->row_src, c->tile, c->rp[other], c->tmp_col, c->tmp_val,
-                         c->col[other], c->val[other], c->cap[other], nrows, c->err_flag, c->stream));
-  check_debug(c, "compact");
   DD_CUDA(launch_reduce_cells(a, c->totals, c->stream));
+  c->prof.launches += 5;
   DD_CUDA(cudaMemcpyAsync(c->h_tot, c->totals, sizeof(SweepTotals), cudaMemcpyDeviceToHost, c->stream));
   DD_CUDA(cudaMemcpyAsync(c->h_nnz, c->rp[other] + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
   DD_CUDA(cudaMemcpyAsync(c->h_err, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   DD_CUDA(cudaStreamSynchronize(c->stream));
+  if ((*c->h_err & 4) == 0) {
+    // output sized exactly from the scan total
+    state_reserve(c, other, *c->h_nnz);
+    DD_CUDA(launch_compact(c->row_cnt, c->row_src, c->tile, c->rp[other], c->tmp_col, c->tmp_val,
+                           c->col[other], c->val[other], c->cap[other], nrows, c->err_flag, c->stream));
+    c->prof.launches += 1;
+    check_debug(c, "compact");
+    DD_CUDA(cudaMemcpyAsync(c->h_err, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+  }
   if (*c->h_err & 2 || c->h_tot->nonfinite)
     throw DdError{DD_ERR_NUMERIC, "a cell solve produced a non-finite value"};
   if (*c->h_err & (4 | 8))
@@ -333,10 +350,24 @@ void half_sweep(dd_ctx* c, int part, double eps) {
   c->last_part = part;
   c->eps_cur = eps;
   c->last_tot = *c->h_tot;
+  c->prof.half_sweeps += 1;
+  c->prof.solve_launches += 1;
+  c->prof.gather_launches += 1;
+  c->prof.kernel_evals += c->last_tot.kernel_evals;
+  c->prof.sinkhorn_iters += (double)c->last_tot.iters_sum;
+  c->prof.cells += a.ncells;
+  if (timing) {
+    float g_ms = 0.f, s_ms = 0.f;
+    DD_CUDA(cudaEventElapsedTime(&g_ms, c->ev[0], c->ev[1]));
+    DD_CUDA(cudaEventElapsedTime(&s_ms, c->ev[1], c->ev[2]));
+    c->prof.gather_ms += g_ms;
+    c->prof.solve_ms += s_ms;
+  }
 }
 
 // move the state one level finer (§6.4)
 void refine(dd_ctx* c) {
+  ensure_state(c);
   const int lc = c->lev, lf = lc + 1;
   const LevelHost& hc = c->lh[lc];
   const LevelHost& hf = c->lh[lf];
@@ -405,6 +436,7 @@ void refine(dd_ctx* c) {
   check_debug(c, "refine_write");
   DD_CUDA(launch_refine_duals(C, F, cpart, alpha_c, anchor_c, 0, a0, n0, c->stream));
   DD_CUDA(launch_refine_duals(C, F, cpart, alpha_c, anchor_c, 1, a1, n1, c->stream));
+  c->prof.launches += 7;
   check_debug(c, "refine_duals");
   DD_CUDA(cudaStreamSynchronize(c->stream));
   dev_free(rp_c);
@@ -442,16 +474,34 @@ void enter_level0(dd_ctx* c) {
   DD_CUDA(cudaMemsetAsync(a1, 0, n2 * 4, c->stream));
   corner_anchors(c, 0, 0, n0);
   corner_anchors(c, 0, 1, n1);
-  // product coupling ν_i = ‖μ_i‖·ν (dense rows)
-  const int64_t nnz = (int64_t)h.nb * h.nb * (int64_t)n2;
+  c->cur = 0;
+  c->nnz = 0;
+  c->need_init = true;  // the product coupling is built on first use
+}
+
+// the level-0 product coupling ν_i = ‖μ_i‖·ν (dense rows, §6.4), built on
+// first use so that dd_set_state can replace it without paying for it
+constexpr int64_t kMaxProductEntries = (int64_t)1 << 31;
+
+void ensure_state(dd_ctx* c) {
+  if (!c->need_init) return;
+  if (c->lev != 0) throw DdError{DD_ERR_STATE, "no state at this level"};
+  const LevelHost& h = c->lh[0];
+  const int64_t n2 = (int64_t)h.n * h.n;
+  const int64_t nnz = (int64_t)h.nb * h.nb * n2;
+  if (nnz > kMaxProductEntries)
+    throw DdError{DD_ERR_ARG, "the product coupling at level 0 has " + std::to_string(nnz) +
+                                  " entries; use more levels (a coarser level 0) or dd_set_state"};
   state_reserve(c, 0, nnz);
   int imax = 0;
   for (int i = 1; i < h.nb * h.nb; ++i)
     if (h.M_q[i] > h.M_q[imax]) imax = i;
   DD_CUDA(launch_init_product(view(c), c->rp[0], c->col[0], c->val[0], imax, c->stream));
+  c->prof.launches += 1;
   DD_CUDA(cudaStreamSynchronize(c->stream));
   c->cur = 0;
   c->nnz = nnz;
+  c->need_init = false;
 }
 
 void build_levels(dd_ctx* c, const double* mu, const double* nu) {
@@ -530,6 +580,8 @@ void release(dd_ctx* c) {
   if (c->h_nnz) cudaFreeHost(c->h_nnz);
   if (c->h_err) cudaFreeHost(c->h_err);
   if (c->h_yerr) cudaFreeHost(c->h_yerr);
+  for (int k = 0; k < 3; ++k)
+    if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -671,6 +723,7 @@ dd_status dd_create(const double* mu, const double* nu, const dd_grid* grid, int
     DD_CUDA(cudaMallocHost((void**)&c->h_nnz, sizeof(int64_t)));
     DD_CUDA(cudaMallocHost((void**)&c->h_err, sizeof(int)));
     DD_CUDA(cudaMallocHost((void**)&c->h_yerr, sizeof(double)));
+    for (int k = 0; k < 3; ++k) DD_CUDA(cudaEventCreate(&c->ev[k]));
     build_levels(c, mu, nu);
     enter_level0(c);
     c->eps_cur = c->sched[0].eps;
@@ -746,6 +799,7 @@ dd_status dd_set_state(dd_ctx* c, const int64_t* row_ptr, const int32_t* col, co
     }
     c->nnz = nnz;
     c->last_part = -1;
+    c->need_init = false;
   });
 }
 
@@ -787,9 +841,11 @@ dd_status dd_cost(dd_ctx* c, double* cost, double* err_x, double* err_y) {
     if (cost) *cost = c->last_part < 0 ? NAN : c->last_tot.cost;
     if (err_x) *err_x = c->last_part < 0 ? NAN : c->last_tot.errx;
     if (err_y) {
+      ensure_state(c);
       const LevelHost& h = c->lh[c->lev];
       DD_CUDA(launch_y_error(view(c), c->rp[c->cur], c->col[c->cur], c->val[c->cur], h.nb * h.nb, c->ydense,
                              c->yerr, c->stream));
+      c->prof.launches += 2;
       DD_CUDA(cudaMemcpyAsync(c->h_yerr, c->yerr, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       DD_CUDA(cudaStreamSynchronize(c->stream));
       *err_y = *c->h_yerr;
@@ -801,6 +857,7 @@ dd_status dd_get_basic_marginals(dd_ctx* c, int64_t* nnz, int64_t* row_ptr, int3
                                  int64_t cap) {
   return guarded(c, [&] {
     if (!nnz) throw DdError{DD_ERR_ARG, "nnz is NULL"};
+    ensure_state(c);
     const LevelHost& h = c->lh[c->lev];
     const int nrows = h.nb * h.nb;
     *nnz = c->nnz;
@@ -905,6 +962,17 @@ dd_status dd_get_info(dd_ctx* c, int32_t* level, int32_t* n_level, int32_t* n_ba
     if (eps) *eps = c->eps_cur;
     if (nnz) *nnz = c->nnz;
   });
+}
+
+dd_status dd_get_profile(dd_ctx* c, dd_profile* out) {
+  return guarded(c, [&] {
+    if (!out) throw DdError{DD_ERR_ARG, "out is NULL"};
+    *out = c->prof;
+  });
+}
+
+dd_status dd_reset_profile(dd_ctx* c) {
+  return guarded(c, [&] { c->prof = dd_profile{}; });
 }
 
 void dd_destroy(dd_ctx* c) {

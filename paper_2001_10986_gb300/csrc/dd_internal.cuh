@@ -131,6 +131,7 @@ cudaError_t launch_init_product(LevelView L, int64_t* rp, int32_t* col, uint64_t
 
 struct SweepTotals {
   double cost, errx;
+  double kernel_evals;       // Σ_J |X_J|·N_y·(iterations + 1)
   long long iters_sum;
   int iters_max, not_converged, nonfinite, overflow;
 };

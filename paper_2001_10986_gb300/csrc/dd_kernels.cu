@@ -220,21 +220,29 @@ __global__ void __launch_bounds__(256) k_gather(SweepArgs a) {
 // ---------------------------------------------------------------------------
 // S2-S5: cell Sinkhorn + extraction + BalanceMeasures + Truncate
 // ---------------------------------------------------------------------------
-// Thread layout: every y of the cell support is handled by a group of G
-// consecutive threads; thread g of the group owns RPT = 32/W pixel rows
-// (32 pixels) of the H×W cell. Potentials in log2 units:
-//   F(ξ) = f̃(ξ)/(ε ln 2),  G(η) = g̃(η)/(ε ln 2),  κ = Δ²/(ε ln 2),
-//   π(x,y) = 2^(F(ξ) + G(η) − κ|ξ−η|²).
-// A Y-iteration with stabiliser Gs(y) computes p = 2^(F + Gs − κc̃),
-// s(y) = Σ_x p, G(y) = Gs + log2 ν(y) − log2 s, and the X-marginal of the new
-// plan as Σ_y p·ν(y)/s(y). The previous G is the stabiliser, so p is a plan
-// entry of the previous iterate and s(y) stays near ν(y): no running maximum
-// is needed after the first iteration, which takes Gs = −max_x(F − κc̃).
+// Stabilised Sinkhorn with absorption (the log-domain stabilisation that the
+// paper takes from its reference implementation, §7.3 "Numerical
+// stability"): the plan of a cell is
+//     π(x,y) = u(x) · K̃(x,y) · v(y),   K̃(x,y) = 2^(F(ξ) + Gs(η) − κ|ξ−η|²),
+// with log2-unit stabilisers F (per pixel, from the stored dual α̃) and Gs
+// (per support point), κ = Δ²/(ε ln 2), and scalings u, v near 1.
+//   Y-iteration: s(y) = Σ_x K̃ u, v(y) = ν(y)/s(y);
+//   X-marginal:  P_X π(x) = u(x) Σ_y K̃ v;   X-iteration: u ← u·μ/P_X π.
+// The stabilisers stay fixed while |log2 u|, |log2 v| ≤ kTau, so K̃ is
+// recomputed bit-identically in every pass and the scalings converge to FP32
+// precision; a scaling that leaves that band is absorbed into its stabiliser.
+// The first pass of a solve sets Gs = −max_x(F − κc̃) and absorbs v.
+//
+// Thread layout: each support point y is handled by a group of G consecutive
+// threads; thread g of the group owns RPT = 16/W pixel rows (16 pixels) of
+// the H×W cell.
 
 constexpr int kMaxHW = 256;
+constexpr float kTau = 16.0f;
 
 struct SinkSmem {
   float F[kMaxHW];
+  float u[kMaxHW];
   float l2mu[kMaxHW];
   float mu[kMaxHW];
   float PX[kMaxHW];
@@ -245,16 +253,10 @@ struct SinkSmem {
   double dws[32];
   float s_err;
   int s_stop;
-  int s_flag;
   uint64_t q64[4];
   uint64_t w64[4];
-  int nsur, ndef, last_def;
+  int nsur, ndef;
   int sur[4], def[4];
-};
-
-template <int W, int G>
-struct SinkCfg {
-  static constexpr int RPT = 32 / W;
 };
 
 template <int G>
@@ -270,29 +272,36 @@ __device__ __forceinline__ float group_max(float v) {
   return v;
 }
 
-// Sum v[0..31] over the lanes of a warp that share lane%G; afterwards lane
-// holds G fully reduced values for chunk-local x = base + j.
+// Sum v[0..15] over the lanes of a warp that share lane % G. Afterwards the
+// lane holds max(1, G/2) fully reduced values for chunk-local pixels
+// base + j; with G == 1 two lanes hold each value and only even lanes write.
 template <int G>
-__device__ __forceinline__ int warp_reduce_scatter(float (&v)[32], int lane) {
+__device__ __forceinline__ int warp_reduce_scatter16(float (&v)[16], int lane) {
   int base = 0;
 #pragma unroll
-  for (int m = 16, cnt = 32; m >= G; m >>= 1, cnt >>= 1) {
-    const int half = cnt >> 1;
-    const bool up = (lane & m) != 0;
+  for (int m = 16, cnt = 16; m >= G; m >>= 1) {
+    if (cnt > 1) {
+      const int half = cnt >> 1;
+      const bool up = (lane & m) != 0;
 #pragma unroll
-    for (int j = 0; j < half; ++j) {
-      float send = up ? v[j] : v[j + half];
-      float keep = up ? v[j + half] : v[j];
-      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+      for (int j = 0; j < half; ++j) {
+        const float send = up ? v[j] : v[j + half];
+        const float keep = up ? v[j + half] : v[j];
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+      }
+      if (up) base += half;
+      cnt = half;
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], m);
     }
-    if (up) base += half;
   }
   return base;
 }
 
 template <int W, int G>
 __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g, SinkSmem& sm) {
-  constexpr int RPT = 32 / W;
+  constexpr int RPT = 16 / W;
+  constexpr int NV = G >= 2 ? G / 2 : 1;
   const LevelView& L = a.L;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int NT = blockDim.x;
@@ -313,49 +322,52 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   const int Dr = g.r0 - anc.x, Dc = g.c0 - anc.y;
   const int shr = anc.x - anc_old.x, shc = anc.y - anc_old.y;
 
-  // potentials of the cell in the new frame
+  // stabiliser F in the new frame, scalings u = 1
   for (int x = tid; x < HW; x += NT) {
     const int ar = x / g.W, ac = x - (x / g.W) * g.W;
     const int p = (g.r0 + ar) * L.n + g.c0 + ac;
     const float l2 = L.log2mu[p];
-    float at = a.alpha[p] + 2.0f * d2 * (float)(shr * ar + shc * ac);
+    const float at = a.alpha[p] + 2.0f * d2 * (float)(shr * ar + shc * ac);
     sm.F[x] = at * inv_eln2 + l2;
+    sm.u[x] = 1.0f;
     sm.l2mu[x] = l2;
     sm.mu[x] = L.mu_f[p];
   }
-  float tol_part = 0.f, nu_part = 0.f;
-  for (int x = tid; x < HW; x += NT) tol_part += sm.mu[x];
+  float mu_part = 0.f, nu_part = 0.f;
+  for (int x = tid; x < HW; x += NT) mu_part += L.mu_f[(g.r0 + x / g.W) * L.n + g.c0 + x % g.W];
   for (int k = tid; k < ny; k += NT) nu_part += (float)a.ws_nu[off + k] * kFixToFloat;
-  __syncthreads();
-  const float muJ = block_sum(tol_part, sm.fws);
+  const float muJ = block_sum(mu_part, sm.fws);
   const float nuJ = block_sum(nu_part, sm.fws);
   const float tol = a.err_tol * muJ;
-  // truncated mass leaves ‖ν_cell‖ ≤ ‖μ_J‖: the stopping test compares P_X π
-  // with μ rescaled to ‖ν_cell‖ (the §6.2 rule when nothing was truncated)
+  // Truncate leaves ‖ν_cell‖ ≤ ‖μ_J‖: the stopping test compares P_X π with μ
+  // rescaled to ‖ν_cell‖ (the §6.2 rule when nothing was truncated)
   const float mscale = muJ > 0.f ? nuJ / muJ : 1.f;
 
-  float Fr[RPT][W];
+  float Fr[16], ur[16];
   int arow[RPT];
-  auto load_F = [&]() {
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      arow[r] = gid * RPT + r;
+  for (int r = 0; r < RPT; ++r) arow[r] = gid * RPT + r;
+  auto load_Fu = [&]() {
 #pragma unroll
-      for (int c = 0; c < W; ++c)
-        Fr[r][c] = (arow[r] < g.H && c < g.W) ? sm.F[arow[r] * g.W + c] : kNegBig;
-    }
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        const bool ok = arow[r] < g.H;
+        Fr[r * W + c] = ok ? sm.F[arow[r] * W + c] : kNegBig;
+        ur[r * W + c] = ok ? sm.u[arow[r] * W + c] : 0.f;
+      }
   };
-  load_F();
+  load_Fu();
 
-  float acc[32];
-  float pv[32];
+  float acc[16];
+  float pv[16];
   int it = 0;
   float errx = 0.f;
   bool converged = false, bad = false;
   for (;;) {
-    // ---- Y-iteration + X-marginal of the new plan ----
+    // ---- Y-iteration and X-marginal of the new plan ----
 #pragma unroll
-    for (int k = 0; k < 32; ++k) acc[k] = 0.f;
+    for (int q = 0; q < 16; ++q) acc[q] = 0.f;
     for (int k0 = 0; k0 < ny; k0 += YS) {
       const int k = k0 + slot;
       const bool valid = k < ny;
@@ -363,27 +375,26 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
       const int32_t e = a.ws_eta[off + kk];
       const int er = eta_r(e), ec = eta_c(e);
       const float lognu = a.ws_lognu[off + kk];
-      float Cc[W];
+      float Cc[W], Rq[RPT];
 #pragma unroll
       for (int c = 0; c < W; ++c) {
-        float t = (float)(c - ec);
+        const float t = (float)(c - ec);
         Cc[c] = kappa * t * t;
       }
-      float Rq[RPT];
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
-        float t = (float)(arow[r] - er);
+        const float t = (float)(arow[r] - er);
         Rq[r] = kappa * t * t;
       }
       float Gs;
+      bool absorb = (it == 0);
       if (it == 0) {
         float m = kNegBig;
 #pragma unroll
         for (int r = 0; r < RPT; ++r)
 #pragma unroll
-          for (int c = 0; c < W; ++c) m = fmaxf(m, Fr[r][c] - Rq[r] - Cc[c]);
-        m = group_max<G>(m);
-        Gs = -m;
+          for (int c = 0; c < W; ++c) m = fmaxf(m, Fr[r * W + c] - Rq[r] - Cc[c]);
+        Gs = -group_max<G>(m);
       } else {
         Gs = a.ws_g[off + kk];
       }
@@ -393,59 +404,62 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
         const float Ra = Gs - Rq[r];
 #pragma unroll
         for (int c = 0; c < W; ++c) {
-          float p = ex2(Fr[r][c] + Ra - Cc[c]);
+          const float p = ex2(Fr[r * W + c] + Ra - Cc[c]);
           pv[r * W + c] = p;
-          s += p;
+          s = fmaf(p, ur[r * W + c], s);
         }
       }
       s = group_sum<G>(s);
       if (!(s > 1e-30f && s < 1e30f)) {
-        // stabiliser too far off: restart this y from the running maximum
+        // stabiliser too far off for this y: restart it from the running maximum
         float m = kNegBig;
 #pragma unroll
         for (int r = 0; r < RPT; ++r)
 #pragma unroll
-          for (int c = 0; c < W; ++c) m = fmaxf(m, Fr[r][c] - Rq[r] - Cc[c]);
-        m = group_max<G>(m);
-        Gs = -m;
+          for (int c = 0; c < W; ++c)
+            m = fmaxf(m, Fr[r * W + c] + (ur[r * W + c] > 0.f ? lg2(ur[r * W + c]) : kNegBig) - Rq[r] - Cc[c]);
+        Gs = -group_max<G>(m);
         s = 0.f;
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
           const float Ra = Gs - Rq[r];
 #pragma unroll
           for (int c = 0; c < W; ++c) {
-            float p = ex2(Fr[r][c] + Ra - Cc[c]);
+            const float p = ex2(Fr[r * W + c] + Ra - Cc[c]);
             pv[r * W + c] = p;
-            s += p;
+            s = fmaf(p, ur[r * W + c], s);
           }
         }
         s = group_sum<G>(s);
+        absorb = true;
       }
-      const float ls = lg2(s);
-      const float rY = valid ? ex2(lognu - ls) : 0.f;
-      if (valid && gid == 0) a.ws_g[off + k] = Gs + lognu - ls;
+      const float lv = lognu - lg2(s);
+      const float v = valid ? ex2(lv) : 0.f;
+      if (valid && gid == 0 && (absorb || fabsf(lv) > kTau)) a.ws_g[off + k] = Gs + lv;
 #pragma unroll
-      for (int q = 0; q < 32; ++q) acc[q] = fmaf(rY, pv[q], acc[q]);
+      for (int q = 0; q < 16; ++q) acc[q] = fmaf(v, pv[q], acc[q]);
     }
-    // ---- reduce the X-marginal over y ----
+    // ---- reduce Σ_y K̃ v over the support ----
     {
-      const int base = warp_reduce_scatter<G>(acc, lane);
+      const int base = warp_reduce_scatter16<G>(acc, lane);
+      if (G > 1 || (lane & 1) == 0) {
 #pragma unroll
-      for (int j = 0; j < G; ++j) sm.red[warp][gid * 32 + base + j] = acc[j];
+        for (int j = 0; j < NV; ++j) sm.red[warp][gid * 16 + base + j] = acc[j];
+      }
     }
     __syncthreads();
-    float ep = 0.f, er = 0.f;
+    float ep = 0.f, erp = 0.f;
     const int nw = NT >> 5;
     for (int x = tid; x < HW; x += NT) {
-      // chunk gid owns rows [gid·RPT, (gid+1)·RPT) = chunk-local x of W·RPT = 32
-      float px = 0.f;
-      for (int w = 0; w < nw; ++w) px += sm.red[w][x];
+      float t = 0.f;
+      for (int w = 0; w < nw; ++w) t += sm.red[w][x];
+      const float px = sm.u[x] * t;
       sm.PX[x] = px;
       ep += fabsf(px - sm.mu[x] * mscale);
-      er += fabsf(px - sm.mu[x]);
+      erp += fabsf(px - sm.mu[x]);
     }
     ep = block_sum(ep, sm.fws);
-    er = block_sum(er, sm.fws);
+    erp = block_sum(erp, sm.fws);
     ++it;
     if (tid == 0) {
       int stop = 0;
@@ -453,7 +467,7 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
       else if (ep <= tol) stop = 1;
       else if (it >= a.max_iter) stop = 3;
       sm.s_stop = stop;
-      sm.s_err = er;
+      sm.s_err = erp;
     }
     __syncthreads();
     const int stop = sm.s_stop;
@@ -463,13 +477,21 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
       bad = stop == 2;
       break;
     }
-    // ---- X-iteration: F ← F + log2 μ − log2 P_X π ----
+    // ---- X-iteration u ← u·μ/P_X π, absorbing large scalings into F ----
     for (int x = tid; x < HW; x += NT) {
       const float px = sm.PX[x];
       if (px > 1e-37f && px < 1e37f) {
-        sm.F[x] += sm.l2mu[x] - lg2(px);
+        const float un = sm.u[x] * (sm.mu[x] / px);
+        const float lu = lg2(un);
+        if (fabsf(lu) > kTau) {
+          sm.F[x] += lu;
+          sm.u[x] = 1.0f;
+        } else {
+          sm.u[x] = un;
+        }
       } else {
-        // full log-sum-exp over the support for this x
+        // no mass reached this x: full log-sum-exp over the support with the
+        // current stabilisers
         const int ar = x / g.W, ac = x - (x / g.W) * g.W;
         float m = kNegBig;
         for (int k = 0; k < ny; ++k) {
@@ -484,13 +506,14 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
           s += ex2(a.ws_g[off + k] - kappa * (tr * tr + tc * tc) - m);
         }
         sm.F[x] = sm.l2mu[x] - (m + lg2(s));
+        sm.u[x] = 1.0f;
       }
     }
     __syncthreads();
-    load_F();
+    load_Fu();
   }
 
-  // ---- epilogue: final plan → fractions per basic cell, cost ----
+  // ---- epilogue: final plan → fractions per basic cell, transport cost ----
   const int nbas = g.nbr * g.nbc;
   const int bsh = __ffs(L.b) - 1;  // b is a power of two
   const int64_t tbase = 4 * off;
@@ -505,10 +528,10 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     float Cc[W], Dcc[W];
 #pragma unroll
     for (int c = 0; c < W; ++c) {
-      float t = (float)(c - ec);
+      const float t = (float)(c - ec);
       Cc[c] = kappa * t * t;
-      float u = (float)(Dc + c - ec);
-      Dcc[c] = u * u;
+      const float w = (float)(Dc + c - ec);
+      Dcc[c] = w * w;
     }
     float q[4] = {0.f, 0.f, 0.f, 0.f};
     float cst = 0.f, s = 0.f;
@@ -516,46 +539,43 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     for (int r = 0; r < RPT; ++r) {
       const float tr = (float)(arow[r] - er);
       const float Ra = Gs - kappa * tr * tr;
-      const float ur = (float)(Dr + arow[r] - er);
-      const float Drr = ur * ur;
+      const float wr = (float)(Dr + arow[r] - er);
+      const float Drr = wr * wr;
       const int kb_r = (arow[r] >> bsh) * g.nbc;
-      float rs = 0.f;
 #pragma unroll
       for (int c = 0; c < W; ++c) {
-        float p = ex2(Fr[r][c] + Ra - Cc[c]);
-        rs += p;
+        const float p = ex2(Fr[r * W + c] + Ra - Cc[c]) * ur[r * W + c];
+        s += p;
         cst = fmaf(p, Drr + Dcc[c], cst);
-        int kb = kb_r + (c >> bsh);
-        if (arow[r] < g.H && c < g.W) {
-          // kb < 4 for valid pixels
+        if (arow[r] < g.H) {
+          const int kb = kb_r + (c >> bsh);
           if (kb == 0) q[0] += p; else if (kb == 1) q[1] += p; else if (kb == 2) q[2] += p; else q[3] += p;
         }
       }
-      s += rs;
     }
     s = group_sum<G>(s);
     cst = group_sum<G>(cst);
 #pragma unroll
     for (int i = 0; i < 4; ++i) q[i] = group_sum<G>(q[i]);
     if (valid && gid == 0) {
-      const uint64_t nuJ = a.ws_nu[off + k];
+      const uint64_t nuq = a.ws_nu[off + k];
       const float S = q[0] + q[1] + q[2] + q[3];
       int imax = 0;
       for (int i = 1; i < nbas; ++i)
         if (q[i] > q[imax]) imax = i;
-      uint64_t rest = nuJ;
+      uint64_t rest = nuq;
       const int y = (anc.x + er) * L.n + (anc.y + ec);
       const float invS = S > 0.f ? 1.0f / S : 0.f;
       for (int i = 0; i < nbas; ++i) {
         if (i == imax) continue;
-        const uint64_t v = __umul64hi(nuJ, frac_to_u64(q[i] * invS));
-        rest -= v;
-        a.tmp_val[tbase + (int64_t)i * ny + k] = v;
+        const uint64_t vq = __umul64hi(nuq, frac_to_u64(q[i] * invS));
+        rest -= vq;
+        a.tmp_val[tbase + (int64_t)i * ny + k] = vq;
         a.tmp_col[tbase + (int64_t)i * ny + k] = y;
       }
       a.tmp_val[tbase + (int64_t)imax * ny + k] = rest;
       a.tmp_col[tbase + (int64_t)imax * ny + k] = y;
-      const double nuf = (double)nuJ * (1.0 / kFixOne);
+      const double nuf = (double)nuq * (1.0 / kFixOne);
       if (s > 0.f) cost_acc += (double)cst * (nuf / (double)s);
     }
   }
@@ -596,9 +616,9 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
       uint64_t T = 0;
       for (int j = 0; j < sm.nsur; ++j) {
         const int64_t idx = tbase + (int64_t)sm.sur[j] * ny + k;
-        const uint64_t v = a.tmp_val[idx];
-        const uint64_t t = __umul64hi(v, sm.q64[j]);
-        a.tmp_val[idx] = v - t;
+        const uint64_t vq = a.tmp_val[idx];
+        const uint64_t t = __umul64hi(vq, sm.q64[j]);
+        a.tmp_val[idx] = vq - t;
         T += t;
       }
       uint64_t rem = T;
@@ -619,18 +639,18 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     int carry = 0;
     for (int k0 = 0; k0 < ny; k0 += NT) {
       const int k = k0 + tid;
-      uint64_t v = 0;
+      uint64_t vq = 0;
       int y = 0;
       int keep = 0;
       if (k < ny) {
-        v = a.tmp_val[rb + k];
+        vq = a.tmp_val[rb + k];
         y = a.tmp_col[rb + k];
-        keep = v > a.trunc_q;
+        keep = vq > a.trunc_q;
       }
       int tot;
       const int pos = block_exscan(keep, sm.iws, tot);  // contains the barrier
       if (keep) {
-        a.tmp_val[rb + carry + pos] = v;
+        a.tmp_val[rb + carry + pos] = vq;
         a.tmp_col[rb + carry + pos] = y;
       }
       carry += tot;
@@ -648,11 +668,9 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   for (int x = tid; x < HW; x += NT) {
     const int ar = x / g.W, ac = x - (x / g.W) * g.W;
     const int p = (g.r0 + ar) * L.n + g.c0 + ac;
-    a.alpha[p] = (sm.F[x] - sm.l2mu[x]) * eln2;
+    a.alpha[p] = (sm.F[x] + lg2(sm.u[x]) - sm.l2mu[x]) * eln2;
   }
-  // costs: Δ²·Σ over leaders
-  double cs = cost_acc;
-  cs = block_sum<double>(cs, sm.dws);
+  double cs = block_sum<double>(cost_acc, sm.dws);
   if (tid == 0) {
     a.anchor[J] = anc;
     a.cell_cost[J] = cs * (double)L.spacing * (double)L.spacing;
@@ -663,7 +681,8 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   }
 }
 
-// one launch per (W, G) class is avoided by dispatching inside one kernel
+// one kernel for all cell shapes of a partition; the shape picks the
+// instantiation (A cells share one shape, B has corner/edge shapes)
 __global__ void __launch_bounds__(256) k_sinkhorn(SweepArgs a) {
   __shared__ SinkSmem sm;
   const int J = blockIdx.x;
@@ -671,14 +690,16 @@ __global__ void __launch_bounds__(256) k_sinkhorn(SweepArgs a) {
   const CellGeom g = cell_geom(a.part, J, a.L.nb, a.L.b);
   const int W = g.W, H = g.H;
   if (W == 2) sinkhorn_cell<2, 1>(a, J, g, sm);
-  else if (W == 4) sinkhorn_cell<4, 1>(a, J, g, sm);
-  else if (W == 8) {
-    if (H <= 4) sinkhorn_cell<8, 1>(a, J, g, sm);
-    else if (H <= 8) sinkhorn_cell<8, 2>(a, J, g, sm);
-    else sinkhorn_cell<8, 4>(a, J, g, sm);
+  else if (W == 4) {
+    if (H <= 4) sinkhorn_cell<4, 1>(a, J, g, sm);
+    else sinkhorn_cell<4, 2>(a, J, g, sm);
+  } else if (W == 8) {
+    if (H <= 4) sinkhorn_cell<8, 2>(a, J, g, sm);
+    else if (H <= 8) sinkhorn_cell<8, 4>(a, J, g, sm);
+    else sinkhorn_cell<8, 8>(a, J, g, sm);
   } else {
-    if (H <= 8) sinkhorn_cell<16, 4>(a, J, g, sm);
-    else sinkhorn_cell<16, 8>(a, J, g, sm);
+    if (H <= 8) sinkhorn_cell<16, 8>(a, J, g, sm);
+    else sinkhorn_cell<16, 16>(a, J, g, sm);
   }
 }
 
@@ -773,12 +794,14 @@ __global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals*
   __shared__ double dws[32];
   __shared__ long long lws[32];
   __shared__ int iws[32];
-  double c = 0.0, e = 0.0;
+  double c = 0.0, e = 0.0, ev = 0.0;
   long long its = 0;
   int mx = 0, nc = 0, nf = 0, ov = 0;
   for (int J = threadIdx.x; J < a.ncells; J += blockDim.x) {
     const int st = a.cell_status[J];
     if (st & 4) { ++ov; continue; }
+    const CellGeom g = cell_geom(a.part, J, a.L.nb, a.L.b);
+    ev += (double)(g.H * g.W) * (double)a.cell_ny[J] * (double)(a.cell_iters[J] + 1);
     c += a.cell_cost[J];
     e += a.cell_errx[J];
     its += a.cell_iters[J];
@@ -788,6 +811,7 @@ __global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals*
   }
   c = block_sum<double>(c, dws);
   e = block_sum<double>(e, dws);
+  ev = block_sum<double>(ev, dws);
   its = block_sum<long long>(its, lws);
   nc = block_sum<int>(nc, iws);
   nf = block_sum<int>(nf, iws);
@@ -802,6 +826,7 @@ __global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals*
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, iws[w]);
     out->cost = c;
     out->errx = e;
+    out->kernel_evals = ev;
     out->iters_sum = its;
     out->iters_max = m;
     out->not_converged = nc;

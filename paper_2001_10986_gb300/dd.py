@@ -37,6 +37,12 @@ class dd_sweep_stats(C.Structure):
                 ("sweeps_done", C.c_int64)]
 
 
+class dd_profile(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("half_sweeps", C.c_int64), ("solve_launches", C.c_int64),
+                ("solve_ms", C.c_double), ("gather_launches", C.c_int64), ("gather_ms", C.c_double),
+                ("kernel_evals", C.c_double), ("sinkhorn_iters", C.c_double), ("cells", C.c_int64)]
+
+
 class DDError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
@@ -66,17 +72,20 @@ _lib.dd_get_plan.argtypes = [_P, C.c_double, C.POINTER(C.c_int64), _P, _P, _P, C
 _lib.dd_get_duals.argtypes = [_P, C.c_int32, _pd]
 _lib.dd_get_info.argtypes = [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                              C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+_lib.dd_get_profile.argtypes = [_P, C.POINTER(dd_profile)]
+_lib.dd_reset_profile.argtypes = [_P]
 _lib.dd_destroy.argtypes = [_P]
 _lib.dd_destroy.restype = None
 _lib.dd_last_error.argtypes = [_P]
 _lib.dd_last_error.restype = C.c_char_p
 for _f in ("dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep", "dd_run_schedule", "dd_cost",
-           "dd_get_basic_marginals", "dd_get_plan", "dd_get_duals", "dd_get_info"):
+           "dd_get_basic_marginals", "dd_get_plan", "dd_get_duals", "dd_get_info", "dd_get_profile",
+           "dd_reset_profile"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep",
             "dd_run_schedule", "dd_cost", "dd_get_basic_marginals", "dd_get_plan", "dd_get_duals",
-            "dd_get_info", "dd_destroy", "dd_last_error")
+            "dd_get_info", "dd_get_profile", "dd_reset_profile", "dd_destroy", "dd_last_error")
 
 
 def _check(ctx, st):
@@ -188,6 +197,16 @@ def dd_get_duals(ctx, partition):
     return out
 
 
+def dd_get_profile(ctx) -> dd_profile:
+    p = dd_profile()
+    _check(ctx, _lib.dd_get_profile(ctx, C.byref(p)))
+    return p
+
+
+def dd_reset_profile(ctx):
+    _check(ctx, _lib.dd_reset_profile(ctx))
+
+
 def dd_destroy(ctx):
     _lib.dd_destroy(ctx)
 
@@ -233,6 +252,12 @@ class DD:
 
     def duals(self, partition):
         return dd_get_duals(self.ctx, partition)
+
+    def profile(self):
+        return dd_get_profile(self.ctx)
+
+    def reset_profile(self):
+        dd_reset_profile(self.ctx)
 
     def close(self):
         if self.ctx:

@@ -81,13 +81,13 @@ WORKLOADS = {
     "gm32_b4": Workload("gm32_b4", 32, 3, 4, 1),
     # 256×256, 5 blobs, 4×4 cells, 64²→128²→256²
     "gm256_b4_l3": Workload("gm256_b4_l3", 256, 5, 4, 3),
-    # 1024×1024, 8 anisotropic blobs, 4×4 cells, 128²→…→1024²
-    "gm1024_b4_l4": Workload("gm1024_b4_l4", 1024, 8, 4, 4, anisotropic=True),
-    # same images with 8×8 basic cells
-    "gm1024_b8_l3": Workload("gm1024_b8_l3", 1024, 8, 8, 3, anisotropic=True),
-    # 512×512, 6 blobs
-    "gm512_b4_l4": Workload("gm512_b4_l4", 512, 6, 4, 4),
-    # 2048×2048, 12 blobs, floor 1e-4, 5 levels
+    # 1024×1024, 8 anisotropic blobs, 4×4 cells, layers 8²→…→1024² as in §7.1
+    "gm1024_b4": Workload("gm1024_b4", 1024, 8, 4, 8, anisotropic=True),
+    # same images with 8×8 basic cells, 16²→…→1024²
+    "gm1024_b8": Workload("gm1024_b8", 1024, 8, 8, 7, anisotropic=True),
+    # 512×512, 6 blobs, 8²→…→512²
+    "gm512_b4": Workload("gm512_b4", 512, 6, 4, 7),
+    # 2048×2048, 12 blobs, floor 1e-4, 5 levels 128²→…→2048²
     "gm2048_b4_l5": Workload("gm2048_b4_l5", 2048, 12, 4, 5, floor=1e-4),
 }
 
@@ -101,17 +101,26 @@ def image_pair(w: Workload | str, k: int = 0) -> tuple[np.ndarray, np.ndarray]:
     return mu, nu
 
 
-def paper_schedule(n: int, levels: int, final_sweeps: int, *, coarse_sweeps=(2, 1, 1)):
+def paper_schedule(n: int, levels: int, final_sweeps: int, *, coarse_sweeps=(2, 1, 1),
+                   eps_start: float = 2.0 / 64, start_sweeps: int = 1):
     """ε schedule of the multi-scale protocol in [0,1]² units.
 
     At a coarse level with pixel spacing Δ the paper runs 4 iterations at ε=2Δ²,
     then 2 at Δ², then 2 at Δ²/2, then refines (one A+B sweep = 2 iterations).
     At the finest level (Δ = h = 1/n) the run stays at ε = 2h² for
-    `final_sweeps` sweeps. Returns a list of (eps, sweeps, level), level 0 being
-    the coarsest.
+    `final_sweeps` sweeps. The paper's coarsest layer is 8×8, where the first ε
+    is 2·(1/8)² = eps_start; when level 0 is finer than that, ε is first halved
+    from eps_start down to 2Δ₀² on level 0 (`start_sweeps` sweeps each), so
+    that the product coupling is never solved at a small ε. Returns a list of
+    (eps, sweeps, level), level 0 being the coarsest.
     """
     h = 1.0 / n
     steps = []
+    d0 = h * 2 ** (levels - 1)
+    e = float(eps_start)
+    while e > 2.0 * d0 * d0 * (1 + 1e-12):
+        steps.append((e, int(start_sweeps), 0))
+        e *= 0.5
     for lev in range(levels):
         d = h * 2 ** (levels - 1 - lev)
         if lev < levels - 1:

@@ -161,7 +161,7 @@ def test_sampled_cells_full_size(lib):
     # ε = 2h², compared on a sample of cells that the oracle solves one by one
     n, b = 1024, 4
     eps = 2.0 / n**2
-    mu, _ = syn.image_pair("gm1024_b4_l4", 0)
+    mu, _ = syn.image_pair("gm1024_b4", 0)
     nu, rp, col, val = syn.feasible_state(mu, b, seed=7)
     g = lib.DD(mu, nu, b, 1, [(eps, 1, 0)], err_tol=1e-6)
     g.set_state(rp, col, val)
