@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -88,6 +89,8 @@ struct dd_ctx {
   double* cell_errx = nullptr;
   int32_t* cell_iters = nullptr;
   int32_t* cell_status = nullptr;
+  int32_t* order = nullptr;
+  int32_t* iters_hist[2] = {nullptr, nullptr};
   unsigned long long* ydense = nullptr;
   int64_t level_alloc_n = 0;   // n of the per-level buffers
 
@@ -103,6 +106,9 @@ struct dd_ctx {
   double* h_yerr = nullptr;
 
   dd_profile prof{};
+  // debug trace of one cell (environment DD_TRACE_CELL="part,cell")
+  int trace_part = -1, trace_cell = -1;
+  float* trace_buf = nullptr;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   int last_part = -1;
   bool need_init = false;  // level-0 product coupling not built yet
@@ -222,6 +228,11 @@ void alloc_level_buffers(dd_ctx* c, int l, float*& alpha0, float*& alpha1, int2*
   dev_alloc(c->cell_errx, ncell);
   dev_alloc(c->cell_iters, ncell);
   dev_alloc(c->cell_status, ncell);
+  dev_alloc(c->order, ncell);
+  for (int k = 0; k < 2; ++k) {
+    dev_alloc(c->iters_hist[k], ncell);
+    DD_CUDA(cudaMemsetAsync(c->iters_hist[k], 0, sizeof(int32_t) * ncell, c->stream));
+  }
   dev_alloc(c->ydense, n2);
   for (int k = 0; k < 2; ++k) {
     dev_alloc(c->rp[k], nbasic + 1);
@@ -299,6 +310,14 @@ SweepArgs sweep_args(dd_ctx* c, int part, double eps) {
   a.cell_iters = c->cell_iters;
   a.cell_status = c->cell_status;
   a.err_flag = c->err_flag;
+  a.order = nullptr;
+  a.iters_hist = c->iters_hist[part];
+  a.trace_cell = -1;
+  a.trace = nullptr;
+  if (c->trace_buf && c->trace_part == part) {
+    a.trace_cell = c->trace_cell;
+    a.trace = c->trace_buf;
+  }
   return a;
 }
 
@@ -320,13 +339,15 @@ void half_sweep(dd_ctx* c, int part, double eps) {
   if (timing) DD_CUDA(cudaEventRecord(c->ev[0], c->stream));
   DD_CUDA(launch_gather(a, c->stream));
   check_debug(c, "gather");
+  DD_CUDA(launch_order(a, c->order, c->stream));
+  a.order = c->order;
   if (timing) DD_CUDA(cudaEventRecord(c->ev[1], c->stream));
   DD_CUDA(launch_sinkhorn(a, threads_per_cell(c), c->stream));
   check_debug(c, "sinkhorn");
   if (timing) DD_CUDA(cudaEventRecord(c->ev[2], c->stream));
   DD_CUDA(launch_row_scan(c->row_cnt, c->rp[other], c->tile, nrows, c->stream));
   DD_CUDA(launch_reduce_cells(a, c->totals, c->stream));
-  c->prof.launches += 5;
+  c->prof.launches += 6;
   DD_CUDA(cudaMemcpyAsync(c->h_tot, c->totals, sizeof(SweepTotals), cudaMemcpyDeviceToHost, c->stream));
   DD_CUDA(cudaMemcpyAsync(c->h_nnz, c->rp[other] + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
   DD_CUDA(cudaMemcpyAsync(c->h_err, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -356,6 +377,15 @@ void half_sweep(dd_ctx* c, int part, double eps) {
   c->prof.kernel_evals += c->last_tot.kernel_evals;
   c->prof.sinkhorn_iters += (double)c->last_tot.iters_sum;
   c->prof.cells += a.ncells;
+  if (a.trace) {
+    std::vector<float> t(1024);
+    DD_CUDA(cudaMemcpy(t.data(), c->trace_buf, 4096, cudaMemcpyDeviceToHost));
+    std::fprintf(stderr, "trace part %d cell %d:", part, c->trace_cell);
+    for (int k = 0; k < 512 && t[2 * k] != 0.f; k += (k < 40 ? 1 : 50))
+      std::fprintf(stderr, " %d:%.3g(w%.2f)", k + 1, t[2 * k], t[2 * k + 1]);
+    std::fprintf(stderr, "\n");
+    DD_CUDA(cudaMemset(c->trace_buf, 0, 4096));
+  }
   if (timing) {
     float g_ms = 0.f, s_ms = 0.f;
     DD_CUDA(cudaEventElapsedTime(&g_ms, c->ev[0], c->ev[1]));
@@ -574,7 +604,7 @@ void release(dd_ctx* c) {
   void* bufs[] = {c->ws_ytmp, c->ws_vtmp, c->ws_eta, c->ws_nu, c->ws_lognu, c->ws_g, c->tmp_col, c->tmp_val,
                   c->row_cnt, c->row_src, c->tile, c->cell_off, c->cell_ny, c->anchor_new, c->cell_cost,
                   c->cell_errx, c->cell_iters, c->cell_status, c->ydense, c->ws_counter, c->err_flag,
-                  c->totals, c->yerr};
+                  c->totals, c->yerr, c->order, c->iters_hist[0], c->iters_hist[1], c->trace_buf};
   for (void* p : bufs) dev_free(p);
   if (c->h_tot) cudaFreeHost(c->h_tot);
   if (c->h_nnz) cudaFreeHost(c->h_nnz);
@@ -724,6 +754,12 @@ dd_status dd_create(const double* mu, const double* nu, const dd_grid* grid, int
     DD_CUDA(cudaMallocHost((void**)&c->h_err, sizeof(int)));
     DD_CUDA(cudaMallocHost((void**)&c->h_yerr, sizeof(double)));
     for (int k = 0; k < 3; ++k) DD_CUDA(cudaEventCreate(&c->ev[k]));
+    if (const char* tr = std::getenv("DD_TRACE_CELL")) {
+      if (std::sscanf(tr, "%d,%d", &c->trace_part, &c->trace_cell) == 2) {
+        dev_alloc(c->trace_buf, 1024);
+        DD_CUDA(cudaMemset(c->trace_buf, 0, 4096));
+      }
+    }
     build_levels(c, mu, nu);
     enter_level0(c);
     c->eps_cur = c->sched[0].eps;
@@ -961,6 +997,21 @@ dd_status dd_get_info(dd_ctx* c, int32_t* level, int32_t* n_level, int32_t* n_ba
     if (n_basic) *n_basic = c->lh[c->lev].nb * c->lh[c->lev].nb;
     if (eps) *eps = c->eps_cur;
     if (nnz) *nnz = c->nnz;
+  });
+}
+
+dd_status dd_get_cell_stats(dd_ctx* c, int32_t* iters, double* err_x, int32_t* n_y, int32_t* status,
+                            int32_t cap, int32_t* n_cells) {
+  return guarded(c, [&] {
+    if (c->last_part < 0) throw DdError{DD_ERR_STATE, "no half-sweep has run at this level"};
+    const int nc = num_cells(c->last_part, c->lh[c->lev].nb);
+    if (n_cells) *n_cells = nc;
+    if ((iters || err_x || n_y || status) && cap < nc) throw DdError{DD_ERR_CAPACITY, "buffer too small"};
+    if (iters) DD_CUDA(cudaMemcpyAsync(iters, c->cell_iters, 4 * (size_t)nc, cudaMemcpyDeviceToHost, c->stream));
+    if (err_x) DD_CUDA(cudaMemcpyAsync(err_x, c->cell_errx, 8 * (size_t)nc, cudaMemcpyDeviceToHost, c->stream));
+    if (n_y) DD_CUDA(cudaMemcpyAsync(n_y, c->cell_ny, 4 * (size_t)nc, cudaMemcpyDeviceToHost, c->stream));
+    if (status) DD_CUDA(cudaMemcpyAsync(status, c->cell_status, 4 * (size_t)nc, cudaMemcpyDeviceToHost, c->stream));
+    DD_CUDA(cudaStreamSynchronize(c->stream));
   });
 }
 

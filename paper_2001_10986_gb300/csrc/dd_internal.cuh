@@ -113,10 +113,15 @@ struct SweepArgs {
   int32_t* cell_iters;
   int32_t* cell_status;     // bit0 not converged, bit1 non-finite, bit2 workspace overflow
   int* err_flag;
+  const int32_t* order;     // launch order of the cells (NULL: natural order)
+  int32_t* iters_hist;      // iterations of each cell's last solve in this partition
+  int trace_cell;           // debug: cell whose per-iteration error is recorded (-1: none)
+  float* trace;             // debug: 2×512 floats (relative X-error, ω) per iteration
 };
 
 // kernel launchers (dd_kernels.cu)
 cudaError_t launch_gather(const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_order(const SweepArgs& a, int32_t* order, cudaStream_t s);
 cudaError_t launch_sinkhorn(const SweepArgs& a, int threads, cudaStream_t s);
 cudaError_t launch_row_scan(const int32_t* cnt, int64_t* rp_out, int64_t* tile_sum, int nrows,
                             cudaStream_t s);

@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256) k_gather(SweepArgs a) {
 // (per support point), κ = Δ²/(ε ln 2), and scalings u, v near 1.
 //   Y-iteration: s(y) = Σ_x K̃ u, v(y) = ν(y)/s(y);
 //   X-marginal:  P_X π(x) = u(x) Σ_y K̃ v;   X-iteration: u ← u·μ/P_X π.
-// The stabilisers stay fixed while |log2 u|, |log2 v| ≤ kTau, so K̃ is
+// The stabilisers stay fixed while u, v stay in [2^-16, 2^16], so K̃ is
 // recomputed bit-identically in every pass and the scalings converge to FP32
 // precision; a scaling that leaves that band is absorbed into its stabiliser.
 // The first pass of a solve sets Gs = −max_x(F − κc̃) and absorbs v.
@@ -238,7 +238,8 @@ __global__ void __launch_bounds__(256) k_gather(SweepArgs a) {
 // the H×W cell.
 
 constexpr int kMaxHW = 256;
-constexpr float kTau = 16.0f;
+constexpr int kTraceLen = 512;
+constexpr float kTwoTau = 65536.0f;   // scalings leave the band [2^-16, 2^16] → absorb
 
 struct SinkSmem {
   float F[kMaxHW];
@@ -253,6 +254,9 @@ struct SinkSmem {
   double dws[32];
   float s_err;
   int s_stop;
+  float omega;       // over-relaxation factor of the X-iteration
+  float e3, emin;    // error history for choosing / safeguarding omega
+  int relax_off;
   uint64_t q64[4];
   uint64_t w64[4];
   int nsur, ndef;
@@ -342,6 +346,12 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   // Truncate leaves ‖ν_cell‖ ≤ ‖μ_J‖: the stopping test compares P_X π with μ
   // rescaled to ‖ν_cell‖ (the §6.2 rule when nothing was truncated)
   const float mscale = muJ > 0.f ? nuJ / muJ : 1.f;
+  if (tid == 0) {
+    sm.omega = 1.0f;
+    sm.e3 = 0.f;
+    sm.emin = 3.0e38f;
+    sm.relax_off = 0;
+  }
 
   float Fr[16], ur[16];
   int arow[RPT];
@@ -374,7 +384,7 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
       const int kk = valid ? k : 0;
       const int32_t e = a.ws_eta[off + kk];
       const int er = eta_r(e), ec = eta_c(e);
-      const float lognu = a.ws_lognu[off + kk];
+      const float nuy = (float)a.ws_nu[off + kk] * kFixToFloat;
       float Cc[W], Rq[RPT];
 #pragma unroll
       for (int c = 0; c < W; ++c) {
@@ -433,9 +443,12 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
         s = group_sum<G>(s);
         absorb = true;
       }
-      const float lv = lognu - lg2(s);
-      const float v = valid ? ex2(lv) : 0.f;
-      if (valid && gid == 0 && (absorb || fabsf(lv) > kTau)) a.ws_g[off + k] = Gs + lv;
+      // v = ν/s with IEEE division: the iteration map itself uses correctly
+      // rounded arithmetic; only the frozen kernel K̃ uses ex2.approx
+      float v = valid ? nuy / s : 0.f;
+      if (valid && (absorb || v > kTwoTau || v < 1.0f / kTwoTau)) {
+        if (gid == 0) a.ws_g[off + k] = Gs + log2f(v);
+      }
 #pragma unroll
       for (int q = 0; q < 16; ++q) acc[q] = fmaf(v, pv[q], acc[q]);
     }
@@ -468,6 +481,25 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
       else if (it >= a.max_iter) stop = 3;
       sm.s_stop = stop;
       sm.s_err = erp;
+      // Over-relaxed X-iteration u ← u·(μ/P_X π)^ω (same fixed point, same
+      // stopping rule, always ending on a Y-iteration). ω follows from the
+      // contraction ρ of the plain iteration measured over iterations 3..6,
+      // ω = 2/(1+√(1−ρ)) capped at 1.8, and falls back to 1 for good when the
+      // error grows well above its running minimum.
+      if (it == 3) sm.e3 = ep;
+      if (it == 6 && !sm.relax_off && sm.e3 > 0.f) {
+        const float rho = cbrtf(ep / sm.e3);
+        if (rho > 0.5f && rho < 1.0f) sm.omega = fminf(1.8f, 2.0f / (1.0f + sqrtf(1.0f - rho)));
+      }
+      if (ep > 1.5f * sm.emin && sm.omega != 1.0f) {
+        sm.omega = 1.0f;
+        sm.relax_off = 1;
+      }
+      sm.emin = fminf(sm.emin, ep);
+      if (J == a.trace_cell && a.trace && it <= kTraceLen) {
+        a.trace[2 * (it - 1)] = ep / muJ;
+        a.trace[2 * (it - 1) + 1] = sm.omega;
+      }
     }
     __syncthreads();
     const int stop = sm.s_stop;
@@ -477,14 +509,15 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
       bad = stop == 2;
       break;
     }
-    // ---- X-iteration u ← u·μ/P_X π, absorbing large scalings into F ----
+    // ---- X-iteration u ← u·(μ/P_X π)^ω, absorbing large scalings into F ----
+    const float omega = sm.omega;
     for (int x = tid; x < HW; x += NT) {
       const float px = sm.PX[x];
       if (px > 1e-37f && px < 1e37f) {
-        const float un = sm.u[x] * (sm.mu[x] / px);
-        const float lu = lg2(un);
-        if (fabsf(lu) > kTau) {
-          sm.F[x] += lu;
+        const float ratio = sm.mu[x] / px;
+        const float un = sm.u[x] * (omega == 1.0f ? ratio : exp2f(omega * log2f(ratio)));
+        if (un > kTwoTau || un < 1.0f / kTwoTau) {
+          sm.F[x] += log2f(un);
           sm.u[x] = 1.0f;
         } else {
           sm.u[x] = un;
@@ -677,6 +710,7 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     a.cell_errx[J] = (double)errx;
     a.cell_iters[J] = it;
     a.cell_status[J] = (converged ? 0 : 1) | (bad ? 2 : 0);
+    if (a.iters_hist) a.iters_hist[J] = it;
     if (bad) atomicOr(a.err_flag, 2);
   }
 }
@@ -685,7 +719,7 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
 // instantiation (A cells share one shape, B has corner/edge shapes)
 __global__ void __launch_bounds__(256) k_sinkhorn(SweepArgs a) {
   __shared__ SinkSmem sm;
-  const int J = blockIdx.x;
+  const int J = a.order ? a.order[blockIdx.x] : blockIdx.x;
   if (*a.err_flag & 4) return;
   const CellGeom g = cell_geom(a.part, J, a.L.nb, a.L.b);
   const int W = g.W, H = g.H;
@@ -701,6 +735,39 @@ __global__ void __launch_bounds__(256) k_sinkhorn(SweepArgs a) {
     if (H <= 8) sinkhorn_cell<16, 8>(a, J, g, sm);
     else sinkhorn_cell<16, 16>(a, J, g, sm);
   }
+}
+
+// ---------------------------------------------------------------------------
+// launch order of the cells: largest predicted work first (Sinkhorn
+// iterations of the cell's previous solve × support size × pixels), so that
+// slowly converging cells do not start last and stretch the launch. Counting
+// sort over 32 logarithmic buckets, one CTA.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_order(SweepArgs a, int32_t* order) {
+  __shared__ int cnt[32];
+  __shared__ int off[32];
+  const int nc = a.ncells;
+  if (threadIdx.x < 32) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  auto bucket = [&](int J) {
+    if (a.cell_off[J] < 0) return 0;
+    const CellGeom g = cell_geom(a.part, J, a.L.nb, a.L.b);
+    const int it = a.iters_hist ? max(a.iters_hist[J], 1) : 1;
+    const double w = (double)it * (double)max(a.cell_ny[J], 1) * (double)(g.H * g.W);
+    const int lg = 63 - __clzll((unsigned long long)w);
+    return 31 - min(31, lg / 2);   // heavier cells → smaller bucket index
+  };
+  for (int J = threadIdx.x; J < nc; J += blockDim.x) atomicAdd(&cnt[bucket(J)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int k = 0; k < 32; ++k) {
+      off[k] = s;
+      s += cnt[k];
+    }
+  }
+  __syncthreads();
+  for (int J = threadIdx.x; J < nc; J += blockDim.x) order[atomicAdd(&off[bucket(J)], 1)] = J;
 }
 
 // ---------------------------------------------------------------------------
@@ -1059,6 +1126,11 @@ __global__ void __launch_bounds__(256) k_plan(SweepArgs a, float trunc, const in
 // ---------------------------------------------------------------------------
 cudaError_t launch_gather(const SweepArgs& a, cudaStream_t s) {
   k_gather<<<a.ncells, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_order(const SweepArgs& a, int32_t* order, cudaStream_t s) {
+  k_order<<<1, 1024, 0, s>>>(a, order);
   return cudaGetLastError();
 }
 

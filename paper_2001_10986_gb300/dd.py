@@ -72,6 +72,7 @@ _lib.dd_get_plan.argtypes = [_P, C.c_double, C.POINTER(C.c_int64), _P, _P, _P, C
 _lib.dd_get_duals.argtypes = [_P, C.c_int32, _pd]
 _lib.dd_get_info.argtypes = [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                              C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+_lib.dd_get_cell_stats.argtypes = [_P, _P, _P, _P, _P, C.c_int32, C.POINTER(C.c_int32)]
 _lib.dd_get_profile.argtypes = [_P, C.POINTER(dd_profile)]
 _lib.dd_reset_profile.argtypes = [_P]
 _lib.dd_destroy.argtypes = [_P]
@@ -80,12 +81,13 @@ _lib.dd_last_error.argtypes = [_P]
 _lib.dd_last_error.restype = C.c_char_p
 for _f in ("dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep", "dd_run_schedule", "dd_cost",
            "dd_get_basic_marginals", "dd_get_plan", "dd_get_duals", "dd_get_info", "dd_get_profile",
-           "dd_reset_profile"):
+           "dd_reset_profile", "dd_get_cell_stats"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep",
             "dd_run_schedule", "dd_cost", "dd_get_basic_marginals", "dd_get_plan", "dd_get_duals",
-            "dd_get_info", "dd_get_profile", "dd_reset_profile", "dd_destroy", "dd_last_error")
+            "dd_get_info", "dd_get_cell_stats", "dd_get_profile", "dd_reset_profile", "dd_destroy",
+            "dd_last_error")
 
 
 def _check(ctx, st):
@@ -197,6 +199,19 @@ def dd_get_duals(ctx, partition):
     return out
 
 
+def dd_get_cell_stats(ctx):
+    """Returns dict of per-cell arrays (iters, err_x, n_y, status) of the last half-sweep."""
+    nc = C.c_int32()
+    _check(ctx, _lib.dd_get_cell_stats(ctx, None, None, None, None, 0, C.byref(nc)))
+    it = np.zeros(nc.value, np.int32)
+    ex = np.zeros(nc.value, np.float64)
+    ny = np.zeros(nc.value, np.int32)
+    st = np.zeros(nc.value, np.int32)
+    _check(ctx, _lib.dd_get_cell_stats(ctx, it.ctypes.data, ex.ctypes.data, ny.ctypes.data, st.ctypes.data,
+                                       nc.value, C.byref(nc)))
+    return {"iters": it, "err_x": ex, "n_y": ny, "status": st}
+
+
 def dd_get_profile(ctx) -> dd_profile:
     p = dd_profile()
     _check(ctx, _lib.dd_get_profile(ctx, C.byref(p)))
@@ -252,6 +267,9 @@ class DD:
 
     def duals(self, partition):
         return dd_get_duals(self.ctx, partition)
+
+    def cell_stats(self):
+        return dd_get_cell_stats(self.ctx)
 
     def profile(self):
         return dd_get_profile(self.ctx)
