@@ -196,6 +196,48 @@ dd_status dd_get_profile(dd_ctx* ctx, dd_profile* out);
 /* Reset the context's counters to zero. */
 dd_status dd_reset_profile(dd_ctx* ctx);
 
+/* Solve one composite cell without allocating any memory (no counterpart in
+ * the paper: this is a library facility). Some callers cannot call
+ * cudaMalloc when they need a solve: code that is capturing a stream into a
+ * CUDA graph (an allocation is not a capturable operation and synchronises
+ * the device), latency-critical loops that must not wait on the allocator,
+ * and hosts whose device memory belongs to another runtime. This entry point
+ * runs the same cell solve as a half-sweep (Sinkhorn with the §6.2 stop rule,
+ * extraction, BalanceMeasures, Truncate) with all scratch memory in one
+ * fixed-size array that the library holds on every device that loads it,
+ * from load until process exit (about 1.9 MB).
+ *
+ * The cell is a 2b×2b block of 4 basic cells of b×b pixels with pixel
+ * spacing `spacing` ([0,1]² units). All array arguments are DEVICE pointers
+ * owned by the caller:
+ *   mu        (2b)² FP64, μ of the cell's pixels, row-major;
+ *   y_row, y_col  n_y int32 offsets of the support points of ν_cell from the
+ *             cell's top-left pixel, distinct, sorted row-major, each in
+ *             (−2048, 2048);
+ *   nu        n_y FP64 masses ν_cell(y) > 0 (all masses are fractions of a
+ *             total mass 1, as in dd_create);
+ *   alpha     (2b)² FP64, in: warm-start α = ε·log u (any constant offset),
+ *             out: the cell's new α (up to a constant);
+ *   nu_basic  4·n_y FP64 output, row k = basic cell k (row-major in the 2×2
+ *             block): its new Y-marginal on the support points, 0 where
+ *             truncated.
+ * eps, err_tol (Err), max_iter and trunc as in dd_options. stream: the
+ * cudaStream_t to run on (NULL = the legacy default stream). The call
+ * returns after the solve has finished on that stream.
+ *
+ * Limits: b ∈ {2,4,8}; 1 ≤ n_y ≤ 16384; larger inputs are rejected with
+ * DD_ERR_ARG before any work is queued, and dd_last_error(NULL) says why.
+ * The first call on a device resolves the address of the scratch array with
+ * cudaGetSymbolAddress; make that first call before any stream capture
+ * begins. Every call reuses the same array and leaves its own data in it;
+ * calls that overlap on the GPU (other streams or host threads) race on it
+ * and must be serialised by the caller. Errors: DD_ERR_ARG (sizes, NULL,
+ * unsorted or out-of-range support), DD_ERR_NUMERIC, DD_ERR_CUDA. */
+dd_status dd_solve_cell_noalloc(const double* mu, int32_t b, double spacing, int32_t n_y,
+                                const int32_t* y_row, const int32_t* y_col, const double* nu,
+                                double eps, double err_tol, int32_t max_iter, double trunc,
+                                double* alpha, double* nu_basic, void* stream);
+
 /* Free the context and all device memory it owns. NULL is allowed. */
 void dd_destroy(dd_ctx* ctx);
 

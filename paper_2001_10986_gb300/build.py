@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libddot.so")
-SOURCES = ["dd_kernels.cu", "dd_api.cu"]
+SOURCES = ["dd_kernels.cu", "dd_api.cu", "dd_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -35,7 +35,17 @@ def _run(cmd):
     return r.stdout + r.stderr
 
 
-def build(verbose: bool = False, extra_flags=()) -> str:
+def _up_to_date() -> bool:
+    if not os.path.exists(LIB):
+        return False
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "dd.h"), __file__]
+    return os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps)
+
+
+def build(verbose: bool = False, extra_flags=(), force: bool = False) -> str:
+    """Compile libddot.so unless it is newer than every source (or force)."""
+    if not force and not extra_flags and _up_to_date():
+        return LIB
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
     objs = []
@@ -55,4 +65,4 @@ def build(verbose: bool = False, extra_flags=()) -> str:
 
 
 if __name__ == "__main__":
-    print(build(verbose=True))
+    print(build(verbose=True, force=True))

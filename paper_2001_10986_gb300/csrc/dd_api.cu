@@ -674,6 +674,8 @@ void fill_stats(dd_ctx* c, dd_sweep_stats* st) {
 
 }  // namespace
 
+void dd_set_noalloc_error(const char* msg) { g_create_error = msg ? msg : ""; }
+
 extern "C" {
 
 void dd_options_default(dd_options* opt) {

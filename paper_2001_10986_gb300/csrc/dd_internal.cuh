@@ -167,3 +167,6 @@ cudaError_t launch_plan(const SweepArgs& a, float trunc, const int64_t* xrp, int
                         int32_t* pcol, double* pval, int write, cudaStream_t s);
 
 }  // namespace ddk
+
+// sets the message returned by dd_last_error(NULL) in this thread
+void dd_set_noalloc_error(const char* msg);

@@ -72,6 +72,9 @@ _lib.dd_get_plan.argtypes = [_P, C.c_double, C.POINTER(C.c_int64), _P, _P, _P, C
 _lib.dd_get_duals.argtypes = [_P, C.c_int32, _pd]
 _lib.dd_get_info.argtypes = [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                              C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+_lib.dd_solve_cell_noalloc.argtypes = [_P, C.c_int32, C.c_double, C.c_int32, _P, _P, _P, C.c_double,
+                                       C.c_double, C.c_int32, C.c_double, _P, _P, _P]
+_lib.dd_solve_cell_noalloc.restype = C.c_int
 _lib.dd_get_cell_stats.argtypes = [_P, _P, _P, _P, _P, C.c_int32, C.POINTER(C.c_int32)]
 _lib.dd_get_profile.argtypes = [_P, C.POINTER(dd_profile)]
 _lib.dd_reset_profile.argtypes = [_P]
@@ -87,7 +90,7 @@ for _f in ("dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep", "dd_run_sch
 EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep",
             "dd_run_schedule", "dd_cost", "dd_get_basic_marginals", "dd_get_plan", "dd_get_duals",
             "dd_get_info", "dd_get_cell_stats", "dd_get_profile", "dd_reset_profile", "dd_destroy",
-            "dd_last_error")
+            "dd_last_error", "dd_solve_cell_noalloc")
 
 
 def _check(ctx, st):
@@ -210,6 +213,14 @@ def dd_get_cell_stats(ctx):
     _check(ctx, _lib.dd_get_cell_stats(ctx, it.ctypes.data, ex.ctypes.data, ny.ctypes.data, st.ctypes.data,
                                        nc.value, C.byref(nc)))
     return {"iters": it, "err_x": ex, "n_y": ny, "status": st}
+
+
+def dd_solve_cell_noalloc(mu, b, spacing, n_y, y_row, y_col, nu, eps, err_tol, max_iter, trunc,
+                          alpha, nu_basic, stream=None):
+    """All array arguments are device addresses (ints, e.g. tensor.data_ptr())."""
+    _check(None, _lib.dd_solve_cell_noalloc(mu, int(b), float(spacing), int(n_y), y_row, y_col, nu,
+                                            float(eps), float(err_tol), int(max_iter), float(trunc),
+                                            alpha, nu_basic, _stream_ptr(stream)))
 
 
 def dd_get_profile(ctx) -> dd_profile:
