@@ -110,6 +110,9 @@ struct dd_ctx {
   int trace_part = -1, trace_cell = -1;
   float* trace_buf = nullptr;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t stream2 = nullptr;     // cluster solves run beside the per-CTA solves
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int* nbig = nullptr;
   int last_part = -1;
   bool need_init = false;  // level-0 product coupling not built yet
   double eps_cur = 0.0;
@@ -311,6 +314,8 @@ SweepArgs sweep_args(dd_ctx* c, int part, double eps) {
   a.cell_status = c->cell_status;
   a.err_flag = c->err_flag;
   a.order = nullptr;
+  a.nbig = nullptr;
+  a.max_big = c->opt.max_cluster_cells < 0 ? 32 : std::min(c->opt.max_cluster_cells, 32);
   a.iters_hist = c->iters_hist[part];
   a.trace_cell = -1;
   a.trace = nullptr;
@@ -339,15 +344,22 @@ void half_sweep(dd_ctx* c, int part, double eps) {
   if (timing) DD_CUDA(cudaEventRecord(c->ev[0], c->stream));
   DD_CUDA(launch_gather(a, c->stream));
   check_debug(c, "gather");
-  DD_CUDA(launch_order(a, c->order, c->stream));
+  DD_CUDA(launch_order(a, c->order, c->nbig, c->stream));
   a.order = c->order;
+  a.nbig = c->nbig;
   if (timing) DD_CUDA(cudaEventRecord(c->ev[1], c->stream));
+  // the largest cells go to clusters on a second stream, the rest run beside them
+  DD_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+  DD_CUDA(cudaStreamWaitEvent(c->stream2, c->ev_fork, 0));
+  DD_CUDA(launch_sinkhorn_cluster(a, c->stream2));
+  DD_CUDA(cudaEventRecord(c->ev_join, c->stream2));
   DD_CUDA(launch_sinkhorn(a, threads_per_cell(c), c->stream));
+  DD_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   check_debug(c, "sinkhorn");
   if (timing) DD_CUDA(cudaEventRecord(c->ev[2], c->stream));
   DD_CUDA(launch_row_scan(c->row_cnt, c->rp[other], c->tile, nrows, c->stream));
   DD_CUDA(launch_reduce_cells(a, c->totals, c->stream));
-  c->prof.launches += 6;
+  c->prof.launches += 7;
   DD_CUDA(cudaMemcpyAsync(c->h_tot, c->totals, sizeof(SweepTotals), cudaMemcpyDeviceToHost, c->stream));
   DD_CUDA(cudaMemcpyAsync(c->h_nnz, c->rp[other] + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
   DD_CUDA(cudaMemcpyAsync(c->h_err, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -604,7 +616,7 @@ void release(dd_ctx* c) {
   void* bufs[] = {c->ws_ytmp, c->ws_vtmp, c->ws_eta, c->ws_nu, c->ws_lognu, c->ws_g, c->tmp_col, c->tmp_val,
                   c->row_cnt, c->row_src, c->tile, c->cell_off, c->cell_ny, c->anchor_new, c->cell_cost,
                   c->cell_errx, c->cell_iters, c->cell_status, c->ydense, c->ws_counter, c->err_flag,
-                  c->totals, c->yerr, c->order, c->iters_hist[0], c->iters_hist[1], c->trace_buf};
+                  c->totals, c->yerr, c->order, c->iters_hist[0], c->iters_hist[1], c->trace_buf, c->nbig};
   for (void* p : bufs) dev_free(p);
   if (c->h_tot) cudaFreeHost(c->h_tot);
   if (c->h_nnz) cudaFreeHost(c->h_nnz);
@@ -612,6 +624,9 @@ void release(dd_ctx* c) {
   if (c->h_yerr) cudaFreeHost(c->h_yerr);
   for (int k = 0; k < 3; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->stream2) cudaStreamDestroy(c->stream2);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -685,6 +700,7 @@ void dd_options_default(dd_options* opt) {
   opt->trunc = 1e-15;
   opt->max_iter = 2000;
   opt->threads_per_cell = 0;
+  opt->max_cluster_cells = -1;
   opt->stream = nullptr;
   opt->debug_flags = 0;
 }
@@ -756,6 +772,10 @@ dd_status dd_create(const double* mu, const double* nu, const dd_grid* grid, int
     DD_CUDA(cudaMallocHost((void**)&c->h_err, sizeof(int)));
     DD_CUDA(cudaMallocHost((void**)&c->h_yerr, sizeof(double)));
     for (int k = 0; k < 3; ++k) DD_CUDA(cudaEventCreate(&c->ev[k]));
+    DD_CUDA(cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking));
+    DD_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    DD_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    dev_alloc(c->nbig, 1);
     if (const char* tr = std::getenv("DD_TRACE_CELL")) {
       if (std::sscanf(tr, "%d,%d", &c->trace_part, &c->trace_cell) == 2) {
         dev_alloc(c->trace_buf, 1024);

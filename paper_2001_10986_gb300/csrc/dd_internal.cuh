@@ -114,6 +114,8 @@ struct SweepArgs {
   int32_t* cell_status;     // bit0 not converged, bit1 non-finite, bit2 workspace overflow
   int* err_flag;
   const int32_t* order;     // launch order of the cells (NULL: natural order)
+  const int* nbig;          // the first *nbig cells of `order` are solved by clusters (NULL: none)
+  int max_big;              // upper limit for *nbig (≤ 32)
   int32_t* iters_hist;      // iterations of each cell's last solve in this partition
   int trace_cell;           // debug: cell whose per-iteration error is recorded (-1: none)
   float* trace;             // debug: 2×512 floats (relative X-error, ω) per iteration
@@ -121,7 +123,8 @@ struct SweepArgs {
 
 // kernel launchers (dd_kernels.cu)
 cudaError_t launch_gather(const SweepArgs& a, cudaStream_t s);
-cudaError_t launch_order(const SweepArgs& a, int32_t* order, cudaStream_t s);
+cudaError_t launch_order(const SweepArgs& a, int32_t* order, int* nbig, cudaStream_t s);
+cudaError_t launch_sinkhorn_cluster(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_sinkhorn(const SweepArgs& a, int threads, cudaStream_t s);
 cudaError_t launch_row_scan(const int32_t* cnt, int64_t* rp_out, int64_t* tile_sum, int nrows,
                             cudaStream_t s);

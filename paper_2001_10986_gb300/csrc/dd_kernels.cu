@@ -14,8 +14,12 @@
 // All kernels are plain launches; none of them waits on another CTA.
 #include "dd_internal.cuh"
 
+#include <cooperative_groups.h>
+
 #include <cfloat>
 #include <cstdint>
+
+namespace cg = cooperative_groups;
 
 namespace ddk {
 
@@ -239,6 +243,8 @@ __global__ void __launch_bounds__(256) k_gather(SweepArgs a) {
 
 constexpr int kMaxHW = 256;
 constexpr int kTraceLen = 512;
+constexpr int kClusterCTAs = 8;    // CTAs sharing one large cell
+constexpr int kMaxBig = 32;        // cells solved by clusters per launch
 constexpr float kTwoTau = 65536.0f;   // scalings leave the band [2^-16, 2^16] → absorb
 
 struct SinkSmem {
@@ -247,6 +253,7 @@ struct SinkSmem {
   float l2mu[kMaxHW];
   float mu[kMaxHW];
   float PX[kMaxHW];
+  float PXp[kMaxHW];     // this CTA's partial Σ_y K̃ v (read by the other CTAs of a cluster)
   float red[8][kMaxHW];
   float fws[32];
   int iws[32];
@@ -302,8 +309,13 @@ __device__ __forceinline__ int warp_reduce_scatter16(float (&v)[16], int lane) {
   return base;
 }
 
-template <int W, int G>
-__device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g, SinkSmem& sm) {
+// CS > 1: a cluster of CS CTAs shares one cell; CTA `rank` takes the support
+// points k ≡ rank (mod CS) in blocks of YS, the X-marginal is summed over the
+// cluster through distributed shared memory, every CTA applies the same
+// X-iteration, and rank 0 alone runs the epilogue.
+template <int W, int G, int CS>
+__device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g, SinkSmem& sm,
+                              const int rank) {
   constexpr int RPT = 16 / W;
   constexpr int NV = G >= 2 ? G / 2 : 1;
   const LevelView& L = a.L;
@@ -318,6 +330,13 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     return;
   }
   const int ny = a.cell_ny[J];
+  if (ny <= 0) {
+    if (tid == 0 && rank == 0) {
+      a.cell_status[J] = 2;
+      atomicOr(a.err_flag, 2);
+    }
+    return;
+  }
   const int2 anc_old = a.anchor[J];
   const int2 anc = a.anchor_new[J];
   const float d2 = (float)(L.spacing * L.spacing);
@@ -325,6 +344,7 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   const float kappa = (float)(L.spacing * L.spacing / ((double)a.eps * 0.69314718055994530942));
   const int Dr = g.r0 - anc.x, Dc = g.c0 - anc.y;
   const int shr = anc.x - anc_old.x, shc = anc.y - anc_old.y;
+  const int kstep = CS * YS;
 
   // stabiliser F in the new frame, scalings u = 1
   for (int x = tid; x < HW; x += NT) {
@@ -378,13 +398,25 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     // ---- Y-iteration and X-marginal of the new plan ----
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc[q] = 0.f;
-    for (int k0 = 0; k0 < ny; k0 += YS) {
+    // per-y data of the next support point are loaded one step ahead
+    int kn = rank * YS + slot;
+    int kkn = kn < ny ? kn : ny - 1;
+    int32_t e_n = a.ws_eta[off + kkn];
+    uint64_t nu_n = a.ws_nu[off + kkn];
+    float g_n = it > 0 ? a.ws_g[off + kkn] : 0.f;
+    for (int k0 = rank * YS; k0 < ny; k0 += kstep) {
       const int k = k0 + slot;
       const bool valid = k < ny;
-      const int kk = valid ? k : 0;
-      const int32_t e = a.ws_eta[off + kk];
+      const int32_t e = e_n;
+      const uint64_t nuq = nu_n;
+      const float g_pre = g_n;
+      kn = k + kstep;
+      kkn = kn < ny ? kn : ny - 1;
+      e_n = a.ws_eta[off + kkn];
+      nu_n = a.ws_nu[off + kkn];
+      if (it > 0) g_n = a.ws_g[off + kkn];
       const int er = eta_r(e), ec = eta_c(e);
-      const float nuy = (float)a.ws_nu[off + kk] * kFixToFloat;
+      const float nuy = (float)nuq * kFixToFloat;
       float Cc[W], Rq[RPT];
 #pragma unroll
       for (int c = 0; c < W; ++c) {
@@ -406,9 +438,9 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
           for (int c = 0; c < W; ++c) m = fmaxf(m, Fr[r * W + c] - Rq[r] - Cc[c]);
         Gs = -group_max<G>(m);
       } else {
-        Gs = a.ws_g[off + kk];
+        Gs = g_pre;
       }
-      float s = 0.f;
+      float s0 = 0.f, s1 = 0.f;
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
         const float Ra = Gs - Rq[r];
@@ -416,10 +448,11 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
         for (int c = 0; c < W; ++c) {
           const float p = ex2(Fr[r * W + c] + Ra - Cc[c]);
           pv[r * W + c] = p;
-          s = fmaf(p, ur[r * W + c], s);
+          if (((r * W + c) & 1) == 0) s0 = fmaf(p, ur[r * W + c], s0);
+          else s1 = fmaf(p, ur[r * W + c], s1);
         }
       }
-      s = group_sum<G>(s);
+      float s = group_sum<G>(s0 + s1);
       if (!(s > 1e-30f && s < 1e30f)) {
         // stabiliser too far off for this y: restart it from the running maximum
         float m = kNegBig;
@@ -466,11 +499,29 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     for (int x = tid; x < HW; x += NT) {
       float t = 0.f;
       for (int w = 0; w < nw; ++w) t += sm.red[w][x];
+      sm.PXp[x] = t;
+    }
+    if constexpr (CS > 1) {
+      cg::this_cluster().sync();
+    } else {
+      __syncthreads();
+    }
+    for (int x = tid; x < HW; x += NT) {
+      float t;
+      if constexpr (CS > 1) {
+        cg::cluster_group cl = cg::this_cluster();
+        t = 0.f;
+#pragma unroll
+        for (int r = 0; r < CS; ++r) t += cl.map_shared_rank(sm.PXp, r)[x];
+      } else {
+        t = sm.PXp[x];
+      }
       const float px = sm.u[x] * t;
       sm.PX[x] = px;
       ep += fabsf(px - sm.mu[x] * mscale);
       erp += fabsf(px - sm.mu[x]);
     }
+    if constexpr (CS > 1) cg::this_cluster().sync();  // remote reads done before PXp is rewritten
     ep = block_sum(ep, sm.fws);
     erp = block_sum(erp, sm.fws);
     ++it;
@@ -544,6 +595,12 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     }
     __syncthreads();
     load_Fu();
+  }
+  if constexpr (CS > 1) {
+    // the stabilisers G written by the other CTAs must be visible to rank 0
+    __threadfence();
+    cg::this_cluster().sync();
+    if (rank != 0) return;
   }
 
   // ---- epilogue: final plan → fractions per basic cell, transport cost ----
@@ -715,26 +772,47 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   }
 }
 
-// one kernel for all cell shapes of a partition; the shape picks the
-// instantiation (A cells share one shape, B has corner/edge shapes)
-__global__ void __launch_bounds__(256) k_sinkhorn(SweepArgs a) {
-  __shared__ SinkSmem sm;
-  const int J = a.order ? a.order[blockIdx.x] : blockIdx.x;
-  if (*a.err_flag & 4) return;
+// the cell shape picks the instantiation (A cells share one shape, B has
+// corner and edge shapes)
+template <int CS>
+__device__ void solve_cell(const SweepArgs& a, int J, SinkSmem& sm, int rank) {
   const CellGeom g = cell_geom(a.part, J, a.L.nb, a.L.b);
   const int W = g.W, H = g.H;
-  if (W == 2) sinkhorn_cell<2, 1>(a, J, g, sm);
+  if (W == 2) sinkhorn_cell<2, 1, CS>(a, J, g, sm, rank);
   else if (W == 4) {
-    if (H <= 4) sinkhorn_cell<4, 1>(a, J, g, sm);
-    else sinkhorn_cell<4, 2>(a, J, g, sm);
+    if (H <= 4) sinkhorn_cell<4, 1, CS>(a, J, g, sm, rank);
+    else sinkhorn_cell<4, 2, CS>(a, J, g, sm, rank);
   } else if (W == 8) {
-    if (H <= 4) sinkhorn_cell<8, 2>(a, J, g, sm);
-    else if (H <= 8) sinkhorn_cell<8, 4>(a, J, g, sm);
-    else sinkhorn_cell<8, 8>(a, J, g, sm);
+    if (H <= 4) sinkhorn_cell<8, 2, CS>(a, J, g, sm, rank);
+    else if (H <= 8) sinkhorn_cell<8, 4, CS>(a, J, g, sm, rank);
+    else sinkhorn_cell<8, 8, CS>(a, J, g, sm, rank);
   } else {
-    if (H <= 8) sinkhorn_cell<16, 8>(a, J, g, sm);
-    else sinkhorn_cell<16, 16>(a, J, g, sm);
+    if (H <= 8) sinkhorn_cell<16, 8, CS>(a, J, g, sm, rank);
+    else sinkhorn_cell<16, 16, CS>(a, J, g, sm, rank);
   }
+}
+
+// one CTA per cell, for the cells after the first nbig of the launch order
+__global__ void __launch_bounds__(256) k_sinkhorn(SweepArgs a) {
+  __shared__ SinkSmem sm;
+  const int nbig = a.nbig ? *a.nbig : 0;
+  const int pos = nbig + blockIdx.x;
+  if (pos >= a.ncells) return;
+  const int J = a.order ? a.order[pos] : pos;
+  if (*a.err_flag & 4) return;
+  solve_cell<1>(a, J, sm, 0);
+}
+
+// a cluster of kClusterCTAs CTAs per cell, for the first nbig cells of the
+// launch order (largest predicted work)
+__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256) k_sinkhorn_cluster(SweepArgs a) {
+  __shared__ SinkSmem sm;
+  const int c = blockIdx.x / kClusterCTAs;
+  if (c >= *a.nbig) return;   // uniform over the cluster
+  const int rank = (int)cg::this_cluster().block_rank();
+  const int J = a.order[c];
+  if (*a.err_flag & 4) return;
+  solve_cell<kClusterCTAs>(a, J, sm, rank);
 }
 
 // ---------------------------------------------------------------------------
@@ -743,31 +821,49 @@ __global__ void __launch_bounds__(256) k_sinkhorn(SweepArgs a) {
 // slowly converging cells do not start last and stretch the launch. Counting
 // sort over 32 logarithmic buckets, one CTA.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_order(SweepArgs a, int32_t* order) {
-  __shared__ int cnt[32];
-  __shared__ int off[32];
+__global__ void __launch_bounds__(1024) k_order(SweepArgs a, int32_t* order, int* nbig) {
+  constexpr int NB = 64;
+  __shared__ int cnt[NB];
+  __shared__ int off[NB];
+  __shared__ double dws[32];
+  __shared__ double s_thr;
   const int nc = a.ncells;
-  if (threadIdx.x < 32) cnt[threadIdx.x] = 0;
-  __syncthreads();
-  auto bucket = [&](int J) {
-    if (a.cell_off[J] < 0) return 0;
+  if (threadIdx.x < NB) cnt[threadIdx.x] = 0;
+  auto work = [&](int J) {
+    if (a.cell_off[J] < 0) return 1.0;
     const CellGeom g = cell_geom(a.part, J, a.L.nb, a.L.b);
     const int it = a.iters_hist ? max(a.iters_hist[J], 1) : 1;
-    const double w = (double)it * (double)max(a.cell_ny[J], 1) * (double)(g.H * g.W);
-    const int lg = 63 - __clzll((unsigned long long)w);
-    return 31 - min(31, lg / 2);   // heavier cells → smaller bucket index
+    return (double)it * (double)max(a.cell_ny[J], 1) * (double)(g.H * g.W);
   };
-  for (int J = threadIdx.x; J < nc; J += blockDim.x) atomicAdd(&cnt[bucket(J)], 1);
+  auto bucket = [&](double w) {
+    // half-octave buckets, heavier cells first
+    const int b2 = (int)(2.0 * log2(fmax(w, 1.0)));
+    return NB - 1 - min(NB - 1, b2);
+  };
+  double tot = 0.0;
+  for (int J = threadIdx.x; J < nc; J += blockDim.x) tot += work(J);
+  tot = block_sum<double>(tot, dws);
+  if (threadIdx.x == 0) s_thr = tot / (2.0 * 152.0);   // half of one SM's fair share
+  __syncthreads();
+  for (int J = threadIdx.x; J < nc; J += blockDim.x) atomicAdd(&cnt[bucket(work(J))], 1);
   __syncthreads();
   if (threadIdx.x == 0) {
     int s = 0;
-    for (int k = 0; k < 32; ++k) {
+    for (int k = 0; k < NB; ++k) {
       off[k] = s;
       s += cnt[k];
     }
   }
   __syncthreads();
-  for (int J = threadIdx.x; J < nc; J += blockDim.x) order[atomicAdd(&off[bucket(J)], 1)] = J;
+  for (int J = threadIdx.x; J < nc; J += blockDim.x) order[atomicAdd(&off[bucket(work(J))], 1)] = J;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // the leading cells at or above the threshold go to clusters
+    int k = 0;
+    const int lim = min(nc, min(kMaxBig, a.max_big));
+    while (k < lim && work(order[k]) >= s_thr) ++k;
+    *nbig = k;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1129,14 +1225,19 @@ cudaError_t launch_gather(const SweepArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_order(const SweepArgs& a, int32_t* order, cudaStream_t s) {
-  k_order<<<1, 1024, 0, s>>>(a, order);
+cudaError_t launch_order(const SweepArgs& a, int32_t* order, int* nbig, cudaStream_t s) {
+  k_order<<<1, 1024, 0, s>>>(a, order, nbig);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sinkhorn(const SweepArgs& a, int threads, cudaStream_t s) {
   if (threads != 64 && threads != 128 && threads != 256) threads = 128;
   k_sinkhorn<<<a.ncells, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sinkhorn_cluster(const SweepArgs& a, cudaStream_t s) {
+  k_sinkhorn_cluster<<<kMaxBig * kClusterCTAs, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

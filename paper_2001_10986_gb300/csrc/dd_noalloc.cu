@@ -266,6 +266,8 @@ extern "C" dd_status dd_solve_cell_noalloc(const double* mu, int32_t b, double s
   a.cell_status = &S->cell_status - q.J;
   a.err_flag = &S->err_flag;
   a.order = &S->order;
+  a.nbig = nullptr;
+  a.max_big = 0;
   a.iters_hist = nullptr;
   a.trace_cell = -1;
   a.trace = nullptr;

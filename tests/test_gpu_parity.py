@@ -129,10 +129,12 @@ def ref32():
     return mu, nu, sched, odd.run_schedule(mu, nu, 4, 1, sched, odd.Params(err=1e-10))
 
 
-@pytest.mark.parametrize("threads", [64, 128, 256])
-def test_threads_per_cell(lib, ref32, threads):
+@pytest.mark.parametrize("threads,clusters", [(64, 0), (128, 0), (256, 0), (128, 4), (128, 32)])
+def test_threads_and_clusters(lib, ref32, threads, clusters):
+    # per-CTA cell solves with 64/128/256 threads, and cluster solves of the
+    # 4 or all largest cells (8 CTAs sharing one cell)
     mu, nu, sched, ref = ref32
-    g = lib.DD(mu, nu, 4, 1, sched, err_tol=1e-7, threads_per_cell=threads)
+    g = lib.DD(mu, nu, 4, 1, sched, err_tol=1e-7, threads_per_cell=threads, max_cluster_cells=clusters)
     g.run_schedule()
     rp, col, val = g.basic_marginals()
     cost, _, _ = g.cost(with_y=False)
