@@ -74,9 +74,9 @@ typedef struct {
   int32_t threads_per_cell; /* CUDA threads per composite cell (64, 128 or
                             256); 0 = library choice. Default 0.               */
   int32_t max_cluster_cells; /* at most this many of the cells with the
-                            largest predicted work (≥ half of one SM's share)
-                            are solved by a cluster of 8 CTAs each; 0 = none,
-                            −1 = library default (32).                         */
+                            largest predicted work (≥ a quarter of one SM's
+                            share) are solved by a cluster of 8 CTAs each;
+                            0 = none, −1 = library default (128).              */
   void* stream;          /* cudaStream_t to run on; NULL = a stream owned by
                             the context.                                       */
   uint64_t debug_flags;  /* bit 0: synchronise and check after every kernel;

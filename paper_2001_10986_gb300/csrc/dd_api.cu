@@ -315,7 +315,7 @@ SweepArgs sweep_args(dd_ctx* c, int part, double eps) {
   a.err_flag = c->err_flag;
   a.order = nullptr;
   a.nbig = nullptr;
-  a.max_big = c->opt.max_cluster_cells < 0 ? 32 : std::min(c->opt.max_cluster_cells, 32);
+  a.max_big = c->opt.max_cluster_cells < 0 ? 128 : std::min(c->opt.max_cluster_cells, 128);
   a.iters_hist = c->iters_hist[part];
   a.trace_cell = -1;
   a.trace = nullptr;

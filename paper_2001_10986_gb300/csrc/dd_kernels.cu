@@ -39,6 +39,37 @@ __device__ __forceinline__ float lg2(float x) {
   return y;
 }
 
+// packed pairs of FP32 values and the f32x2 arithmetic of sm_100-class GPUs
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 __device__ __forceinline__ int32_t pack_eta(int r, int c) {
   return (int32_t)((uint32_t)(r & 0xffff) | ((uint32_t)(c & 0xffff) << 16));
 }
@@ -244,7 +275,7 @@ __global__ void __launch_bounds__(256) k_gather(SweepArgs a) {
 constexpr int kMaxHW = 256;
 constexpr int kTraceLen = 512;
 constexpr int kClusterCTAs = 8;    // CTAs sharing one large cell
-constexpr int kMaxBig = 32;        // cells solved by clusters per launch
+constexpr int kMaxBig = 128;       // cells solved by clusters per launch
 constexpr float kTwoTau = 65536.0f;   // scalings leave the band [2^-16, 2^16] → absorb
 
 struct SinkSmem {
@@ -373,31 +404,46 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     sm.relax_off = 0;
   }
 
-  float Fr[16], ur[16];
   int arow[RPT];
+  float arowf[RPT];
 #pragma unroll
-  for (int r = 0; r < RPT; ++r) arow[r] = gid * RPT + r;
+  for (int r = 0; r < RPT; ++r) {
+    arow[r] = gid * RPT + r;
+    arowf[r] = (float)arow[r];
+  }
+  // The thread's 16 pixels as 8 packed pairs of neighbouring columns,
+  // pair q = r·W/2 + j holding columns 2j, 2j+1 of row r: the exponents and
+  // the sums over x and y use the f32x2 instructions (two FP32 lanes each).
+  constexpr int WP = W / 2;
+  unsigned long long F2[8], U2[8];
   auto load_Fu = [&]() {
 #pragma unroll
     for (int r = 0; r < RPT; ++r)
 #pragma unroll
-      for (int c = 0; c < W; ++c) {
-        const bool ok = arow[r] < g.H;
-        Fr[r * W + c] = ok ? sm.F[arow[r] * W + c] : kNegBig;
-        ur[r * W + c] = ok ? sm.u[arow[r] * W + c] : 0.f;
+      for (int j = 0; j < WP; ++j) {
+        const int q = r * WP + j;
+        if (arow[r] < g.H) {
+          F2[q] = pk2(sm.F[arow[r] * W + 2 * j], sm.F[arow[r] * W + 2 * j + 1]);
+          U2[q] = pk2(sm.u[arow[r] * W + 2 * j], sm.u[arow[r] * W + 2 * j + 1]);
+        } else {
+          F2[q] = pk2(kNegBig, kNegBig);
+          U2[q] = pk2(0.f, 0.f);
+        }
       }
   };
   load_Fu();
+  const unsigned long long K2 = pk2(kappa, kappa);
 
+  unsigned long long A2[8];
+  unsigned long long P2[8];
   float acc[16];
-  float pv[16];
   int it = 0;
   float errx = 0.f;
   bool converged = false, bad = false;
   for (;;) {
     // ---- Y-iteration and X-marginal of the new plan ----
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+    for (int q = 0; q < 8; ++q) A2[q] = 0ull;
     // per-y data of the next support point are loaded one step ahead
     int kn = rank * YS + slot;
     int kkn = kn < ny ? kn : ny - 1;
@@ -415,17 +461,20 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
       e_n = a.ws_eta[off + kkn];
       nu_n = a.ws_nu[off + kkn];
       if (it > 0) g_n = a.ws_g[off + kkn];
-      const int er = eta_r(e), ec = eta_c(e);
+      const float erf = (float)eta_r(e), ecf = (float)eta_c(e);
       const float nuy = (float)nuq * kFixToFloat;
-      float Cc[W], Rq[RPT];
+      // κ(c − η_c)² for the pairs of columns, κ(a − η_r)² for the rows
+      unsigned long long CC2[WP];
+      const unsigned long long EC2 = pk2(ecf, ecf);
 #pragma unroll
-      for (int c = 0; c < W; ++c) {
-        const float t = (float)(c - ec);
-        Cc[c] = kappa * t * t;
+      for (int j = 0; j < WP; ++j) {
+        const unsigned long long t2 = sub2(pk2((float)(2 * j), (float)(2 * j + 1)), EC2);
+        CC2[j] = mul2(mul2(K2, t2), t2);
       }
+      float Rq[RPT];
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
-        const float t = (float)(arow[r] - er);
+        const float t = arowf[r] - erf;
         Rq[r] = kappa * t * t;
       }
       float Gs;
@@ -433,58 +482,68 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
       if (it == 0) {
         float m = kNegBig;
 #pragma unroll
-        for (int r = 0; r < RPT; ++r)
+        for (int r = 0; r < RPT; ++r) {
+          const unsigned long long R2 = pk2(-Rq[r], -Rq[r]);
 #pragma unroll
-          for (int c = 0; c < W; ++c) m = fmaxf(m, Fr[r * W + c] - Rq[r] - Cc[c]);
+          for (int j = 0; j < WP; ++j) {
+            float e0, e1;
+            upk2(sub2(add2(F2[r * WP + j], R2), CC2[j]), e0, e1);
+            m = fmaxf(m, fmaxf(e0, e1));
+          }
+        }
         Gs = -group_max<G>(m);
       } else {
         Gs = g_pre;
       }
-      float s0 = 0.f, s1 = 0.f;
+      auto kernel_row = [&](float gs) {
+        unsigned long long S2 = 0ull;
 #pragma unroll
-      for (int r = 0; r < RPT; ++r) {
-        const float Ra = Gs - Rq[r];
+        for (int r = 0; r < RPT; ++r) {
+          const unsigned long long RA2 = pk2(gs - Rq[r], gs - Rq[r]);
 #pragma unroll
-        for (int c = 0; c < W; ++c) {
-          const float p = ex2(Fr[r * W + c] + Ra - Cc[c]);
-          pv[r * W + c] = p;
-          if (((r * W + c) & 1) == 0) s0 = fmaf(p, ur[r * W + c], s0);
-          else s1 = fmaf(p, ur[r * W + c], s1);
+          for (int j = 0; j < WP; ++j) {
+            const int q = r * WP + j;
+            float e0, e1;
+            upk2(sub2(add2(F2[q], RA2), CC2[j]), e0, e1);
+            P2[q] = pk2(ex2(e0), ex2(e1));
+            S2 = fma2(P2[q], U2[q], S2);
+          }
         }
-      }
-      float s = group_sum<G>(s0 + s1);
+        float s0, s1;
+        upk2(S2, s0, s1);
+        return group_sum<G>(s0 + s1);
+      };
+      float s = kernel_row(Gs);
       if (!(s > 1e-30f && s < 1e30f)) {
         // stabiliser too far off for this y: restart it from the running maximum
         float m = kNegBig;
 #pragma unroll
-        for (int r = 0; r < RPT; ++r)
-#pragma unroll
-          for (int c = 0; c < W; ++c)
-            m = fmaxf(m, Fr[r * W + c] + (ur[r * W + c] > 0.f ? lg2(ur[r * W + c]) : kNegBig) - Rq[r] - Cc[c]);
-        Gs = -group_max<G>(m);
-        s = 0.f;
-#pragma unroll
         for (int r = 0; r < RPT; ++r) {
-          const float Ra = Gs - Rq[r];
+          const unsigned long long R2 = pk2(-Rq[r], -Rq[r]);
 #pragma unroll
-          for (int c = 0; c < W; ++c) {
-            const float p = ex2(Fr[r * W + c] + Ra - Cc[c]);
-            pv[r * W + c] = p;
-            s = fmaf(p, ur[r * W + c], s);
+          for (int j = 0; j < WP; ++j) {
+            float e0, e1, u0, u1;
+            upk2(sub2(add2(F2[r * WP + j], R2), CC2[j]), e0, e1);
+            upk2(U2[r * WP + j], u0, u1);
+            m = fmaxf(m, fmaxf(u0 > 0.f ? e0 + lg2(u0) : kNegBig, u1 > 0.f ? e1 + lg2(u1) : kNegBig));
           }
         }
-        s = group_sum<G>(s);
+        Gs = -group_max<G>(m);
+        s = kernel_row(Gs);
         absorb = true;
       }
       // v = ν/s with IEEE division: the iteration map itself uses correctly
       // rounded arithmetic; only the frozen kernel K̃ uses ex2.approx
-      float v = valid ? nuy / s : 0.f;
+      const float v = valid ? nuy / s : 0.f;
       if (valid && (absorb || v > kTwoTau || v < 1.0f / kTwoTau)) {
         if (gid == 0) a.ws_g[off + k] = Gs + log2f(v);
       }
+      const unsigned long long V2 = pk2(v, v);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) acc[q] = fmaf(v, pv[q], acc[q]);
+      for (int q = 0; q < 8; ++q) A2[q] = fma2(V2, P2[q], A2[q]);
     }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) upk2(A2[q], acc[2 * q], acc[2 * q + 1]);
     // ---- reduce Σ_y K̃ v over the support ----
     {
       const int base = warp_reduce_scatter16<G>(acc, lane);
@@ -604,6 +663,15 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   }
 
   // ---- epilogue: final plan → fractions per basic cell, transport cost ----
+  float Fr[16], ur[16];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r)
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      const bool ok = arow[r] < g.H;
+      Fr[r * W + c] = ok ? sm.F[arow[r] * W + c] : kNegBig;
+      ur[r * W + c] = ok ? sm.u[arow[r] * W + c] : 0.f;
+    }
   const int nbas = g.nbr * g.nbc;
   const int bsh = __ffs(L.b) - 1;  // b is a power of two
   const int64_t tbase = 4 * off;
@@ -805,7 +873,7 @@ __global__ void __launch_bounds__(256) k_sinkhorn(SweepArgs a) {
 
 // a cluster of kClusterCTAs CTAs per cell, for the first nbig cells of the
 // launch order (largest predicted work)
-__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256) k_sinkhorn_cluster(SweepArgs a) {
+__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256, 2) k_sinkhorn_cluster(SweepArgs a) {
   __shared__ SinkSmem sm;
   const int c = blockIdx.x / kClusterCTAs;
   if (c >= *a.nbig) return;   // uniform over the cluster
@@ -843,7 +911,7 @@ __global__ void __launch_bounds__(1024) k_order(SweepArgs a, int32_t* order, int
   double tot = 0.0;
   for (int J = threadIdx.x; J < nc; J += blockDim.x) tot += work(J);
   tot = block_sum<double>(tot, dws);
-  if (threadIdx.x == 0) s_thr = tot / (2.0 * 152.0);   // half of one SM's fair share
+  if (threadIdx.x == 0) s_thr = tot / (4.0 * 152.0);   // a quarter of one SM's fair share
   __syncthreads();
   for (int J = threadIdx.x; J < nc; J += blockDim.x) atomicAdd(&cnt[bucket(work(J))], 1);
   __syncthreads();
