@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-cells", type=int, default=160)
     p.add_argument("--err", type=float, default=1e-6)
+    p.add_argument("--tpc", type=int, default=0, help="threads per cell solve (0: library choice)")
+    p.add_argument("--clusters", type=int, default=-1, help="max cells solved by 8-CTA clusters (-1: library choice)")
     return p.parse_args()
 
 
@@ -214,7 +216,8 @@ def run_cuda(args):
     stream = torch.cuda.current_stream()
 
     # ---- setup (untimed): coarse levels, refinement, warm-up sweeps at 2h² ----
-    g = dd.DD(mu, nu, b, L, sched, err_tol=args.err, stream=stream, debug_flags=2)
+    g = dd.DD(mu, nu, b, L, sched, err_tol=args.err, stream=stream, debug_flags=2,
+              threads_per_cell=args.tpc, max_cluster_cells=args.clusters)
     g.run_schedule()
     torch.cuda.synchronize()
     g.reset_profile()
@@ -256,6 +259,7 @@ def run_cuda(args):
                 "evals_per_launch": evals, "ms_per_launch": solve_ms,
                 "solve_share": prof.solve_ms / ms_total if ms_total > 0 else None,
                 "gather_ms_per_launch": prof.gather_ms / max(prof.gather_launches, 1),
+                "cluster_ms_per_launch": prof.cluster_ms / max(prof.solve_launches, 1),
                 "mean_sinkhorn_iters": prof.sinkhorn_iters / max(prof.cells, 1)}
 
     # ---- end to end through the C ABI from host buffers ----
@@ -264,7 +268,8 @@ def run_cuda(args):
         torch.cuda.synchronize()
         t = time.perf_counter()
         sched_e2e = syn.paper_schedule(n, L, args.steps)
-        h = dd.DD(mu, nu, b, L, sched_e2e, err_tol=args.err, stream=stream)
+        h = dd.DD(mu, nu, b, L, sched_e2e, err_tol=args.err, stream=stream, threads_per_cell=args.tpc,
+                  max_cluster_cells=args.clusters)
         h.run_schedule()
         c2, ex2_, ey2 = h.cost()
         rp, col, val = h.basic_marginals()

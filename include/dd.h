@@ -71,12 +71,12 @@ typedef struct {
                             mass. Default 1e-15.                               */
   int32_t max_iter;      /* cap on Sinkhorn Y-iterations per cell solve.
                             Default 2000.                                      */
-  int32_t threads_per_cell; /* CUDA threads per composite cell (64, 128 or
-                            256); 0 = library choice. Default 0.               */
+  int32_t threads_per_cell; /* CUDA threads per composite cell (32, 64, 128
+                            or 256); 0 = library choice. Default 0.            */
   int32_t max_cluster_cells; /* at most this many of the cells with the
-                            largest predicted work (≥ a quarter of one SM's
+                            largest predicted work (≥ an eighth of one SM's
                             share) are solved by a cluster of 8 CTAs each;
-                            0 = none, −1 = library default (128).              */
+                            0 = none, −1 = library default (256).              */
   void* stream;          /* cudaStream_t to run on; NULL = a stream owned by
                             the context.                                       */
   uint64_t debug_flags;  /* bit 0: synchronise and check after every kernel;
@@ -93,6 +93,8 @@ typedef struct {
   double solve_ms;           /* their summed duration (CUDA events)             */
   int64_t gather_launches;   /* launches of the Y-marginal gather kernel        */
   double gather_ms;          /* their summed duration (CUDA events)             */
+  double cluster_ms;         /* summed duration of the cluster cell solves,
+                                which run beside the per-CTA solves (events)    */
   double kernel_evals;       /* Σ over cell solves of |X_J|·N_y(J)·(iterations+1):
                                 kernel entries exp(…) evaluated                  */
   double sinkhorn_iters;     /* Σ over cell solves of the Sinkhorn iterations   */

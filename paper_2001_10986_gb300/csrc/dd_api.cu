@@ -109,9 +109,12 @@ struct dd_ctx {
   // debug trace of one cell (environment DD_TRACE_CELL="part,cell")
   int trace_part = -1, trace_cell = -1;
   float* trace_buf = nullptr;
+  unsigned long long* cell_times = nullptr;  // DD_TRACE_TIMES: per-cell solve times
+  bool serial_solve = false;                  // DD_SERIAL_SOLVE: cluster kernel before, not beside
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   cudaStream_t stream2 = nullptr;     // cluster solves run beside the per-CTA solves
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_c0 = nullptr, ev_c1 = nullptr;   // cluster kernel timing
   int* nbig = nullptr;
   int last_part = -1;
   bool need_init = false;  // level-0 product coupling not built yet
@@ -232,6 +235,8 @@ void alloc_level_buffers(dd_ctx* c, int l, float*& alpha0, float*& alpha1, int2*
   dev_alloc(c->cell_iters, ncell);
   dev_alloc(c->cell_status, ncell);
   dev_alloc(c->order, ncell);
+  if (std::getenv("DD_TRACE_TIMES")) dev_alloc(c->cell_times, 2 * ncell);
+  c->serial_solve = std::getenv("DD_SERIAL_SOLVE") != nullptr;
   for (int k = 0; k < 2; ++k) {
     dev_alloc(c->iters_hist[k], ncell);
     DD_CUDA(cudaMemsetAsync(c->iters_hist[k], 0, sizeof(int32_t) * ncell, c->stream));
@@ -315,10 +320,11 @@ SweepArgs sweep_args(dd_ctx* c, int part, double eps) {
   a.err_flag = c->err_flag;
   a.order = nullptr;
   a.nbig = nullptr;
-  a.max_big = c->opt.max_cluster_cells < 0 ? 128 : std::min(c->opt.max_cluster_cells, 128);
+  a.max_big = c->opt.max_cluster_cells < 0 ? 256 : std::min(c->opt.max_cluster_cells, 256);
   a.iters_hist = c->iters_hist[part];
   a.trace_cell = -1;
   a.trace = nullptr;
+  a.cell_times = c->cell_times;
   if (c->trace_buf && c->trace_part == part) {
     a.trace_cell = c->trace_cell;
     a.trace = c->trace_buf;
@@ -328,7 +334,7 @@ SweepArgs sweep_args(dd_ctx* c, int part, double eps) {
 
 int threads_per_cell(dd_ctx* c) {
   const int t = c->opt.threads_per_cell;
-  return (t == 64 || t == 128 || t == 256) ? t : 128;
+  return (t == 32 || t == 64 || t == 128 || t == 256) ? t : 128;
 }
 
 void half_sweep(dd_ctx* c, int part, double eps) {
@@ -344,17 +350,32 @@ void half_sweep(dd_ctx* c, int part, double eps) {
   if (timing) DD_CUDA(cudaEventRecord(c->ev[0], c->stream));
   DD_CUDA(launch_gather(a, c->stream));
   check_debug(c, "gather");
+  std::vector<int32_t> pred_copy;
+  if (c->cell_times && std::getenv("DD_TRACE_TIMES_FILE")) {
+    pred_copy.resize(a.ncells);
+    DD_CUDA(cudaMemcpyAsync(pred_copy.data(), c->iters_hist[part], 4 * (size_t)a.ncells, cudaMemcpyDeviceToHost,
+                            c->stream));
+  }
   DD_CUDA(launch_order(a, c->order, c->nbig, c->stream));
   a.order = c->order;
   a.nbig = c->nbig;
   if (timing) DD_CUDA(cudaEventRecord(c->ev[1], c->stream));
   // the largest cells go to clusters on a second stream, the rest run beside them
-  DD_CUDA(cudaEventRecord(c->ev_fork, c->stream));
-  DD_CUDA(cudaStreamWaitEvent(c->stream2, c->ev_fork, 0));
-  DD_CUDA(launch_sinkhorn_cluster(a, c->stream2));
-  DD_CUDA(cudaEventRecord(c->ev_join, c->stream2));
-  DD_CUDA(launch_sinkhorn(a, threads_per_cell(c), c->stream));
-  DD_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  if (c->serial_solve) {
+    if (timing) DD_CUDA(cudaEventRecord(c->ev_c0, c->stream));
+    DD_CUDA(launch_sinkhorn_cluster(a, c->stream));
+    if (timing) DD_CUDA(cudaEventRecord(c->ev_c1, c->stream));
+    DD_CUDA(launch_sinkhorn(a, threads_per_cell(c), c->stream));
+  } else {
+    DD_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+    DD_CUDA(cudaStreamWaitEvent(c->stream2, c->ev_fork, 0));
+    if (timing) DD_CUDA(cudaEventRecord(c->ev_c0, c->stream2));
+    DD_CUDA(launch_sinkhorn_cluster(a, c->stream2));
+    if (timing) DD_CUDA(cudaEventRecord(c->ev_c1, c->stream2));
+    DD_CUDA(cudaEventRecord(c->ev_join, c->stream2));
+    DD_CUDA(launch_sinkhorn(a, threads_per_cell(c), c->stream));
+    DD_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  }
   check_debug(c, "sinkhorn");
   if (timing) DD_CUDA(cudaEventRecord(c->ev[2], c->stream));
   DD_CUDA(launch_row_scan(c->row_cnt, c->rp[other], c->tile, nrows, c->stream));
@@ -389,6 +410,21 @@ void half_sweep(dd_ctx* c, int part, double eps) {
   c->prof.kernel_evals += c->last_tot.kernel_evals;
   c->prof.sinkhorn_iters += (double)c->last_tot.iters_sum;
   c->prof.cells += a.ncells;
+  if (c->cell_times && std::getenv("DD_TRACE_TIMES_FILE")) {
+    const int nc = a.ncells;
+    std::vector<unsigned long long> t(2 * nc);
+    std::vector<int32_t> it(nc), ny(nc), pred(pred_copy);
+    pred.resize(nc);
+    DD_CUDA(cudaMemcpy(t.data(), c->cell_times, 16 * (size_t)nc, cudaMemcpyDeviceToHost));
+    DD_CUDA(cudaMemcpy(it.data(), c->cell_iters, 4 * (size_t)nc, cudaMemcpyDeviceToHost));
+    DD_CUDA(cudaMemcpy(ny.data(), c->cell_ny, 4 * (size_t)nc, cudaMemcpyDeviceToHost));
+    if (FILE* f = std::fopen(std::getenv("DD_TRACE_TIMES_FILE"), "a")) {
+      std::fprintf(f, "# half-sweep part %d level %d ncells %d\n", part, c->lev, nc);
+      for (int J = 0; J < nc; ++J)
+        std::fprintf(f, "%d %d %d %llu %llu %d\n", J, it[J], ny[J], t[2 * J], t[2 * J + 1], pred[J]);
+      std::fclose(f);
+    }
+  }
   if (a.trace) {
     std::vector<float> t(1024);
     DD_CUDA(cudaMemcpy(t.data(), c->trace_buf, 4096, cudaMemcpyDeviceToHost));
@@ -402,8 +438,11 @@ void half_sweep(dd_ctx* c, int part, double eps) {
     float g_ms = 0.f, s_ms = 0.f;
     DD_CUDA(cudaEventElapsedTime(&g_ms, c->ev[0], c->ev[1]));
     DD_CUDA(cudaEventElapsedTime(&s_ms, c->ev[1], c->ev[2]));
+    float c_ms = 0.f;
+    DD_CUDA(cudaEventElapsedTime(&c_ms, c->ev_c0, c->ev_c1));
     c->prof.gather_ms += g_ms;
     c->prof.solve_ms += s_ms;
+    c->prof.cluster_ms += c_ms;
   }
 }
 
@@ -616,7 +655,7 @@ void release(dd_ctx* c) {
   void* bufs[] = {c->ws_ytmp, c->ws_vtmp, c->ws_eta, c->ws_nu, c->ws_lognu, c->ws_g, c->tmp_col, c->tmp_val,
                   c->row_cnt, c->row_src, c->tile, c->cell_off, c->cell_ny, c->anchor_new, c->cell_cost,
                   c->cell_errx, c->cell_iters, c->cell_status, c->ydense, c->ws_counter, c->err_flag,
-                  c->totals, c->yerr, c->order, c->iters_hist[0], c->iters_hist[1], c->trace_buf, c->nbig};
+                  c->totals, c->yerr, c->order, c->iters_hist[0], c->iters_hist[1], c->trace_buf, c->nbig, c->cell_times};
   for (void* p : bufs) dev_free(p);
   if (c->h_tot) cudaFreeHost(c->h_tot);
   if (c->h_nnz) cudaFreeHost(c->h_nnz);
@@ -626,6 +665,8 @@ void release(dd_ctx* c) {
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_c0) cudaEventDestroy(c->ev_c0);
+  if (c->ev_c1) cudaEventDestroy(c->ev_c1);
   if (c->stream2) cudaStreamDestroy(c->stream2);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
@@ -772,9 +813,15 @@ dd_status dd_create(const double* mu, const double* nu, const dd_grid* grid, int
     DD_CUDA(cudaMallocHost((void**)&c->h_err, sizeof(int)));
     DD_CUDA(cudaMallocHost((void**)&c->h_yerr, sizeof(double)));
     for (int k = 0; k < 3; ++k) DD_CUDA(cudaEventCreate(&c->ev[k]));
-    DD_CUDA(cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking));
+    // cluster solves take the highest stream priority: when per-CTA solves
+    // retire, their SMs go to the waiting clusters first
+    int prio_least = 0, prio_greatest = 0;
+    DD_CUDA(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+    DD_CUDA(cudaStreamCreateWithPriority(&c->stream2, cudaStreamNonBlocking, prio_greatest));
     DD_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     DD_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    DD_CUDA(cudaEventCreate(&c->ev_c0));
+    DD_CUDA(cudaEventCreate(&c->ev_c1));
     dev_alloc(c->nbig, 1);
     if (const char* tr = std::getenv("DD_TRACE_CELL")) {
       if (std::sscanf(tr, "%d,%d", &c->trace_part, &c->trace_cell) == 2) {

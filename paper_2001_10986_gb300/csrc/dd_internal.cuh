@@ -115,10 +115,11 @@ struct SweepArgs {
   int* err_flag;
   const int32_t* order;     // launch order of the cells (NULL: natural order)
   const int* nbig;          // the first *nbig cells of `order` are solved by clusters (NULL: none)
-  int max_big;              // upper limit for *nbig (≤ 128)
+  int max_big;              // upper limit for *nbig (≤ 256)
   int32_t* iters_hist;      // iterations of each cell's last solve in this partition
   int trace_cell;           // debug: cell whose per-iteration error is recorded (-1: none)
   float* trace;             // debug: 2×512 floats (relative X-error, ω) per iteration
+  unsigned long long* cell_times;  // debug: per cell [start, end] in ns (NULL: off)
 };
 
 // kernel launchers (dd_kernels.cu)

@@ -40,6 +40,12 @@ __device__ __forceinline__ float lg2(float x) {
 }
 
 // packed pairs of FP32 values and the f32x2 arithmetic of sm_100-class GPUs
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
 __device__ __forceinline__ unsigned long long pk2(float a, float b) {
   unsigned long long r;
   asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
@@ -118,6 +124,23 @@ __device__ T block_sum(T v, T* ws) {
   T t = 0;
   for (int w = 0; w < nw; ++w) t += ws[w];
   __syncthreads();
+  return t;
+}
+
+// block sum with one barrier: ws holds two buffers of 32 used alternately, so
+// a buffer is rewritten only after every thread has passed the barrier of the
+// following call
+__device__ __forceinline__ float block_sum1(float v, float* ws, int& phase) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  float* buf = ws + 32 * phase;
+  if (lane == 0) buf[warp] = v;
+  __syncthreads();
+  float t = 0.f;
+  for (int w = 0; w < nw; ++w) t += buf[w];
+  phase ^= 1;
   return t;
 }
 
@@ -275,7 +298,9 @@ __global__ void __launch_bounds__(256) k_gather(SweepArgs a) {
 constexpr int kMaxHW = 256;
 constexpr int kTraceLen = 512;
 constexpr int kClusterCTAs = 8;    // CTAs sharing one large cell
-constexpr int kMaxBig = 128;       // cells solved by clusters per launch
+constexpr int kMaxBig = 256;       // cells solved by clusters per launch
+constexpr int kStageSmall = 2048;  // support points staged in shared memory per CTA (per-CTA solves)
+constexpr int kStageBig = 4096;    // … and per CTA of a cluster
 constexpr float kTwoTau = 65536.0f;   // scalings leave the band [2^-16, 2^16] → absorb
 
 struct SinkSmem {
@@ -287,14 +312,10 @@ struct SinkSmem {
   float PXp[kMaxHW];     // this CTA's partial Σ_y K̃ v (read by the other CTAs of a cluster)
   float red[8][kMaxHW];
   float fws[32];
+  float fws2[64];      // two buffers for single-barrier block sums
   int iws[32];
   unsigned long long uws[32];
   double dws[32];
-  float s_err;
-  int s_stop;
-  float omega;       // over-relaxation factor of the X-iteration
-  float e3, emin;    // error history for choosing / safeguarding omega
-  int relax_off;
   uint64_t q64[4];
   uint64_t w64[4];
   int nsur, ndef;
@@ -344,9 +365,10 @@ __device__ __forceinline__ int warp_reduce_scatter16(float (&v)[16], int lane) {
 // points k ≡ rank (mod CS) in blocks of YS, the X-marginal is summed over the
 // cluster through distributed shared memory, every CTA applies the same
 // X-iteration, and rank 0 alone runs the epilogue.
-template <int W, int G, int CS>
+// XI: pixels of the cell each thread updates in the X-iteration (≥ 256/NT)
+template <int W, int G, int CS, int XI>
 __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g, SinkSmem& sm,
-                              const int rank) {
+                              const int rank, float4* ys, const int ycap) {
   constexpr int RPT = 16 / W;
   constexpr int NV = G >= 2 ? G / 2 : 1;
   const LevelView& L = a.L;
@@ -375,7 +397,6 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   const float kappa = (float)(L.spacing * L.spacing / ((double)a.eps * 0.69314718055994530942));
   const int Dr = g.r0 - anc.x, Dc = g.c0 - anc.y;
   const int shr = anc.x - anc_old.x, shc = anc.y - anc_old.y;
-  const int kstep = CS * YS;
 
   // stabiliser F in the new frame, scalings u = 1
   for (int x = tid; x < HW; x += NT) {
@@ -397,12 +418,28 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   // Truncate leaves ‖ν_cell‖ ≤ ‖μ_J‖: the stopping test compares P_X π with μ
   // rescaled to ‖ν_cell‖ (the §6.2 rule when nothing was truncated)
   const float mscale = muJ > 0.f ? nuJ / muJ : 1.f;
-  if (tid == 0) {
-    sm.omega = 1.0f;
-    sm.e3 = 0.f;
-    sm.emin = 3.0e38f;
-    sm.relax_off = 0;
+  // over-relaxation state, identical in every thread
+  float omega = 1.0f, e3 = 0.f, emin = 3.0e38f;
+  bool relax_off = false;
+  int phase = 0;
+
+  // This CTA's share of the support: all of it, or a contiguous chunk per
+  // cluster rank. When it fits, the share is staged once in shared memory as
+  // {η, ν, G, −} per point (one 128-bit load per point in every pass); G
+  // changes only at absorptions, which also write it to global memory.
+  int ylo = 0, yhi = ny;
+  if constexpr (CS > 1) {
+    const int chunk = (ny + CS - 1) / CS;
+    ylo = min(ny, rank * chunk);
+    yhi = min(ny, ylo + chunk);
   }
+  const bool staged = (yhi - ylo) <= ycap;
+  if (staged) {
+    for (int k = ylo + tid; k < yhi; k += NT)
+      ys[k - ylo] = make_float4(__int_as_float(a.ws_eta[off + k]), (float)a.ws_nu[off + k] * kFixToFloat,
+                                0.f, 0.f);
+  }
+  __syncthreads();
 
   int arow[RPT];
   float arowf[RPT];
@@ -444,25 +481,23 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     // ---- Y-iteration and X-marginal of the new plan ----
 #pragma unroll
     for (int q = 0; q < 8; ++q) A2[q] = 0ull;
-    // per-y data of the next support point are loaded one step ahead
-    int kn = rank * YS + slot;
-    int kkn = kn < ny ? kn : ny - 1;
-    int32_t e_n = a.ws_eta[off + kkn];
-    uint64_t nu_n = a.ws_nu[off + kkn];
-    float g_n = it > 0 ? a.ws_g[off + kkn] : 0.f;
-    for (int k0 = rank * YS; k0 < ny; k0 += kstep) {
+    for (int k0 = ylo; k0 < yhi; k0 += YS) {
       const int k = k0 + slot;
-      const bool valid = k < ny;
-      const int32_t e = e_n;
-      const uint64_t nuq = nu_n;
-      const float g_pre = g_n;
-      kn = k + kstep;
-      kkn = kn < ny ? kn : ny - 1;
-      e_n = a.ws_eta[off + kkn];
-      nu_n = a.ws_nu[off + kkn];
-      if (it > 0) g_n = a.ws_g[off + kkn];
+      const bool valid = k < yhi;
+      const int kk = valid ? k : yhi - 1;
+      int32_t e;
+      float nuy, g_pre;
+      if (staged) {
+        const float4 yd = ys[kk - ylo];
+        e = __float_as_int(yd.x);
+        nuy = yd.y;
+        g_pre = yd.z;
+      } else {
+        e = a.ws_eta[off + kk];
+        nuy = (float)a.ws_nu[off + kk] * kFixToFloat;
+        g_pre = it > 0 ? a.ws_g[off + kk] : 0.f;
+      }
       const float erf = (float)eta_r(e), ecf = (float)eta_c(e);
-      const float nuy = (float)nuq * kFixToFloat;
       // κ(c − η_c)² for the pairs of columns, κ(a − η_r)² for the rows
       unsigned long long CC2[WP];
       const unsigned long long EC2 = pk2(ecf, ecf);
@@ -536,7 +571,11 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
       // rounded arithmetic; only the frozen kernel K̃ uses ex2.approx
       const float v = valid ? nuy / s : 0.f;
       if (valid && (absorb || v > kTwoTau || v < 1.0f / kTwoTau)) {
-        if (gid == 0) a.ws_g[off + k] = Gs + log2f(v);
+        if (gid == 0) {
+          const float gn = Gs + log2f(v);
+          a.ws_g[off + k] = gn;
+          if (staged) ys[k - ylo].z = gn;
+        }
       }
       const unsigned long long V2 = pk2(v, v);
 #pragma unroll
@@ -553,76 +592,87 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
       }
     }
     __syncthreads();
-    float ep = 0.f, erp = 0.f;
+    // X-marginal P_X π(x) = u(x)·Σ_y K̃ v for the pixels this thread updates
+    // (x = tid + i·NT), kept in registers until the X-iteration
     const int nw = NT >> 5;
-    for (int x = tid; x < HW; x += NT) {
-      float t = 0.f;
-      for (int w = 0; w < nw; ++w) t += sm.red[w][x];
-      sm.PXp[x] = t;
-    }
+    float pxl[XI];
+    float ep = 0.f;
     if constexpr (CS > 1) {
+      for (int x = tid; x < HW; x += NT) {
+        float t = 0.f;
+        for (int w = 0; w < nw; ++w) t += sm.red[w][x];
+        sm.PXp[x] = t;
+      }
       cg::this_cluster().sync();
-    } else {
-      __syncthreads();
-    }
-    for (int x = tid; x < HW; x += NT) {
-      float t;
-      if constexpr (CS > 1) {
-        cg::cluster_group cl = cg::this_cluster();
-        t = 0.f;
+      cg::cluster_group cl = cg::this_cluster();
 #pragma unroll
-        for (int r = 0; r < CS; ++r) t += cl.map_shared_rank(sm.PXp, r)[x];
-      } else {
-        t = sm.PXp[x];
+      for (int i = 0; i < XI; ++i) {
+        const int x = tid + i * NT;
+        if (x < HW) {
+          float t = 0.f;
+#pragma unroll
+          for (int r = 0; r < CS; ++r) t += cl.map_shared_rank(sm.PXp, r)[x];
+          pxl[i] = sm.u[x] * t;
+          ep += fabsf(pxl[i] - sm.mu[x] * mscale);
+        }
       }
-      const float px = sm.u[x] * t;
-      sm.PX[x] = px;
-      ep += fabsf(px - sm.mu[x] * mscale);
-      erp += fabsf(px - sm.mu[x]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < XI; ++i) {
+        const int x = tid + i * NT;
+        if (x < HW) {
+          float t = 0.f;
+          for (int w = 0; w < nw; ++w) t += sm.red[w][x];
+          pxl[i] = sm.u[x] * t;
+          ep += fabsf(pxl[i] - sm.mu[x] * mscale);
+        }
+      }
     }
-    if constexpr (CS > 1) cg::this_cluster().sync();  // remote reads done before PXp is rewritten
-    ep = block_sum(ep, sm.fws);
-    erp = block_sum(erp, sm.fws);
+    ep = block_sum1(ep, sm.fws2, phase);
     ++it;
-    if (tid == 0) {
-      int stop = 0;
-      if (!(ep == ep) || isinf(ep)) stop = 2;
-      else if (ep <= tol) stop = 1;
-      else if (it >= a.max_iter) stop = 3;
-      sm.s_stop = stop;
-      sm.s_err = erp;
-      // Over-relaxed X-iteration u ← u·(μ/P_X π)^ω (same fixed point, same
-      // stopping rule, always ending on a Y-iteration). ω follows from the
-      // contraction ρ of the plain iteration measured over iterations 3..6,
-      // ω = 2/(1+√(1−ρ)) capped at 1.8, and falls back to 1 for good when the
-      // error grows well above its running minimum.
-      if (it == 3) sm.e3 = ep;
-      if (it == 6 && !sm.relax_off && sm.e3 > 0.f) {
-        const float rho = cbrtf(ep / sm.e3);
-        if (rho > 0.5f && rho < 1.0f) sm.omega = fminf(1.8f, 2.0f / (1.0f + sqrtf(1.0f - rho)));
-      }
-      if (ep > 1.5f * sm.emin && sm.omega != 1.0f) {
-        sm.omega = 1.0f;
-        sm.relax_off = 1;
-      }
-      sm.emin = fminf(sm.emin, ep);
-      if (J == a.trace_cell && a.trace && it <= kTraceLen) {
-        a.trace[2 * (it - 1)] = ep / muJ;
-        a.trace[2 * (it - 1) + 1] = sm.omega;
-      }
+    // every thread takes the same decisions from the same ep
+    int stop = 0;
+    if (!(ep == ep) || isinf(ep)) stop = 2;
+    else if (ep <= tol) stop = 1;
+    else if (it >= a.max_iter) stop = 3;
+    // Over-relaxed X-iteration u ← u·(μ/P_X π)^ω (same fixed point, same
+    // stopping rule, always ending on a Y-iteration). ω follows from the
+    // contraction ρ of the plain iteration measured over iterations 3..6,
+    // ω = 2/(1+√(1−ρ)) capped at 1.8, and falls back to 1 for good when the
+    // error grows well above its running minimum.
+    if (it == 3) e3 = ep;
+    if (it == 6 && !relax_off && e3 > 0.f) {
+      const float rho = cbrtf(ep / e3);
+      if (rho > 0.5f && rho < 1.0f) omega = fminf(1.8f, 2.0f / (1.0f + sqrtf(1.0f - rho)));
     }
-    __syncthreads();
-    const int stop = sm.s_stop;
-    errx = sm.s_err;
+    if (ep > 1.5f * emin && omega != 1.0f) {
+      omega = 1.0f;
+      relax_off = true;
+    }
+    emin = fminf(emin, ep);
+    if (tid == 0 && rank == 0 && J == a.trace_cell && a.trace && it <= kTraceLen) {
+      a.trace[2 * (it - 1)] = ep / muJ;
+      a.trace[2 * (it - 1) + 1] = omega;
+    }
     if (stop) {
+      // the reported error is the unscaled Σ_x |P_X π − μ|
+      float erp = 0.f;
+#pragma unroll
+      for (int i = 0; i < XI; ++i) {
+        const int x = tid + i * NT;
+        if (x < HW) erp += fabsf(pxl[i] - sm.mu[x]);
+      }
+      errx = block_sum1(erp, sm.fws2, phase);
       converged = stop == 1;
       bad = stop == 2;
       break;
     }
     // ---- X-iteration u ← u·(μ/P_X π)^ω, absorbing large scalings into F ----
-    const float omega = sm.omega;
-    for (int x = tid; x < HW; x += NT) {
-      const float px = sm.PX[x];
+#pragma unroll
+    for (int i = 0; i < XI; ++i) {
+      const int x = tid + i * NT;
+      if (x >= HW) continue;
+      const float px = pxl[i];
       if (px > 1e-37f && px < 1e37f) {
         const float ratio = sm.mu[x] / px;
         const float un = sm.u[x] * (omega == 1.0f ? ratio : exp2f(omega * log2f(ratio)));
@@ -652,7 +702,13 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
         sm.u[x] = 1.0f;
       }
     }
-    __syncthreads();
+    // the whole cluster syncs here: the reads of PXp above are complete
+    // before any CTA overwrites it in the next iteration
+    if constexpr (CS > 1) {
+      cg::this_cluster().sync();
+    } else {
+      __syncthreads();
+    }
     load_Fu();
   }
   if constexpr (CS > 1) {
@@ -842,21 +898,21 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
 
 // the cell shape picks the instantiation (A cells share one shape, B has
 // corner and edge shapes)
-template <int CS>
-__device__ void solve_cell(const SweepArgs& a, int J, SinkSmem& sm, int rank) {
+template <int CS, int XI>
+__device__ void solve_cell(const SweepArgs& a, int J, SinkSmem& sm, int rank, float4* ys, int ycap) {
   const CellGeom g = cell_geom(a.part, J, a.L.nb, a.L.b);
   const int W = g.W, H = g.H;
-  if (W == 2) sinkhorn_cell<2, 1, CS>(a, J, g, sm, rank);
+  if (W == 2) sinkhorn_cell<2, 1, CS, XI>(a, J, g, sm, rank, ys, ycap);
   else if (W == 4) {
-    if (H <= 4) sinkhorn_cell<4, 1, CS>(a, J, g, sm, rank);
-    else sinkhorn_cell<4, 2, CS>(a, J, g, sm, rank);
+    if (H <= 4) sinkhorn_cell<4, 1, CS, XI>(a, J, g, sm, rank, ys, ycap);
+    else sinkhorn_cell<4, 2, CS, XI>(a, J, g, sm, rank, ys, ycap);
   } else if (W == 8) {
-    if (H <= 4) sinkhorn_cell<8, 2, CS>(a, J, g, sm, rank);
-    else if (H <= 8) sinkhorn_cell<8, 4, CS>(a, J, g, sm, rank);
-    else sinkhorn_cell<8, 8, CS>(a, J, g, sm, rank);
+    if (H <= 4) sinkhorn_cell<8, 2, CS, XI>(a, J, g, sm, rank, ys, ycap);
+    else if (H <= 8) sinkhorn_cell<8, 4, CS, XI>(a, J, g, sm, rank, ys, ycap);
+    else sinkhorn_cell<8, 8, CS, XI>(a, J, g, sm, rank, ys, ycap);
   } else {
-    if (H <= 8) sinkhorn_cell<16, 8, CS>(a, J, g, sm, rank);
-    else sinkhorn_cell<16, 16, CS>(a, J, g, sm, rank);
+    if (H <= 8) sinkhorn_cell<16, 8, CS, XI>(a, J, g, sm, rank, ys, ycap);
+    else sinkhorn_cell<16, 16, CS, XI>(a, J, g, sm, rank, ys, ycap);
   }
 }
 
@@ -868,7 +924,10 @@ __global__ void __launch_bounds__(256) k_sinkhorn(SweepArgs a) {
   if (pos >= a.ncells) return;
   const int J = a.order ? a.order[pos] : pos;
   if (*a.err_flag & 4) return;
-  solve_cell<1>(a, J, sm, 0);
+  extern __shared__ float4 ys_small[];
+  if (a.cell_times && threadIdx.x == 0) a.cell_times[2 * J] = globaltimer();
+  solve_cell<1, kMaxHW / 32>(a, J, sm, 0, ys_small, kStageSmall);
+  if (a.cell_times && threadIdx.x == 0) a.cell_times[2 * J + 1] = globaltimer();
 }
 
 // a cluster of kClusterCTAs CTAs per cell, for the first nbig cells of the
@@ -880,7 +939,10 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256, 2) k
   const int rank = (int)cg::this_cluster().block_rank();
   const int J = a.order[c];
   if (*a.err_flag & 4) return;
-  solve_cell<kClusterCTAs>(a, J, sm, rank);
+  extern __shared__ float4 ys_big[];
+  if (a.cell_times && threadIdx.x == 0 && rank == 0) a.cell_times[2 * J] = globaltimer();
+  solve_cell<kClusterCTAs, 1>(a, J, sm, rank, ys_big, kStageBig);
+  if (a.cell_times && threadIdx.x == 0 && rank == 0) a.cell_times[2 * J + 1] = globaltimer();
 }
 
 // ---------------------------------------------------------------------------
@@ -890,29 +952,33 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256, 2) k
 // sort over 32 logarithmic buckets, one CTA.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_order(SweepArgs a, int32_t* order, int* nbig) {
-  constexpr int NB = 64;
+  // buckets [0, 64): cells for clusters, [64, 128): cells for one CTA each;
+  // half-octave buckets of predicted work inside each class, heaviest first
+  constexpr int NB = 128;
   __shared__ int cnt[NB];
   __shared__ int off[NB];
   __shared__ double dws[32];
   __shared__ double s_thr;
   const int nc = a.ncells;
-  if (threadIdx.x < NB) cnt[threadIdx.x] = 0;
+  for (int k = threadIdx.x; k < NB; k += blockDim.x) cnt[k] = 0;
   auto work = [&](int J) {
     if (a.cell_off[J] < 0) return 1.0;
     const CellGeom g = cell_geom(a.part, J, a.L.nb, a.L.b);
     const int it = a.iters_hist ? max(a.iters_hist[J], 1) : 1;
     return (double)it * (double)max(a.cell_ny[J], 1) * (double)(g.H * g.W);
   };
-  auto bucket = [&](double w) {
-    // half-octave buckets, heavier cells first
-    const int b2 = (int)(2.0 * log2(fmax(w, 1.0)));
-    return NB - 1 - min(NB - 1, b2);
-  };
   double tot = 0.0;
   for (int J = threadIdx.x; J < nc; J += blockDim.x) tot += work(J);
   tot = block_sum<double>(tot, dws);
-  if (threadIdx.x == 0) s_thr = tot / (4.0 * 152.0);   // a quarter of one SM's fair share
+  // an eighth of one SM's fair share: a single CTA runs such a cell long
+  // enough to stretch the launch
+  if (threadIdx.x == 0) s_thr = a.max_big > 0 ? tot / (8.0 * 152.0) : 3.0e300;
   __syncthreads();
+  const double thr = s_thr;
+  auto bucket = [&](double w) {
+    const int b2 = min(63, (int)(2.0 * log2(fmax(w, 1.0))));
+    return (w >= thr ? 0 : 64) + 63 - b2;
+  };
   for (int J = threadIdx.x; J < nc; J += blockDim.x) atomicAdd(&cnt[bucket(work(J))], 1);
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -920,18 +986,11 @@ __global__ void __launch_bounds__(1024) k_order(SweepArgs a, int32_t* order, int
     for (int k = 0; k < NB; ++k) {
       off[k] = s;
       s += cnt[k];
+      if (k == 63) *nbig = min(s, min(kMaxBig, a.max_big));
     }
   }
   __syncthreads();
   for (int J = threadIdx.x; J < nc; J += blockDim.x) order[atomicAdd(&off[bucket(work(J))], 1)] = J;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    // the leading cells at or above the threshold go to clusters
-    int k = 0;
-    const int lim = min(nc, min(kMaxBig, a.max_big));
-    while (k < lim && work(order[k]) >= s_thr) ++k;
-    *nbig = k;
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1299,13 +1358,22 @@ cudaError_t launch_order(const SweepArgs& a, int32_t* order, int* nbig, cudaStre
 }
 
 cudaError_t launch_sinkhorn(const SweepArgs& a, int threads, cudaStream_t s) {
-  if (threads != 64 && threads != 128 && threads != 256) threads = 128;
-  k_sinkhorn<<<a.ncells, threads, 0, s>>>(a);
+  if (threads != 32 && threads != 64 && threads != 128 && threads != 256) threads = 128;
+  k_sinkhorn<<<a.ncells, threads, kStageSmall * sizeof(float4), s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sinkhorn_cluster(const SweepArgs& a, cudaStream_t s) {
-  k_sinkhorn_cluster<<<kMaxBig * kClusterCTAs, 256, 0, s>>>(a);
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    const cudaError_t e = cudaFuncSetAttribute(k_sinkhorn_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(kStageBig * sizeof(float4)));
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  k_sinkhorn_cluster<<<kMaxBig * kClusterCTAs, 256, kStageBig * sizeof(float4), s>>>(a);
   return cudaGetLastError();
 }
 

@@ -271,6 +271,7 @@ extern "C" dd_status dd_solve_cell_noalloc(const double* mu, int32_t b, double s
   a.iters_hist = nullptr;
   a.trace_cell = -1;
   a.trace = nullptr;
+  a.cell_times = nullptr;
   cudaError_t e = launch_sinkhorn(a, 128, st);
   if (e != cudaSuccess) return fail(std::string("launch: ") + cudaGetErrorString(e), DD_ERR_CUDA);
   k_noalloc_finish<<<1, 256, 0, st>>>(S, b, spacing, n_y, y_row, y_col, alpha, nu_basic);

@@ -41,7 +41,7 @@ class dd_sweep_stats(C.Structure):
 class dd_profile(C.Structure):
     _fields_ = [("launches", C.c_int64), ("half_sweeps", C.c_int64), ("solve_launches", C.c_int64),
                 ("solve_ms", C.c_double), ("gather_launches", C.c_int64), ("gather_ms", C.c_double),
-                ("kernel_evals", C.c_double), ("sinkhorn_iters", C.c_double), ("cells", C.c_int64)]
+                ("cluster_ms", C.c_double), ("kernel_evals", C.c_double), ("sinkhorn_iters", C.c_double), ("cells", C.c_int64)]
 
 
 class DDError(RuntimeError):
