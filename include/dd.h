@@ -234,7 +234,8 @@ dd_status dd_reset_profile(dd_ctx* ctx);
  * Limits: b ∈ {2,4,8}; 1 ≤ n_y ≤ 16384; larger inputs are rejected with
  * DD_ERR_ARG before any work is queued, and dd_last_error(NULL) says why.
  * The first call on a device resolves the address of the scratch array with
- * cudaGetSymbolAddress; make that first call before any stream capture
+ * cudaGetSymbolAddress and raises the cell-solve kernel's shared-memory limit
+ * with cudaFuncSetAttribute; make that first call before any stream capture
  * begins. Every call reuses the same array and leaves its own data in it;
  * calls that overlap on the GPU (other streams or host threads) race on it
  * and must be serialised by the caller. Errors: DD_ERR_ARG (sizes, NULL,

@@ -12,6 +12,7 @@
 //               next level.
 //
 // All kernels are plain launches; none of them waits on another CTA.
+#include <atomic>
 #include "dd_internal.cuh"
 
 #include <cooperative_groups.h>
@@ -304,6 +305,7 @@ constexpr int kStageBig = 4096;    // … and per CTA of a cluster
 constexpr float kTwoTau = 65536.0f;   // scalings leave the band [2^-16, 2^16] → absorb
 
 struct SinkSmem {
+  alignas(16) float WT[kMaxHW];   // 2^res·u of the separable split
   float F[kMaxHW];
   float u[kMaxHW];
   float l2mu[kMaxHW];
@@ -322,60 +324,95 @@ struct SinkSmem {
   int sur[4], def[4];
 };
 
+// lanes tid % 32 rounded down to a multiple of G … +G−1 form one group; a
+// group may take a branch the rest of the warp does not, so the shuffles name
+// only the group's lanes
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+  if constexpr (G >= 32) {
+    return 0xffffffffu;
+  } else {
+    return ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(unsigned)(G - 1));
+  }
+}
 template <int G>
 __device__ __forceinline__ float group_sum(float v) {
+  const unsigned mask = group_mask<G>();
 #pragma unroll
-  for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(mask, v, o);
   return v;
 }
 template <int G>
 __device__ __forceinline__ float group_max(float v) {
+  const unsigned mask = group_mask<G>();
 #pragma unroll
-  for (int o = 1; o < G; o <<= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 1; o < G; o <<= 1) v = fmaxf(v, __shfl_xor_sync(mask, v, o));
   return v;
 }
 
-// Sum v[0..15] over the lanes of a warp that share lane % G. Afterwards the
-// lane holds max(1, G/2) fully reduced values for chunk-local pixels
-// base + j; with G == 1 two lanes hold each value and only even lanes write.
-template <int G>
-__device__ __forceinline__ int warp_reduce_scatter16(float (&v)[16], int lane) {
-  int base = 0;
-#pragma unroll
-  for (int m = 16, cnt = 16; m >= G; m >>= 1) {
-    if (cnt > 1) {
-      const int half = cnt >> 1;
-      const bool up = (lane & m) != 0;
+// Sum v[0..N) over the lanes of a warp that share lane % G (all lanes take
+// part). Afterwards the lane holds ScatterShape<N, G>::nv fully reduced values,
+// for thread-local indices base + j; where fewer values than lanes remain,
+// several lanes hold the same values and only ScatterShape::writer lanes
+// store them.
+template <int M, int CNT, int G, int N>
+__device__ __forceinline__ void reduce_scatter_stage(float (&v)[N], int lane, int& base) {
+  if constexpr (M >= G) {
+    if constexpr (CNT > 1) {
+      constexpr int half = CNT / 2;
+      const bool up = (lane & M) != 0;
 #pragma unroll
       for (int j = 0; j < half; ++j) {
         const float send = up ? v[j] : v[j + half];
         const float keep = up ? v[j + half] : v[j];
-        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, M);
       }
       if (up) base += half;
-      cnt = half;
+      reduce_scatter_stage<M / 2, half, G, N>(v, lane, base);
     } else {
-      v[0] += __shfl_xor_sync(0xffffffffu, v[0], m);
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], M);
+      reduce_scatter_stage<M / 2, 1, G, N>(v, lane, base);
     }
   }
+}
+template <int N, int G>
+__device__ __forceinline__ int warp_reduce_scatter(float (&v)[N], int lane) {
+  int base = 0;
+  reduce_scatter_stage<16, N, G, N>(v, lane, base);
   return base;
 }
+constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
+template <int N, int G>
+struct ScatterShape {
+  static constexpr int stages = 5 - ilog2c(G);
+  static constexpr int lgN = ilog2c(N);
+  static constexpr int plain = stages > lgN ? stages - lgN : 0;
+  static constexpr int nv = stages >= lgN ? 1 : (N >> stages);
+  __device__ static bool writer(int lane) { return ((lane / G) & ((1 << plain) - 1)) == 0; }
+};
 
-// CS > 1: a cluster of CS CTAs shares one cell; CTA `rank` takes the support
-// points k ≡ rank (mod CS) in blocks of YS, the X-marginal is summed over the
-// cluster through distributed shared memory, every CTA applies the same
-// X-iteration, and rank 0 alone runs the epilogue.
+// largest |res| of the separable split of the stabiliser for which the
+// factorised kernel is used (see sinkhorn_cell)
+constexpr float kResMax = 24.0f;
+
+// H×W: the cell's shape in pixels. CS > 1: a cluster of CS CTAs shares one
+// cell; CTA `rank` takes a contiguous chunk of the support points, the
+// X-marginal is summed over the cluster through distributed shared memory,
+// every CTA applies the same X-iteration, and rank 0 alone runs the epilogue.
 // XI: pixels of the cell each thread updates in the X-iteration (≥ 256/NT)
-template <int W, int G, int CS, int XI>
+template <int H, int W, int CS, int XI>
 __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g, SinkSmem& sm,
                               const int rank, float4* ys, const int ycap) {
-  constexpr int RPT = 16 / W;
-  constexpr int NV = G >= 2 ? G / 2 : 1;
+  // iterations: a thread holds RM whole rows (at most 64 pixels) of the cell
+  // for one support point at a time; GM threads share a point
+  constexpr int RM = (H < 64 / W) ? H : 64 / W;
+  constexpr int GM = H / RM;
+  constexpr int PT = RM * W;
+  constexpr int WP = W / 2;
   const LevelView& L = a.L;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int NT = blockDim.x;
-  const int gid = tid % G, slot = tid / G, YS = NT / G;
-  const int HW = g.H * g.W;
+  const int HW = H * W;
 
   const int64_t off = a.cell_off[J];
   if (off < 0) {
@@ -441,158 +478,288 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   }
   __syncthreads();
 
-  int arow[RPT];
-  float arowf[RPT];
+  const int gm = tid % GM, slm = tid / GM, YSM = NT / GM;
+  const int row0 = gm * RM;
+  // Separable split of the stabiliser: F(r,c) = fr(r) + fc(c) + res(r,c) with
+  // fr(r) = F(r,c₀), fc(c) = F(r₀,c) − F(r₀,c₀). Because the cost is a sum of
+  // a row and a column term, the kernel entry 2^(F + G − κ|ξ−η|²) of a support
+  // point y factorises as 2^res(r,c) · ρ_y(r) · γ_y(c) with
+  //   γ_y(c) = 2^(fc(c) − κ(c−η_c)² − m_y),  m_y = max_c (fc(c) − κ(c−η_c)²),
+  //   ρ_y(r) = 2^(fr(r) + G(y) − κ(r−η_r)² + m_y),
+  // so a point costs H + W exponentials and two FMAs per pixel instead of H·W
+  // exponentials. Every term keeps the centred form (r−η_r)², (c−η_c)², so the
+  // rounding of the exponents is that of the unsplit form. The split is used
+  // while |res| ≤ kResMax on the whole cell: with the scalings u, v held in
+  // [2^-16, 2^16] the exponent of F + G − κ|ξ−η|² stays below 32, hence
+  // ρ_y ≤ 2^(32+kResMax), γ_y ≤ 1, and entries lost to an underflow of γ_y lie
+  // below 2^-78 of the largest entry of their row. Otherwise the iteration
+  // evaluates every entry with its own exponential.
+  int it = 0;
+  constexpr int rc0 = (H - 1) / 2, cc0 = (W - 1) / 2;
+  unsigned long long FC2[WP];        // fc, pairs of neighbouring columns
+  float FR[RM];                      // fr of the thread's rows
+  bool fact = false;
+  // 2^res·u into shared memory and the decision for this pass; F and u are
+  // final for the pass; contains the barrier before the Y-iteration
+  auto prepare = [&]() {
+    const float f00 = sm.F[rc0 * W + cc0];
+    bool ok = true;
+    for (int x = tid; x < HW; x += NT) {
+      const int r = x / W, c = x % W;
+      const float fc = sm.F[rc0 * W + c] - f00;
+      const float res = (sm.F[x] - sm.F[r * W + cc0]) - fc;
+      ok = ok && fabsf(res) <= kResMax;   // false on NaN
+      sm.WT[x] = ex2(res) * sm.u[x];
+    }
+    fact = __syncthreads_and(ok) != 0;
 #pragma unroll
-  for (int r = 0; r < RPT; ++r) {
-    arow[r] = gid * RPT + r;
-    arowf[r] = (float)arow[r];
-  }
-  // The thread's 16 pixels as 8 packed pairs of neighbouring columns,
-  // pair q = r·W/2 + j holding columns 2j, 2j+1 of row r: the exponents and
-  // the sums over x and y use the f32x2 instructions (two FP32 lanes each).
-  constexpr int WP = W / 2;
-  unsigned long long F2[8], U2[8];
-  auto load_Fu = [&]() {
+    for (int j = 0; j < WP; ++j)
+      FC2[j] = pk2(sm.F[rc0 * W + 2 * j] - f00, sm.F[rc0 * W + 2 * j + 1] - f00);
 #pragma unroll
-    for (int r = 0; r < RPT; ++r)
-#pragma unroll
-      for (int j = 0; j < WP; ++j) {
-        const int q = r * WP + j;
-        if (arow[r] < g.H) {
-          F2[q] = pk2(sm.F[arow[r] * W + 2 * j], sm.F[arow[r] * W + 2 * j + 1]);
-          U2[q] = pk2(sm.u[arow[r] * W + 2 * j], sm.u[arow[r] * W + 2 * j + 1]);
-        } else {
-          F2[q] = pk2(kNegBig, kNegBig);
-          U2[q] = pk2(0.f, 0.f);
-        }
-      }
+    for (int r = 0; r < RM; ++r) FR[r] = sm.F[(row0 + r) * W + cc0];
   };
-  load_Fu();
+  prepare();
+  const unsigned long long NK2 = pk2(-kappa, -kappa);
   const unsigned long long K2 = pk2(kappa, kappa);
 
-  unsigned long long A2[8];
-  unsigned long long P2[8];
-  float acc[16];
-  int it = 0;
+  // the unsplit pass: G threads per support point, RPT whole rows (at most
+  // 16 pixels) each, the entries of K̃ one exponential each
+  constexpr int RPT = (H < 16 / W) ? H : 16 / W;
+  constexpr int G = H / RPT;
+  constexpr int PJ = RPT * W;
+  const int gid = tid % G, slot = tid / G, YS = NT / G;
+
+  // a support point's record {η, ν, G} from the staging buffer or memory
+  auto load_y = [&](int kk, int32_t& e, float& nuy, float& g_pre) {
+    if (staged) {
+      const float4 yd = ys[kk - ylo];
+      e = __float_as_int(yd.x);
+      nuy = yd.y;
+      g_pre = yd.z;
+    } else {
+      e = a.ws_eta[off + kk];
+      nuy = (float)a.ws_nu[off + kk] * kFixToFloat;
+      g_pre = it > 0 ? a.ws_g[off + kk] : 0.f;
+    }
+  };
+  // a new stabiliser, or a scaling outside the band: G ← G + log2 v
+  auto store_g = [&](int k, float gs, float v) {
+    const float gn = gs + log2f(v);
+    a.ws_g[off + k] = gn;
+    if (staged) ys[k - ylo].z = gn;
+  };
+
   float errx = 0.f;
   bool converged = false, bad = false;
   for (;;) {
     // ---- Y-iteration and X-marginal of the new plan ----
+    if (fact) {
+      unsigned long long A2[RM * WP];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) A2[q] = 0ull;
-    for (int k0 = ylo; k0 < yhi; k0 += YS) {
-      const int k = k0 + slot;
-      const bool valid = k < yhi;
-      const int kk = valid ? k : yhi - 1;
-      int32_t e;
-      float nuy, g_pre;
-      if (staged) {
-        const float4 yd = ys[kk - ylo];
-        e = __float_as_int(yd.x);
-        nuy = yd.y;
-        g_pre = yd.z;
-      } else {
-        e = a.ws_eta[off + kk];
-        nuy = (float)a.ws_nu[off + kk] * kFixToFloat;
-        g_pre = it > 0 ? a.ws_g[off + kk] : 0.f;
-      }
-      const float erf = (float)eta_r(e), ecf = (float)eta_c(e);
-      // κ(c − η_c)² for the pairs of columns, κ(a − η_r)² for the rows
-      unsigned long long CC2[WP];
-      const unsigned long long EC2 = pk2(ecf, ecf);
+      for (int q = 0; q < RM * WP; ++q) A2[q] = 0ull;
+      for (int k0 = ylo; k0 < yhi; k0 += YSM) {
+        const int k = k0 + slm;
+        const bool valid = k < yhi;
+        int32_t e;
+        float nuy, g_pre;
+        load_y(valid ? k : yhi - 1, e, nuy, g_pre);
+        const float erf = (float)eta_r(e), ecf = (float)eta_c(e);
+        const unsigned long long EC2 = pk2(ecf, ecf);
+        // stabiliser G from the largest exponent over the cell (with the
+        // scalings u after the first pass)
+        auto restab = [&](bool with_u) {
+          float m = kNegBig;
+#pragma unroll 1
+          for (int r = 0; r < RM; ++r) {
+            const float tr = (float)(row0 + r) - erf;
 #pragma unroll
-      for (int j = 0; j < WP; ++j) {
-        const unsigned long long t2 = sub2(pk2((float)(2 * j), (float)(2 * j + 1)), EC2);
-        CC2[j] = mul2(mul2(K2, t2), t2);
-      }
-      float Rq[RPT];
-#pragma unroll
-      for (int r = 0; r < RPT; ++r) {
-        const float t = arowf[r] - erf;
-        Rq[r] = kappa * t * t;
-      }
-      float Gs;
-      bool absorb = (it == 0);
-      if (it == 0) {
-        float m = kNegBig;
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-          const unsigned long long R2 = pk2(-Rq[r], -Rq[r]);
+            for (int c = 0; c < W; ++c) {
+              const float tc = (float)c - ecf;
+              const int x = (row0 + r) * W + c;
+              const float ev = sm.F[x] - kappa * tr * tr - kappa * tc * tc;
+              const float uu = sm.u[x];
+              m = fmaxf(m, with_u ? (uu > 0.f ? ev + lg2(uu) : kNegBig) : ev);
+            }
+          }
+          return -group_max<GM>(m);
+        };
+        float Gs = (it == 0) ? restab(false) : g_pre;
+        bool absorb = (it == 0);
+        unsigned long long GA2[WP];
+        float rho[RM];
+        // s = Σ_x K̃(x,y) u(x) from the factors
+        auto fact_sum = [&](float gs) {
+          float ce[W];
+          float mc = kNegBig;
 #pragma unroll
           for (int j = 0; j < WP; ++j) {
-            float e0, e1;
-            upk2(sub2(add2(F2[r * WP + j], R2), CC2[j]), e0, e1);
-            m = fmaxf(m, fmaxf(e0, e1));
+            const unsigned long long t2 = sub2(pk2((float)(2 * j), (float)(2 * j + 1)), EC2);
+            upk2(fma2(mul2(NK2, t2), t2, FC2[j]), ce[2 * j], ce[2 * j + 1]);
+            mc = fmaxf(mc, fmaxf(ce[2 * j], ce[2 * j + 1]));
           }
+#pragma unroll
+          for (int j = 0; j < WP; ++j) GA2[j] = pk2(ex2(ce[2 * j] - mc), ex2(ce[2 * j + 1] - mc));
+          const float cy = gs + mc;
+          float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+          for (int r = 0; r < RM; ++r) {
+            const float tr = (float)(row0 + r) - erf;
+            rho[r] = ex2(FR[r] + cy - kappa * tr * tr);
+            unsigned long long T2 = 0ull;
+            if constexpr (W >= 4) {
+              const float4* wr = reinterpret_cast<const float4*>(&sm.WT[(row0 + r) * W]);
+#pragma unroll
+              for (int j4 = 0; j4 < W / 4; ++j4) {
+                const float4 w4 = wr[j4];
+                T2 = fma2(pk2(w4.x, w4.y), GA2[2 * j4], T2);
+                T2 = fma2(pk2(w4.z, w4.w), GA2[2 * j4 + 1], T2);
+              }
+            } else {
+              const float2 w2 = reinterpret_cast<const float2*>(&sm.WT[(row0 + r) * W])[0];
+              T2 = fma2(pk2(w2.x, w2.y), GA2[0], T2);
+            }
+            float t0, t1;
+            upk2(T2, t0, t1);
+            if (r & 1) s1 = fmaf(rho[r], t0 + t1, s1);
+            else s0 = fmaf(rho[r], t0 + t1, s0);
+          }
+          return group_sum<GM>(s0 + s1);
+        };
+        float s = fact_sum(Gs);
+        if (!(s > 1e-30f && s < 1e30f)) {
+          // stabiliser too far off for this y: restart it from the running maximum
+          Gs = restab(true);
+          s = fact_sum(Gs);
+          absorb = true;
         }
-        Gs = -group_max<G>(m);
-      } else {
-        Gs = g_pre;
+        // v = ν/s with IEEE division: the iteration map itself uses correctly
+        // rounded arithmetic; only the frozen kernel K̃ uses ex2.approx
+        const float v = valid ? nuy / s : 0.f;
+        if (valid && gm == 0 && (absorb || v > kTwoTau || v < 1.0f / kTwoTau)) store_g(k, Gs, v);
+        // Σ_y v ρ_y(r) γ_y(c); the factor 2^res·u is applied once per pass
+#pragma unroll
+        for (int r = 0; r < RM; ++r) {
+          const float vr = v * rho[r];
+          const unsigned long long VR2 = pk2(vr, vr);
+#pragma unroll
+          for (int j = 0; j < WP; ++j) A2[r * WP + j] = fma2(VR2, GA2[j], A2[r * WP + j]);
+        }
       }
-      auto kernel_row = [&](float gs) {
-        unsigned long long S2 = 0ull;
+      // P_X π on the thread's pixels, partial over its support points:
+      // (2^res·u)·Σ_y v ρ γ
+      float acc[PT];
+#pragma unroll
+      for (int r = 0; r < RM; ++r)
+#pragma unroll
+        for (int j = 0; j < WP; ++j) {
+          const int x = (row0 + r) * W + 2 * j;
+          upk2(mul2(A2[r * WP + j], pk2(sm.WT[x], sm.WT[x + 1])), acc[r * W + 2 * j], acc[r * W + 2 * j + 1]);
+        }
+      using SS = ScatterShape<PT, GM>;
+      const int base = warp_reduce_scatter<PT, GM>(acc, lane);
+      if (SS::writer(lane)) {
+#pragma unroll
+        for (int j = 0; j < SS::nv; ++j) sm.red[warp][gm * PT + base + j] = acc[j];
+      }
+    } else {
+      const int rj0 = gid * RPT;
+      unsigned long long F2[RPT * WP], U2[RPT * WP], P2[RPT * WP], A2[RPT * WP];
+#pragma unroll
+      for (int r = 0; r < RPT; ++r)
+#pragma unroll
+        for (int j = 0; j < WP; ++j) {
+          const int x = (rj0 + r) * W + 2 * j;
+          F2[r * WP + j] = pk2(sm.F[x], sm.F[x + 1]);
+          U2[r * WP + j] = pk2(sm.u[x], sm.u[x + 1]);
+          A2[r * WP + j] = 0ull;
+        }
+      for (int k0 = ylo; k0 < yhi; k0 += YS) {
+        const int k = k0 + slot;
+        const bool valid = k < yhi;
+        int32_t e;
+        float nuy, g_pre;
+        load_y(valid ? k : yhi - 1, e, nuy, g_pre);
+        const float erf = (float)eta_r(e), ecf = (float)eta_c(e);
+        // κ(c − η_c)² for the pairs of columns, κ(a − η_r)² for the rows
+        unsigned long long CC2[WP];
+        const unsigned long long EC2 = pk2(ecf, ecf);
+#pragma unroll
+        for (int j = 0; j < WP; ++j) {
+          const unsigned long long t2 = sub2(pk2((float)(2 * j), (float)(2 * j + 1)), EC2);
+          CC2[j] = mul2(mul2(K2, t2), t2);
+        }
+        float Rq[RPT];
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
-          const unsigned long long RA2 = pk2(gs - Rq[r], gs - Rq[r]);
+          const float t = (float)(rj0 + r) - erf;
+          Rq[r] = kappa * t * t;
+        }
+        auto row_max = [&](bool with_u) {
+          float m = kNegBig;
 #pragma unroll
-          for (int j = 0; j < WP; ++j) {
-            const int q = r * WP + j;
-            float e0, e1;
-            upk2(sub2(add2(F2[q], RA2), CC2[j]), e0, e1);
-            P2[q] = pk2(ex2(e0), ex2(e1));
-            S2 = fma2(P2[q], U2[q], S2);
+          for (int r = 0; r < RPT; ++r) {
+            const unsigned long long R2 = pk2(-Rq[r], -Rq[r]);
+#pragma unroll
+            for (int j = 0; j < WP; ++j) {
+              float e0, e1;
+              upk2(sub2(add2(F2[r * WP + j], R2), CC2[j]), e0, e1);
+              if (with_u) {
+                float u0, u1;
+                upk2(U2[r * WP + j], u0, u1);
+                e0 = u0 > 0.f ? e0 + lg2(u0) : kNegBig;
+                e1 = u1 > 0.f ? e1 + lg2(u1) : kNegBig;
+              }
+              m = fmaxf(m, fmaxf(e0, e1));
+            }
           }
-        }
-        float s0, s1;
-        upk2(S2, s0, s1);
-        return group_sum<G>(s0 + s1);
-      };
-      float s = kernel_row(Gs);
-      if (!(s > 1e-30f && s < 1e30f)) {
-        // stabiliser too far off for this y: restart it from the running maximum
-        float m = kNegBig;
+          return -group_max<G>(m);
+        };
+        float Gs = (it == 0) ? row_max(false) : g_pre;
+        bool absorb = (it == 0);
+        auto kernel_row = [&](float gs) {
+          unsigned long long S2 = 0ull;
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-          const unsigned long long R2 = pk2(-Rq[r], -Rq[r]);
+          for (int r = 0; r < RPT; ++r) {
+            const unsigned long long RA2 = pk2(gs - Rq[r], gs - Rq[r]);
 #pragma unroll
-          for (int j = 0; j < WP; ++j) {
-            float e0, e1, u0, u1;
-            upk2(sub2(add2(F2[r * WP + j], R2), CC2[j]), e0, e1);
-            upk2(U2[r * WP + j], u0, u1);
-            m = fmaxf(m, fmaxf(u0 > 0.f ? e0 + lg2(u0) : kNegBig, u1 > 0.f ? e1 + lg2(u1) : kNegBig));
+            for (int j = 0; j < WP; ++j) {
+              const int q = r * WP + j;
+              float e0, e1;
+              upk2(sub2(add2(F2[q], RA2), CC2[j]), e0, e1);
+              P2[q] = pk2(ex2(e0), ex2(e1));
+              S2 = fma2(P2[q], U2[q], S2);
+            }
           }
+          float s0, s1;
+          upk2(S2, s0, s1);
+          return group_sum<G>(s0 + s1);
+        };
+        float s = kernel_row(Gs);
+        if (!(s > 1e-30f && s < 1e30f)) {
+          // stabiliser too far off for this y: restart it from the running maximum
+          Gs = row_max(true);
+          s = kernel_row(Gs);
+          absorb = true;
         }
-        Gs = -group_max<G>(m);
-        s = kernel_row(Gs);
-        absorb = true;
+        const float v = valid ? nuy / s : 0.f;
+        if (valid && gid == 0 && (absorb || v > kTwoTau || v < 1.0f / kTwoTau)) store_g(k, Gs, v);
+        const unsigned long long V2 = pk2(v, v);
+#pragma unroll
+        for (int q = 0; q < RPT * WP; ++q) A2[q] = fma2(V2, P2[q], A2[q]);
       }
-      // v = ν/s with IEEE division: the iteration map itself uses correctly
-      // rounded arithmetic; only the frozen kernel K̃ uses ex2.approx
-      const float v = valid ? nuy / s : 0.f;
-      if (valid && (absorb || v > kTwoTau || v < 1.0f / kTwoTau)) {
-        if (gid == 0) {
-          const float gn = Gs + log2f(v);
-          a.ws_g[off + k] = gn;
-          if (staged) ys[k - ylo].z = gn;
-        }
-      }
-      const unsigned long long V2 = pk2(v, v);
+      // u·Σ_y K̃ v
+      float acc[PJ];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) A2[q] = fma2(V2, P2[q], A2[q]);
-    }
+      for (int q = 0; q < RPT * WP; ++q) upk2(mul2(A2[q], U2[q]), acc[2 * q], acc[2 * q + 1]);
+      using SS = ScatterShape<PJ, G>;
+      const int base = warp_reduce_scatter<PJ, G>(acc, lane);
+      if (SS::writer(lane)) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) upk2(A2[q], acc[2 * q], acc[2 * q + 1]);
-    // ---- reduce Σ_y K̃ v over the support ----
-    {
-      const int base = warp_reduce_scatter16<G>(acc, lane);
-      if (G > 1 || (lane & 1) == 0) {
-#pragma unroll
-        for (int j = 0; j < NV; ++j) sm.red[warp][gid * 16 + base + j] = acc[j];
+        for (int j = 0; j < SS::nv; ++j) sm.red[warp][gid * PJ + base + j] = acc[j];
       }
     }
     __syncthreads();
-    // X-marginal P_X π(x) = u(x)·Σ_y K̃ v for the pixels this thread updates
+    // X-marginal P_X π(x) for the pixels this thread updates
     // (x = tid + i·NT), kept in registers until the X-iteration
     const int nw = NT >> 5;
     float pxl[XI];
@@ -612,7 +779,7 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
           float t = 0.f;
 #pragma unroll
           for (int r = 0; r < CS; ++r) t += cl.map_shared_rank(sm.PXp, r)[x];
-          pxl[i] = sm.u[x] * t;
+          pxl[i] = t;
           ep += fabsf(pxl[i] - sm.mu[x] * mscale);
         }
       }
@@ -623,7 +790,7 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
         if (x < HW) {
           float t = 0.f;
           for (int w = 0; w < nw; ++w) t += sm.red[w][x];
-          pxl[i] = sm.u[x] * t;
+          pxl[i] = t;
           ep += fabsf(pxl[i] - sm.mu[x] * mscale);
         }
       }
@@ -709,7 +876,7 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     } else {
       __syncthreads();
     }
-    load_Fu();
+    prepare();
   }
   if constexpr (CS > 1) {
     // the stabilisers G written by the other CTAs must be visible to rank 0
@@ -719,7 +886,11 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   }
 
   // ---- epilogue: final plan → fractions per basic cell, transport cost ----
-  float Fr[16], ur[16];
+  // (the mapping of the unsplit pass: G threads per support point)
+  int arow[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) arow[r] = gid * RPT + r;
+  float Fr[RPT * W], ur[RPT * W];
 #pragma unroll
   for (int r = 0; r < RPT; ++r)
 #pragma unroll
@@ -902,22 +1073,26 @@ template <int CS, int XI>
 __device__ void solve_cell(const SweepArgs& a, int J, SinkSmem& sm, int rank, float4* ys, int ycap) {
   const CellGeom g = cell_geom(a.part, J, a.L.nb, a.L.b);
   const int W = g.W, H = g.H;
-  if (W == 2) sinkhorn_cell<2, 1, CS, XI>(a, J, g, sm, rank, ys, ycap);
-  else if (W == 4) {
-    if (H <= 4) sinkhorn_cell<4, 1, CS, XI>(a, J, g, sm, rank, ys, ycap);
-    else sinkhorn_cell<4, 2, CS, XI>(a, J, g, sm, rank, ys, ycap);
-  } else if (W == 8) {
-    if (H <= 4) sinkhorn_cell<8, 2, CS, XI>(a, J, g, sm, rank, ys, ycap);
-    else if (H <= 8) sinkhorn_cell<8, 4, CS, XI>(a, J, g, sm, rank, ys, ycap);
-    else sinkhorn_cell<8, 8, CS, XI>(a, J, g, sm, rank, ys, ycap);
+  // b ∈ {2, 4, 8}: cells are b or 2b pixels high and wide
+  if (H == 2) {
+    if (W == 2) sinkhorn_cell<2, 2, CS, XI>(a, J, g, sm, rank, ys, ycap);
+    else sinkhorn_cell<2, 4, CS, XI>(a, J, g, sm, rank, ys, ycap);
+  } else if (H == 4) {
+    if (W == 2) sinkhorn_cell<4, 2, CS, XI>(a, J, g, sm, rank, ys, ycap);
+    else if (W == 4) sinkhorn_cell<4, 4, CS, XI>(a, J, g, sm, rank, ys, ycap);
+    else sinkhorn_cell<4, 8, CS, XI>(a, J, g, sm, rank, ys, ycap);
+  } else if (H == 8) {
+    if (W == 4) sinkhorn_cell<8, 4, CS, XI>(a, J, g, sm, rank, ys, ycap);
+    else if (W == 8) sinkhorn_cell<8, 8, CS, XI>(a, J, g, sm, rank, ys, ycap);
+    else sinkhorn_cell<8, 16, CS, XI>(a, J, g, sm, rank, ys, ycap);
   } else {
-    if (H <= 8) sinkhorn_cell<16, 8, CS, XI>(a, J, g, sm, rank, ys, ycap);
+    if (W == 8) sinkhorn_cell<16, 8, CS, XI>(a, J, g, sm, rank, ys, ycap);
     else sinkhorn_cell<16, 16, CS, XI>(a, J, g, sm, rank, ys, ycap);
   }
 }
 
 // one CTA per cell, for the cells after the first nbig of the launch order
-__global__ void __launch_bounds__(256) k_sinkhorn(SweepArgs a) {
+__global__ void __maxnreg__(168) k_sinkhorn(SweepArgs a) {
   __shared__ SinkSmem sm;
   const int nbig = a.nbig ? *a.nbig : 0;
   const int pos = nbig + blockIdx.x;
@@ -1357,22 +1532,33 @@ cudaError_t launch_order(const SweepArgs& a, int32_t* order, int* nbig, cudaStre
   return cudaGetLastError();
 }
 
+// opt in to more than 48 KB of shared memory per CTA, once per device (a
+// repeated or concurrent call only sets the same value again)
+template <typename K>
+static cudaError_t ensure_dyn_smem(K kernel, int bytes, std::atomic<bool>* done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool cached = dev >= 0 && dev < 64;
+  if (cached && done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && cached) done[dev].store(true, std::memory_order_release);
+  return e;
+}
+
 cudaError_t launch_sinkhorn(const SweepArgs& a, int threads, cudaStream_t s) {
+  static std::atomic<bool> done[64];
   if (threads != 32 && threads != 64 && threads != 128 && threads != 256) threads = 128;
+  const cudaError_t e = ensure_dyn_smem(k_sinkhorn, (int)(kStageSmall * sizeof(float4)), done);
+  if (e != cudaSuccess) return e;
   k_sinkhorn<<<a.ncells, threads, kStageSmall * sizeof(float4), s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sinkhorn_cluster(const SweepArgs& a, cudaStream_t s) {
-  static bool attr_set[64] = {false};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    const cudaError_t e = cudaFuncSetAttribute(k_sinkhorn_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)(kStageBig * sizeof(float4)));
-    if (e != cudaSuccess) return e;
-    attr_set[dev] = true;
-  }
+  static std::atomic<bool> done[64];
+  const cudaError_t e = ensure_dyn_smem(k_sinkhorn_cluster, (int)(kStageBig * sizeof(float4)), done);
+  if (e != cudaSuccess) return e;
   k_sinkhorn_cluster<<<kMaxBig * kClusterCTAs, 256, kStageBig * sizeof(float4), s>>>(a);
   return cudaGetLastError();
 }
