@@ -300,8 +300,15 @@ constexpr int kMaxHW = 256;
 constexpr int kTraceLen = 512;
 constexpr int kClusterCTAs = 8;    // CTAs sharing one large cell
 constexpr int kMaxBig = 256;       // cells solved by clusters per launch
-constexpr int kStageSmall = 2048;  // support points staged in shared memory per CTA (per-CTA solves)
-constexpr int kStageBig = 4096;    // … and per CTA of a cluster
+constexpr int kStageSmall = 1536;  // support points staged in shared memory per CTA (per-CTA solves)
+constexpr int kStageBig = 3840;    // … and per CTA of a cluster
+constexpr int kNewtonN = 64;       // pixels of a cell that takes Newton steps
+constexpr int kNewtonLd = kNewtonN + 1;
+// shared floats of the Newton step: the 64×65 matrix C, then M; a batch of
+// up to 64 rows z_y; the right-hand side / step
+constexpr int kNewtonZ = kNewtonN * kNewtonLd;
+constexpr int kNewtonB = kNewtonZ + 64 * kNewtonN;
+constexpr int kNewtonFloats = kNewtonB + kNewtonN;
 constexpr float kTwoTau = 65536.0f;   // scalings leave the band [2^-16, 2^16] → absorb
 
 struct SinkSmem {
@@ -395,6 +402,47 @@ struct ScatterShape {
 // factorised kernel is used (see sinkhorn_cell)
 constexpr float kResMax = 24.0f;
 
+// Σ_y z_y z_yᵀ over a batch of nys rows z_y (64 floats each, at nbuf +
+// kNewtonZ) added into this thread's 4×TC tile of C (stride kNewtonLd at
+// nbuf); 64·64/(4·TC) threads cover C
+template <int TC>
+__device__ __forceinline__ void hess_batch(float* nbuf, int nys, int tid) {
+  constexpr int TJ = kNewtonN / TC;
+  const int ti = tid / TJ, tj = tid % TJ;
+  const float* Z = nbuf + kNewtonZ;
+  unsigned long long C2[2 * TC];
+#pragma unroll
+  for (int q = 0; q < 2 * TC; ++q) C2[q] = 0ull;
+#pragma unroll 2
+  for (int yy = 0; yy < nys; ++yy) {
+    const float4 zi = *reinterpret_cast<const float4*>(Z + yy * kNewtonN + 4 * ti);
+    unsigned long long Jp[TC / 2];
+#pragma unroll
+    for (int c4 = 0; c4 < TC / 4; ++c4) {
+      const float4 zj = *reinterpret_cast<const float4*>(Z + yy * kNewtonN + TC * tj + 4 * c4);
+      Jp[2 * c4] = pk2(zj.x, zj.y);
+      Jp[2 * c4 + 1] = pk2(zj.z, zj.w);
+    }
+    const float zr[4] = {zi.x, zi.y, zi.z, zi.w};
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const unsigned long long I2 = pk2(zr[r], zr[r]);
+#pragma unroll
+      for (int q = 0; q < TC / 2; ++q) C2[r * (TC / 2) + q] = fma2(I2, Jp[q], C2[r * (TC / 2) + q]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < TC / 2; ++q) {
+      float c0, c1;
+      upk2(C2[r * (TC / 2) + q], c0, c1);
+      float* cp = nbuf + (4 * ti + r) * kNewtonLd + TC * tj + 2 * q;
+      cp[0] += c0;
+      cp[1] += c1;
+    }
+}
+
 // H×W: the cell's shape in pixels. CS > 1: a cluster of CS CTAs shares one
 // cell; CTA `rank` takes a contiguous chunk of the support points, the
 // X-marginal is summed over the cluster through distributed shared memory,
@@ -402,7 +450,7 @@ constexpr float kResMax = 24.0f;
 // XI: pixels of the cell each thread updates in the X-iteration (≥ 256/NT)
 template <int H, int W, int CS, int XI>
 __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g, SinkSmem& sm,
-                              const int rank, float4* ys, const int ycap) {
+                              const int rank, float4* ys, const int ycap, float* nbuf) {
   // iterations: a thread holds RM whole rows (at most 64 pixels) of the cell
   // for one support point at a time; GM threads share a point
   constexpr int RM = (H < 64 / W) ? H : 64 / W;
@@ -459,6 +507,17 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   float omega = 1.0f, e3 = 0.f, emin = 3.0e38f;
   bool relax_off = false;
   int phase = 0;
+  // Newton steps for the X-iteration (cells of at most 64 pixels, CTAs of 128
+  // or 256 threads, at most 64 support points per pass, nbuf given):
+  // `newton` = this pass also accumulates the Hessian and the X-iteration
+  // after it is a Newton step. A cell of fewer pixels uses the leading HW
+  // rows and columns of the 64×64 system, the rest being the identity.
+  constexpr bool kNewtonShape = (H * W <= kNewtonN);
+  constexpr int GJ = H / ((H < 16 / W) ? H : 16 / W);   // threads per point in the unsplit pass
+  const bool newton_ok = kNewtonShape && nbuf != nullptr && (NT == 256 || (CS == 1 && NT == 128)) &&
+                         NT / GJ <= 64;
+  bool newton = false, newton_off = false;
+  float ep_before = 0.f, e_mark = 0.f;
 
   // This CTA's share of the support: all of it, or a contiguous chunk per
   // cluster rank. When it fits, the share is staged once in shared memory as
@@ -549,11 +608,107 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     if (staged) ys[k - ylo].z = gn;
   };
 
+  bool stepped = false;
+  // Newton direction from the C of the last pass (each CTA's partial in its
+  // nbuf): every CTA of the cluster sums the partials in the same order and
+  // solves the same system, so all hold the same δ (in nbuf after the
+  // matrix). False if a pivot is not positive or δ is not finite.
+  auto newton_x_step = [&](float px_own) -> bool {
+    if constexpr (kNewtonShape) {
+      float* M = nbuf;
+      float* bv = nbuf + kNewtonB;
+      const float lam = nuJ / (float)(HW * HW);
+      const int tc = NT == 256 ? 4 : 8, tjn = kNewtonN / tc;
+      const int ti = tid / tjn, tj = tid % tjn;
+      if constexpr (CS > 1) {
+        // C summed over the CTAs of the cluster, tile by tile, in rank order
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        float ct[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) ct[q] = 0.f;
+#pragma unroll 1
+        for (int rr = 0; rr < CS; ++rr) {
+          const float* pb = cl.map_shared_rank(nbuf, rr);
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) ct[4 * r + c] += pb[(4 * ti + r) * kNewtonLd + 4 * tj + c];
+        }
+        cl.sync();
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int i = 4 * ti + r, j = 4 * tj + c;
+            M[i * kNewtonLd + j] = (i >= HW || j >= HW) ? (i == j ? 1.f : 0.f)
+                                   : (i == j) ? 0.f : lam - ct[4 * r + c];
+          }
+      } else {
+        __syncthreads();
+        for (int r = 0; r < 4; ++r)
+          for (int c = 0; c < tc; ++c) {
+            const int i = 4 * ti + r, j = tc * tj + c;
+            M[i * kNewtonLd + j] = (i >= HW || j >= HW) ? (i == j ? 1.f : 0.f)
+                                   : (i == j) ? 0.f : lam - M[i * kNewtonLd + j];
+          }
+      }
+      __syncthreads();
+      if (tid < HW) {
+        // diagonal Σ_{j≠x} C(x,j) (C's row sums are P_X π), gauge λ, and a
+        // small regulariser for pixels that receive almost no mass
+        float rs = 0.f;
+        for (int j = 0; j < HW; ++j)
+          if (j != tid) rs += lam - M[tid * kNewtonLd + j];
+        M[tid * kNewtonLd + tid] = rs + lam + 1e-5f * px_own + 1e-7f * nuJ / (float)HW;
+        bv[tid] = sm.mu[tid] * mscale - px_own;
+      } else if (tid < kNewtonN) {
+        bv[tid] = 0.f;
+      }
+      __syncthreads();
+      // LDLᵀ in place: afterwards M(k,k) = D(k), M(i,k) = L(i,k)·D(k) for i > k
+      bool ok = true;
+      for (int k = 0; k < kNewtonN; ++k) {
+        const float d = M[k * kNewtonLd + k];
+        ok = ok && d > 0.f;
+        const int i = tid & (kNewtonN - 1);
+        if (ok && i > k) {
+          const float lik = M[i * kNewtonLd + k] / d;
+          const int jstep = NT >> 6;   // thread groups of 64, one per column residue
+          for (int j = k + 1 + (tid >> 6); j <= i; j += jstep) M[i * kNewtonLd + j] -= lik * M[j * kNewtonLd + k];
+        }
+        __syncthreads();
+      }
+      if (ok && warp == 0) {
+        for (int k = 0; k < kNewtonN; ++k) {
+          const float zk = bv[k] / M[k * kNewtonLd + k];
+          __syncwarp();
+          for (int i = lane; i < kNewtonN; i += 32)
+            if (i > k) bv[i] -= M[i * kNewtonLd + k] * zk;
+          __syncwarp();
+        }
+        for (int i = lane; i < kNewtonN; i += 32) bv[i] /= M[i * kNewtonLd + i];
+        __syncwarp();
+        for (int k = kNewtonN - 1; k >= 0; --k) {
+          const float dk = bv[k];
+          __syncwarp();
+          for (int i = lane; i < k; i += 32) bv[i] -= (M[k * kNewtonLd + i] / M[i * kNewtonLd + i]) * dk;
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      const float dl = (ok && tid < kNewtonN) ? bv[tid] : 0.f;
+      return __syncthreads_and(ok && fabsf(dl) < 60.f) != 0;
+    } else {
+      (void)px_own;
+      return false;
+    }
+  };
   float errx = 0.f;
   bool converged = false, bad = false;
   for (;;) {
     // ---- Y-iteration and X-marginal of the new plan ----
-    if (fact) {
+    if (fact && !newton) {
       unsigned long long A2[RM * WP];
 #pragma unroll
       for (int q = 0; q < RM * WP; ++q) A2[q] = 0ull;
@@ -664,6 +819,20 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     } else {
       const int rj0 = gid * RPT;
       unsigned long long F2[RPT * WP], U2[RPT * WP], P2[RPT * WP], A2[RPT * WP];
+      if constexpr (kNewtonShape) {
+        if (newton) {
+          // C = Σ_y z_y z_yᵀ starts at zero; each thread clears its own tile
+          const int tc = NT == 256 ? 4 : 8, tjn = kNewtonN / tc;
+          const int ti = tid / tjn, tj = tid % tjn;
+          for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < tc; ++c) nbuf[(4 * ti + r) * kNewtonLd + tc * tj + c] = 0.f;
+          // the rows z_y have no entries beyond the cell's pixels
+          if constexpr (H * W < kNewtonN) {
+            constexpr int pad = kNewtonN - H * W;
+            for (int q = tid; q < 64 * pad; q += NT) nbuf[kNewtonZ + (q / pad) * kNewtonN + H * W + q % pad] = 0.f;
+          }
+        }
+      }
 #pragma unroll
       for (int r = 0; r < RPT; ++r)
 #pragma unroll
@@ -746,6 +915,22 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
         const unsigned long long V2 = pk2(v, v);
 #pragma unroll
         for (int q = 0; q < RPT * WP; ++q) A2[q] = fma2(V2, P2[q], A2[q]);
+        if constexpr (kNewtonShape) {
+          if (newton) {
+            // z_y(x) = √ν(y)·K̃(x,y)u(x)/s(y), so that Σ_y z_y(x) z_y(x') =
+            // Σ_y π(x,y)π(x',y)/ν(y); one row per support point of the batch
+            const float w = valid ? sqrtf(nuy) / s : 0.f;
+            const unsigned long long W2 = pk2(w, w);
+            unsigned long long* zrow =
+                reinterpret_cast<unsigned long long*>(nbuf + kNewtonZ + slot * kNewtonN + gid * PJ);
+#pragma unroll
+            for (int q = 0; q < RPT * WP; ++q) zrow[q] = mul2(mul2(P2[q], U2[q]), W2);
+            __syncthreads();
+            if (NT == 256) hess_batch<4>(nbuf, YS, tid);
+            else hess_batch<8>(nbuf, YS, tid);
+            __syncthreads();
+          }
+        }
       }
       // u·Σ_y K̃ v
       float acc[PJ];
@@ -808,9 +993,11 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     // ω = 2/(1+√(1−ρ)) capped at 1.8, and falls back to 1 for good when the
     // error grows well above its running minimum.
     if (it == 3) e3 = ep;
-    if (it == 6 && !relax_off && e3 > 0.f) {
+    float rho6 = 0.f;
+    if (it == 6 && e3 > 0.f) {
       const float rho = cbrtf(ep / e3);
-      if (rho > 0.5f && rho < 1.0f) omega = fminf(1.8f, 2.0f / (1.0f + sqrtf(1.0f - rho)));
+      rho6 = rho;
+      if (!relax_off && rho > 0.5f && rho < 1.0f) omega = fminf(1.8f, 2.0f / (1.0f + sqrtf(1.0f - rho)));
     }
     if (ep > 1.5f * emin && omega != 1.0f) {
       omega = 1.0f;
@@ -834,9 +1021,57 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
       bad = stop == 2;
       break;
     }
+    // ---- Newton X-iteration ----
+    // With the Y-iteration exact, P_X π depends on the scalings u alone, and
+    // its Jacobian in log u is M = diag(P_X π) − Σ_y π(·,y)π(·,y)ᵀ/ν(y), a
+    // graph Laplacian (M·1 = 0). The step solves (M + λ11ᵀ) δ = μ‖ν_cell‖/‖μ_J‖
+    // − P_X π and sets u ← u·e^δ. It has the plain iteration's fixed point and
+    // stopping rule, and converges in a few steps where the plain iteration
+    // needs hundreds (cells whose support spreads far). The decision to take
+    // it: contraction ρ > 0.75 over iterations 3..6, or less than a tenfold
+    // error reduction over 16 iterations; a step that does not lower the error
+    // turns it off for the rest of the solve.
+    bool newton_step = false;
+    if constexpr (kNewtonShape) {
+      if (newton) {
+        if (stepped && ep > ep_before) {
+          newton = false;
+          newton_off = true;
+        } else {
+          newton_step = newton_x_step(pxl[0]);
+          if (newton_step) {
+            ep_before = ep;
+            stepped = true;
+          } else {
+            newton = false;
+            newton_off = true;
+          }
+        }
+      }
+    }
+    if (!newton_step && newton_ok && !newton_off && !newton) {
+      if (it == 6 && rho6 > 0.75f) newton = true;
+      if (it > 6 && (it & 15) == 0) {
+        if (ep > 0.1f * e_mark) newton = true;
+        e_mark = ep;
+      }
+      if (it == 6) e_mark = ep;
+      stepped = false;
+    }
+    if (newton_step) {
+      if (tid < HW) {
+        const float un = sm.u[tid] * expf(nbuf[kNewtonB + tid]);
+        if (un > kTwoTau || un < 1.0f / kTwoTau) {
+          sm.F[tid] += log2f(un);
+          sm.u[tid] = 1.0f;
+        } else {
+          sm.u[tid] = un;
+        }
+      }
+    }
     // ---- X-iteration u ← u·(μ/P_X π)^ω, absorbing large scalings into F ----
 #pragma unroll
-    for (int i = 0; i < XI; ++i) {
+    for (int i = 0; i < XI && !newton_step; ++i) {
       const int x = tid + i * NT;
       if (x >= HW) continue;
       const float px = pxl[i];
@@ -1070,24 +1305,25 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
 // the cell shape picks the instantiation (A cells share one shape, B has
 // corner and edge shapes)
 template <int CS, int XI>
-__device__ void solve_cell(const SweepArgs& a, int J, SinkSmem& sm, int rank, float4* ys, int ycap) {
+__device__ void solve_cell(const SweepArgs& a, int J, SinkSmem& sm, int rank, float4* ys, int ycap,
+                           float* nbuf) {
   const CellGeom g = cell_geom(a.part, J, a.L.nb, a.L.b);
   const int W = g.W, H = g.H;
   // b ∈ {2, 4, 8}: cells are b or 2b pixels high and wide
   if (H == 2) {
-    if (W == 2) sinkhorn_cell<2, 2, CS, XI>(a, J, g, sm, rank, ys, ycap);
-    else sinkhorn_cell<2, 4, CS, XI>(a, J, g, sm, rank, ys, ycap);
+    if (W == 2) sinkhorn_cell<2, 2, CS, XI>(a, J, g, sm, rank, ys, ycap, nbuf);
+    else sinkhorn_cell<2, 4, CS, XI>(a, J, g, sm, rank, ys, ycap, nbuf);
   } else if (H == 4) {
-    if (W == 2) sinkhorn_cell<4, 2, CS, XI>(a, J, g, sm, rank, ys, ycap);
-    else if (W == 4) sinkhorn_cell<4, 4, CS, XI>(a, J, g, sm, rank, ys, ycap);
-    else sinkhorn_cell<4, 8, CS, XI>(a, J, g, sm, rank, ys, ycap);
+    if (W == 2) sinkhorn_cell<4, 2, CS, XI>(a, J, g, sm, rank, ys, ycap, nbuf);
+    else if (W == 4) sinkhorn_cell<4, 4, CS, XI>(a, J, g, sm, rank, ys, ycap, nbuf);
+    else sinkhorn_cell<4, 8, CS, XI>(a, J, g, sm, rank, ys, ycap, nbuf);
   } else if (H == 8) {
-    if (W == 4) sinkhorn_cell<8, 4, CS, XI>(a, J, g, sm, rank, ys, ycap);
-    else if (W == 8) sinkhorn_cell<8, 8, CS, XI>(a, J, g, sm, rank, ys, ycap);
-    else sinkhorn_cell<8, 16, CS, XI>(a, J, g, sm, rank, ys, ycap);
+    if (W == 4) sinkhorn_cell<8, 4, CS, XI>(a, J, g, sm, rank, ys, ycap, nbuf);
+    else if (W == 8) sinkhorn_cell<8, 8, CS, XI>(a, J, g, sm, rank, ys, ycap, nbuf);
+    else sinkhorn_cell<8, 16, CS, XI>(a, J, g, sm, rank, ys, ycap, nbuf);
   } else {
-    if (W == 8) sinkhorn_cell<16, 8, CS, XI>(a, J, g, sm, rank, ys, ycap);
-    else sinkhorn_cell<16, 16, CS, XI>(a, J, g, sm, rank, ys, ycap);
+    if (W == 8) sinkhorn_cell<16, 8, CS, XI>(a, J, g, sm, rank, ys, ycap, nbuf);
+    else sinkhorn_cell<16, 16, CS, XI>(a, J, g, sm, rank, ys, ycap, nbuf);
   }
 }
 
@@ -1101,7 +1337,8 @@ __global__ void __maxnreg__(168) k_sinkhorn(SweepArgs a) {
   if (*a.err_flag & 4) return;
   extern __shared__ float4 ys_small[];
   if (a.cell_times && threadIdx.x == 0) a.cell_times[2 * J] = globaltimer();
-  solve_cell<1, kMaxHW / 32>(a, J, sm, 0, ys_small, kStageSmall);
+  // dynamic shared memory: the staged support points, then the Newton buffer
+  solve_cell<1, kMaxHW / 32>(a, J, sm, 0, ys_small, kStageSmall, reinterpret_cast<float*>(ys_small + kStageSmall));
   if (a.cell_times && threadIdx.x == 0) a.cell_times[2 * J + 1] = globaltimer();
 }
 
@@ -1116,7 +1353,8 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256, 2) k
   if (*a.err_flag & 4) return;
   extern __shared__ float4 ys_big[];
   if (a.cell_times && threadIdx.x == 0 && rank == 0) a.cell_times[2 * J] = globaltimer();
-  solve_cell<kClusterCTAs, 1>(a, J, sm, rank, ys_big, kStageBig);
+  // dynamic shared memory: the staged support points, then the Newton buffer
+  solve_cell<kClusterCTAs, 1>(a, J, sm, rank, ys_big, kStageBig, reinterpret_cast<float*>(ys_big + kStageBig));
   if (a.cell_times && threadIdx.x == 0 && rank == 0) a.cell_times[2 * J + 1] = globaltimer();
 }
 
@@ -1549,17 +1787,19 @@ static cudaError_t ensure_dyn_smem(K kernel, int bytes, std::atomic<bool>* done)
 cudaError_t launch_sinkhorn(const SweepArgs& a, int threads, cudaStream_t s) {
   static std::atomic<bool> done[64];
   if (threads != 32 && threads != 64 && threads != 128 && threads != 256) threads = 128;
-  const cudaError_t e = ensure_dyn_smem(k_sinkhorn, (int)(kStageSmall * sizeof(float4)), done);
+  const int smem = (int)(kStageSmall * sizeof(float4) + kNewtonFloats * sizeof(float));
+  const cudaError_t e = ensure_dyn_smem(k_sinkhorn, smem, done);
   if (e != cudaSuccess) return e;
-  k_sinkhorn<<<a.ncells, threads, kStageSmall * sizeof(float4), s>>>(a);
+  k_sinkhorn<<<a.ncells, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sinkhorn_cluster(const SweepArgs& a, cudaStream_t s) {
   static std::atomic<bool> done[64];
-  const cudaError_t e = ensure_dyn_smem(k_sinkhorn_cluster, (int)(kStageBig * sizeof(float4)), done);
+  const int smem = (int)(kStageBig * sizeof(float4) + kNewtonFloats * sizeof(float));
+  const cudaError_t e = ensure_dyn_smem(k_sinkhorn_cluster, smem, done);
   if (e != cudaSuccess) return e;
-  k_sinkhorn_cluster<<<kMaxBig * kClusterCTAs, 256, kStageBig * sizeof(float4), s>>>(a);
+  k_sinkhorn_cluster<<<kMaxBig * kClusterCTAs, 256, smem, s>>>(a);
   return cudaGetLastError();
 }
 
