@@ -30,12 +30,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pixels·sweeps/s at 1024², plain DD"
 UNIT = "px·sweeps/s"
-# ex2 units per SM per clock, measured on this GPU (see the design notes)
-EX2_PER_CLK_PER_SM = 32
+# FP32 lanes per SM (FFMA per clock), SMs and the maximum SM clock of a GB300:
+# the ALU peak the cell-solve kernels are reported against
+FP32_LANES_PER_SM = 128
 NUM_SM = 152
 SM_MAX_MHZ = 2070.0
-# DRAM bytes per launch of the cell-solve kernel from the last ncu capture of
-# the current kernel (profiles/k_sinkhorn_gm1024_b4.md); None if not captured
+# algorithmic FP32 work of the cell solves:
+#  * every kernel entry of every Y-iteration: 2 FMAs (Σ_x K̃u for s(y) and
+#    Σ_y K̃v for the X-marginal);
+#  * every Newton X-iteration: the symmetric 64×64 Hessian, 64·65/2 FMAs per
+#    support point (the profile counts 64² per point).
+FMA_PER_ENTRY = 2.0
+HESS_SYM = 65.0 / 128.0
+# DRAM bytes per launch of the per-CTA cell-solve kernel from the last ncu
+# capture of the current kernel (profiles/); None if not captured
 SOLVE_TRAFFIC_BYTES = None
 
 
@@ -48,6 +56,7 @@ def parse():
     p.add_argument("--workload", default="gm1024_b4")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-ttc", action="store_true", help="skip the time-to-converged runs")
     p.add_argument("--cpu-cells", type=int, default=160)
     p.add_argument("--err", type=float, default=1e-6)
     p.add_argument("--tpc", type=int, default=0, help="threads per cell solve (0: library choice)")
@@ -191,6 +200,37 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def time_to_converged(dd, syn, mu, nu, w, args, stream, max_final_sweeps=400, **opts):
+    """Wall time from host images to a converged plan: dd_create, the whole
+    coarse-to-fine schedule, then sweeps at the final ε until one sweep
+    changes the FP64 transport cost by at most 1e-7 relative (the cell solves
+    hold the X-marginal error at ≤ Err·‖μ‖, the Y-marginal is exact). Each
+    check is a dd_cost call, i.e. one device→host read per sweep."""
+    import torch
+    n, b, L = w.n, w.b, w.levels
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    h = dd.DD(mu, nu, b, L, syn.paper_schedule(n, L, 1), err_tol=args.err, stream=stream,
+              threads_per_cell=args.tpc, max_cluster_cells=args.clusters, **opts)
+    h.run_schedule()
+    prev, _, _ = h.cost(with_y=False)
+    k, rel = 1, None
+    while k < max_final_sweeps:
+        h.sweep(1)
+        k += 1
+        cur, _, _ = h.cost(with_y=False)
+        rel = abs(cur - prev) / abs(cur)
+        prev = cur
+        if rel <= 1e-7:
+            break
+    cost, ex, ey = h.cost()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    h.close()
+    return {"seconds": dt, "final_sweeps": k, "last_rel_change": rel, "cost": cost, "err_x": ex, "err_y": ey,
+            "criterion": "relative cost change over one final-ε sweep <= 1e-7"}
+
+
 def run_cuda(args):
     import numpy as np
     import torch
@@ -248,18 +288,22 @@ def run_cuda(args):
     ms_max = float(t_rank.item())
     value = world * n * n * args.steps / (ms_max * 1e-3)
 
-    # ---- roofline of the cell-solve kernel (exp evaluations) ----
-    solve_ms = prof.solve_ms / max(prof.solve_launches, 1)
-    evals = prof.kernel_evals / max(prof.solve_launches, 1)
-    achieved = evals / (solve_ms * 1e-3) / 1e9
-    peak = NUM_SM * EX2_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
-    roofline = {"bound": "alu", "kernel": "k_sinkhorn", "achieved": achieved, "peak": peak,
-                "unit": "Gexp/s", "frac": achieved / peak, "traffic": SOLVE_TRAFFIC_BYTES,
-                "peak_source": f"{NUM_SM} SMs x {EX2_PER_CLK_PER_SM} ex2/clk/SM x {SM_MAX_MHZ:.0f} MHz",
-                "evals_per_launch": evals, "ms_per_launch": solve_ms,
+    # ---- roofline of the cell-solve kernels (FP32 ALU) ----
+    launches = max(prof.solve_launches, 1)
+    solve_ms = prof.solve_ms / launches
+    fma = (FMA_PER_ENTRY * prof.kernel_evals + HESS_SYM * prof.hessian_fma) / launches
+    achieved = 2.0 * fma / (solve_ms * 1e-3) / 1e12
+    peak = NUM_SM * FP32_LANES_PER_SM * 2.0 * SM_MAX_MHZ * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": "k_sinkhorn + k_sinkhorn_cluster (one half-sweep's cell solves)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": SOLVE_TRAFFIC_BYTES,
+                "peak_source": f"FP32 FMA: {NUM_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz "
+                               "(unit counts and maximum clock)",
+                "fma_per_launch": fma, "kernel_entries_per_launch": prof.kernel_evals / launches,
+                "newton_steps_per_launch": prof.newton_steps / launches, "ms_per_launch": solve_ms,
                 "solve_share": prof.solve_ms / ms_total if ms_total > 0 else None,
                 "gather_ms_per_launch": prof.gather_ms / max(prof.gather_launches, 1),
-                "cluster_ms_per_launch": prof.cluster_ms / max(prof.solve_launches, 1),
+                "cluster_ms_per_launch": prof.cluster_ms / launches,
                 "mean_sinkhorn_iters": prof.sinkhorn_iters / max(prof.cells, 1)}
 
     # ---- end to end through the C ABI from host buffers ----
@@ -284,6 +328,10 @@ def run_cuda(args):
                        f"px·sweeps over the finest-level sweeps / wall time",
                "seconds": dt}
 
+    ttc = None
+    if not args.no_ttc:
+        ttc = {"plain": time_to_converged(dd, syn, mu, nu, w, args, stream)}
+
     if rank != 0:
         if pg:
             pg.destroy_process_group()
@@ -297,7 +345,7 @@ def run_cuda(args):
            "config": {"workload": args.workload, "n": n, "b": b, "levels": L, "eps_final": eps,
                       "err_tol": args.err, "nnz": nnz0, "l2": "working set larger than L2 (CSR + workspace)",
                       "parallelism": f"replicas x{world} (independent image pairs)"},
-           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "time_to_converged": ttc,
            "gpu_launches": int(prof.launches), "clocks": clk.summary(),
            "quality": {"cost": cost, "err_x": ex, "err_y": ey, "max_iters_last": st.max_iters,
                        "mean_iters_last": st.mean_iters, "cells_not_converged_last": st.cells_not_converged}}

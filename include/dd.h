@@ -77,6 +77,10 @@ typedef struct {
                             largest predicted work (≥ an eighth of one SM's
                             share) are solved by a cluster of 8 CTAs each;
                             0 = none, −1 = library default (256).              */
+  int32_t x_newton;      /* 1: a cell of at most 64 pixels whose X-iteration
+                            contracts slowly switches to Newton X-iterations
+                            (same fixed point, same stopping rule); 0: plain
+                            Sinkhorn X-iterations only. Default 1.             */
   void* stream;          /* cudaStream_t to run on; NULL = a stream owned by
                             the context.                                       */
   uint64_t debug_flags;  /* bit 0: synchronise and check after every kernel;
@@ -99,6 +103,10 @@ typedef struct {
                                 kernel entries exp(…) evaluated                  */
   double sinkhorn_iters;     /* Σ over cell solves of the Sinkhorn iterations   */
   int64_t cells;             /* cell solves                                     */
+  int64_t newton_steps;      /* X-iterations taken as Newton steps (cells of at
+                                most 64 pixels whose iteration converges slowly) */
+  double hessian_fma;        /* FMAs of their Hessian accumulations,
+                                Σ over steps of 64²·N_y(J)                       */
 } dd_profile;
 
 /* Statistics of the last sweep run by dd_sweep / dd_run_schedule. */

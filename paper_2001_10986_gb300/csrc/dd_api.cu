@@ -88,6 +88,7 @@ struct dd_ctx {
   double* cell_cost = nullptr;
   double* cell_errx = nullptr;
   int32_t* cell_iters = nullptr;
+  int32_t* cell_newton = nullptr;
   int32_t* cell_status = nullptr;
   int32_t* order = nullptr;
   int32_t* iters_hist[2] = {nullptr, nullptr};
@@ -233,6 +234,7 @@ void alloc_level_buffers(dd_ctx* c, int l, float*& alpha0, float*& alpha1, int2*
   dev_alloc(c->cell_cost, ncell);
   dev_alloc(c->cell_errx, ncell);
   dev_alloc(c->cell_iters, ncell);
+  dev_alloc(c->cell_newton, ncell);
   dev_alloc(c->cell_status, ncell);
   dev_alloc(c->order, ncell);
   if (std::getenv("DD_TRACE_TIMES")) dev_alloc(c->cell_times, 2 * ncell);
@@ -316,11 +318,13 @@ SweepArgs sweep_args(dd_ctx* c, int part, double eps) {
   a.cell_cost = c->cell_cost;
   a.cell_errx = c->cell_errx;
   a.cell_iters = c->cell_iters;
+  a.cell_newton = c->cell_newton;
   a.cell_status = c->cell_status;
   a.err_flag = c->err_flag;
   a.order = nullptr;
   a.nbig = nullptr;
   a.max_big = c->opt.max_cluster_cells < 0 ? 256 : std::min(c->opt.max_cluster_cells, 256);
+  a.newton = c->opt.x_newton != 0;
   a.iters_hist = c->iters_hist[part];
   a.trace_cell = -1;
   a.trace = nullptr;
@@ -409,6 +413,8 @@ void half_sweep(dd_ctx* c, int part, double eps) {
   c->prof.gather_launches += 1;
   c->prof.kernel_evals += c->last_tot.kernel_evals;
   c->prof.sinkhorn_iters += (double)c->last_tot.iters_sum;
+  c->prof.newton_steps += c->last_tot.newton_steps;
+  c->prof.hessian_fma += c->last_tot.hessian_fma;
   c->prof.cells += a.ncells;
   if (c->cell_times && std::getenv("DD_TRACE_TIMES_FILE")) {
     const int nc = a.ncells;
@@ -654,7 +660,7 @@ void release(dd_ctx* c) {
   free_level(c->ld);
   void* bufs[] = {c->ws_ytmp, c->ws_vtmp, c->ws_eta, c->ws_nu, c->ws_lognu, c->ws_g, c->tmp_col, c->tmp_val,
                   c->row_cnt, c->row_src, c->tile, c->cell_off, c->cell_ny, c->anchor_new, c->cell_cost,
-                  c->cell_errx, c->cell_iters, c->cell_status, c->ydense, c->ws_counter, c->err_flag,
+                  c->cell_errx, c->cell_iters, c->cell_newton, c->cell_status, c->ydense, c->ws_counter, c->err_flag,
                   c->totals, c->yerr, c->order, c->iters_hist[0], c->iters_hist[1], c->trace_buf, c->nbig, c->cell_times};
   for (void* p : bufs) dev_free(p);
   if (c->h_tot) cudaFreeHost(c->h_tot);
@@ -742,6 +748,7 @@ void dd_options_default(dd_options* opt) {
   opt->max_iter = 2000;
   opt->threads_per_cell = 0;
   opt->max_cluster_cells = -1;
+  opt->x_newton = 1;
   opt->stream = nullptr;
   opt->debug_flags = 0;
 }

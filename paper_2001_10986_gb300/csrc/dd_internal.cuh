@@ -111,6 +111,8 @@ struct SweepArgs {
   double* cell_cost;
   double* cell_errx;
   int32_t* cell_iters;
+  int32_t* cell_newton;     // Newton X-iterations of each cell solve (nullable)
+  int newton;               // Newton X-iterations allowed
   int32_t* cell_status;     // bit0 not converged, bit1 non-finite, bit2 workspace overflow
   int* err_flag;
   const int32_t* order;     // launch order of the cells (NULL: natural order)
@@ -141,7 +143,9 @@ cudaError_t launch_init_product(LevelView L, int64_t* rp, int32_t* col, uint64_t
 struct SweepTotals {
   double cost, errx;
   double kernel_evals;       // Σ_J |X_J|·N_y·(iterations + 1)
+  double hessian_fma;        // Σ_J Newton steps · 64²·N_y
   long long iters_sum;
+  long long newton_steps;
   int iters_max, not_converged, nonfinite, overflow;
 };
 cudaError_t launch_reduce_cells(const SweepArgs& a, SweepTotals* out_dev, cudaStream_t s);

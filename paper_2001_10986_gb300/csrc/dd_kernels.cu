@@ -308,7 +308,9 @@ constexpr int kNewtonLd = kNewtonN + 1;
 // up to 64 rows z_y; the right-hand side / step
 constexpr int kNewtonZ = kNewtonN * kNewtonLd;
 constexpr int kNewtonB = kNewtonZ + 64 * kNewtonN;
-constexpr int kNewtonFloats = kNewtonB + kNewtonN;
+constexpr int kNewtonFloats = kNewtonB + kNewtonN + 1;
+// largest |δ| of one Newton step in log u; a longer step is scaled down
+constexpr float kNewtonMaxStep = 4.0f;
 constexpr float kTwoTau = 65536.0f;   // scalings leave the band [2^-16, 2^16] → absorb
 
 struct SinkSmem {
@@ -514,7 +516,7 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   // rows and columns of the 64×64 system, the rest being the identity.
   constexpr bool kNewtonShape = (H * W <= kNewtonN);
   constexpr int GJ = H / ((H < 16 / W) ? H : 16 / W);   // threads per point in the unsplit pass
-  const bool newton_ok = kNewtonShape && nbuf != nullptr && (NT == 256 || (CS == 1 && NT == 128)) &&
+  const bool newton_ok = kNewtonShape && a.newton && nbuf != nullptr && (NT == 256 || (CS == 1 && NT == 128)) &&
                          NT / GJ <= 64;
   bool newton = false, newton_off = false;
   float ep_before = 0.f, e_mark = 0.f;
@@ -609,11 +611,13 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   };
 
   bool stepped = false;
+  int nsteps = 0;
   // Newton direction from the C of the last pass (each CTA's partial in its
   // nbuf): every CTA of the cluster sums the partials in the same order and
   // solves the same system, so all hold the same δ (in nbuf after the
-  // matrix). False if a pivot is not positive or δ is not finite.
-  auto newton_x_step = [&](float px_own) -> bool {
+  // matrix). Returns the step length in (0, 1], or −1 if a pivot is not
+  // positive or δ is not finite.
+  auto newton_x_step = [&](float px_own) -> float {
     if constexpr (kNewtonShape) {
       float* M = nbuf;
       float* bv = nbuf + kNewtonB;
@@ -695,13 +699,23 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
           for (int i = lane; i < k; i += 32) bv[i] -= (M[k * kNewtonLd + i] / M[i * kNewtonLd + i]) * dk;
           __syncwarp();
         }
+        // step length: the whole step scaled so that max |δ| ≤ kNewtonMaxStep
+        float m = 0.f;
+        bool fin = true;
+        for (int i = lane; i < kNewtonN; i += 32) {
+          const float d = bv[i];
+          fin = fin && d == d && fabsf(d) < 1e30f;
+          m = fmaxf(m, fabsf(d));
+        }
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        fin = __all_sync(0xffffffffu, fin);
+        if (lane == 0) bv[kNewtonN] = fin ? fminf(1.0f, kNewtonMaxStep / fmaxf(m, 1e-30f)) : -1.0f;
       }
       __syncthreads();
-      const float dl = (ok && tid < kNewtonN) ? bv[tid] : 0.f;
-      return __syncthreads_and(ok && fabsf(dl) < 60.f) != 0;
+      return ok ? bv[kNewtonN] : -1.0f;
     } else {
       (void)px_own;
-      return false;
+      return -1.0f;
     }
   };
   float errx = 0.f;
@@ -1028,20 +1042,25 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     // − P_X π and sets u ← u·e^δ. It has the plain iteration's fixed point and
     // stopping rule, and converges in a few steps where the plain iteration
     // needs hundreds (cells whose support spreads far). The decision to take
-    // it: contraction ρ > 0.75 over iterations 3..6, or less than a tenfold
-    // error reduction over 16 iterations; a step that does not lower the error
-    // turns it off for the rest of the solve.
+    // it: an error below 5 % of ‖μ_J‖ and a contraction ρ > 0.75 over
+    // iterations 3..6 or less than a tenfold error reduction over 16
+    // iterations. A step longer than kNewtonMaxStep in log u is scaled down;
+    // a step that does not lower the error turns Newton off for the rest of
+    // the solve.
     bool newton_step = false;
+    float step_len = 0.f;
     if constexpr (kNewtonShape) {
       if (newton) {
         if (stepped && ep > ep_before) {
           newton = false;
           newton_off = true;
         } else {
-          newton_step = newton_x_step(pxl[0]);
+          step_len = newton_x_step(pxl[0]);
+          newton_step = step_len > 0.f;
           if (newton_step) {
             ep_before = ep;
             stepped = true;
+            ++nsteps;
           } else {
             newton = false;
             newton_off = true;
@@ -1050,9 +1069,10 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
       }
     }
     if (!newton_step && newton_ok && !newton_off && !newton) {
-      if (it == 6 && rho6 > 0.75f) newton = true;
+      const bool near = ep < 0.05f * muJ;   // Newton steps from close to the solution only
+      if (it == 6 && rho6 > 0.75f && near) newton = true;
       if (it > 6 && (it & 15) == 0) {
-        if (ep > 0.1f * e_mark) newton = true;
+        if (ep > 0.1f * e_mark && near) newton = true;
         e_mark = ep;
       }
       if (it == 6) e_mark = ep;
@@ -1060,12 +1080,13 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     }
     if (newton_step) {
       if (tid < HW) {
-        const float un = sm.u[tid] * expf(nbuf[kNewtonB + tid]);
-        if (un > kTwoTau || un < 1.0f / kTwoTau) {
-          sm.F[tid] += log2f(un);
+        // log2 of the new scaling, absorbed into F when it leaves the band
+        const float lu = log2f(sm.u[tid]) + step_len * nbuf[kNewtonB + tid] * (1.0f / kLn2);
+        if (fabsf(lu) > 16.0f) {
+          sm.F[tid] += lu;
           sm.u[tid] = 1.0f;
         } else {
-          sm.u[tid] = un;
+          sm.u[tid] = exp2f(lu);
         }
       }
     }
@@ -1077,12 +1098,23 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
       const float px = pxl[i];
       if (px > 1e-37f && px < 1e37f) {
         const float ratio = sm.mu[x] / px;
-        const float un = sm.u[x] * (omega == 1.0f ? ratio : exp2f(omega * log2f(ratio)));
-        if (un > kTwoTau || un < 1.0f / kTwoTau) {
-          sm.F[x] += log2f(un);
-          sm.u[x] = 1.0f;
+        if (omega == 1.0f) {
+          const float un = sm.u[x] * ratio;
+          if (un > kTwoTau || un < 1.0f / kTwoTau) {
+            sm.F[x] += log2f(un);
+            sm.u[x] = 1.0f;
+          } else {
+            sm.u[x] = un;
+          }
         } else {
-          sm.u[x] = un;
+          // over-relaxed: in log2, so that (μ/P_X π)^ω cannot overflow
+          const float lu = log2f(sm.u[x]) + omega * log2f(ratio);
+          if (fabsf(lu) > 16.0f) {
+            sm.F[x] += lu;
+            sm.u[x] = 1.0f;
+          } else {
+            sm.u[x] = exp2f(lu);
+          }
         }
       } else {
         // no mass reached this x: full log-sum-exp over the support with the
@@ -1296,6 +1328,7 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     a.cell_cost[J] = cs * (double)L.spacing * (double)L.spacing;
     a.cell_errx[J] = (double)errx;
     a.cell_iters[J] = it;
+    if (a.cell_newton) a.cell_newton[J] = nsteps;
     a.cell_status[J] = (converged ? 0 : 1) | (bad ? 2 : 0);
     if (a.iters_hist) a.iters_hist[J] = it;
     if (bad) atomicOr(a.err_flag, 2);
@@ -1497,8 +1530,8 @@ __global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals*
   __shared__ double dws[32];
   __shared__ long long lws[32];
   __shared__ int iws[32];
-  double c = 0.0, e = 0.0, ev = 0.0;
-  long long its = 0;
+  double c = 0.0, e = 0.0, ev = 0.0, hf = 0.0;
+  long long its = 0, nst = 0;
   int mx = 0, nc = 0, nf = 0, ov = 0;
   for (int J = threadIdx.x; J < a.ncells; J += blockDim.x) {
     const int st = a.cell_status[J];
@@ -1508,6 +1541,10 @@ __global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals*
     c += a.cell_cost[J];
     e += a.cell_errx[J];
     its += a.cell_iters[J];
+    if (a.cell_newton) {
+      nst += a.cell_newton[J];
+      hf += (double)a.cell_newton[J] * (double)(kNewtonN * kNewtonN) * (double)a.cell_ny[J];
+    }
     mx = max(mx, a.cell_iters[J]);
     nc += (st & 1) ? 1 : 0;
     nf += (st & 2) ? 1 : 0;
@@ -1516,6 +1553,8 @@ __global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals*
   e = block_sum<double>(e, dws);
   ev = block_sum<double>(ev, dws);
   its = block_sum<long long>(its, lws);
+  nst = block_sum<long long>(nst, lws);
+  hf = block_sum<double>(hf, dws);
   nc = block_sum<int>(nc, iws);
   nf = block_sum<int>(nf, iws);
   ov = block_sum<int>(ov, iws);
@@ -1531,6 +1570,8 @@ __global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals*
     out->errx = e;
     out->kernel_evals = ev;
     out->iters_sum = its;
+    out->newton_steps = nst;
+    out->hessian_fma = hf;
     out->iters_max = m;
     out->not_converged = nc;
     out->nonfinite = nf;

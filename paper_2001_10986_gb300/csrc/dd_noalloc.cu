@@ -263,6 +263,7 @@ extern "C" dd_status dd_solve_cell_noalloc(const double* mu, int32_t b, double s
   a.cell_cost = &S->cell_cost - q.J;
   a.cell_errx = &S->cell_errx - q.J;
   a.cell_iters = &S->cell_iters - q.J;
+  a.newton = 1;
   a.cell_status = &S->cell_status - q.J;
   a.err_flag = &S->err_flag;
   a.order = &S->order;

@@ -28,7 +28,8 @@ class dd_eps_step(C.Structure):
 
 class dd_options(C.Structure):
     _fields_ = [("err_tol", C.c_double), ("trunc", C.c_double), ("max_iter", C.c_int32),
-                ("threads_per_cell", C.c_int32), ("max_cluster_cells", C.c_int32), ("stream", C.c_void_p),
+                ("threads_per_cell", C.c_int32), ("max_cluster_cells", C.c_int32), ("x_newton", C.c_int32),
+                ("stream", C.c_void_p),
                 ("debug_flags", C.c_uint64)]
 
 
@@ -41,7 +42,8 @@ class dd_sweep_stats(C.Structure):
 class dd_profile(C.Structure):
     _fields_ = [("launches", C.c_int64), ("half_sweeps", C.c_int64), ("solve_launches", C.c_int64),
                 ("solve_ms", C.c_double), ("gather_launches", C.c_int64), ("gather_ms", C.c_double),
-                ("cluster_ms", C.c_double), ("kernel_evals", C.c_double), ("sinkhorn_iters", C.c_double), ("cells", C.c_int64)]
+                ("cluster_ms", C.c_double), ("kernel_evals", C.c_double), ("sinkhorn_iters", C.c_double), ("cells", C.c_int64),
+                ("newton_steps", C.c_int64), ("hessian_fma", C.c_double)]
 
 
 class DDError(RuntimeError):
@@ -110,7 +112,10 @@ def _stream_ptr(stream):
 def dd_options_default(**overrides) -> dd_options:
     o = dd_options()
     _lib.dd_options_default(C.byref(o))
+    names = {f[0] for f in dd_options._fields_}
     for k, v in overrides.items():
+        if k not in names:
+            raise TypeError(f"unknown dd_options field {k!r}")
         if k == "stream":
             v = _stream_ptr(v)
         setattr(o, k, v)

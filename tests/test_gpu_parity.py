@@ -203,3 +203,30 @@ def test_set_state_rejects_unsorted(lib):
     g.set_state(rp, col, val)           # the context is still usable
     g.half_sweep(1, 0.01)
     g.close()
+
+
+@pytest.fixture(scope="module")
+def ref_spread():
+    # a narrow blob spread over a wide one at ε = h²: cells whose X-iteration
+    # contracts slowly (the oracle needs 130–550 iterations per cell)
+    mu = syn.gaussian_mixture(16, 1, 60, sigma_range=(0.05, 0.06))
+    nu = syn.gaussian_mixture(16, 2, 61, sigma_range=(0.3, 0.35))
+    sched = [(1.0 / 256, 4, 0)]
+    return mu, nu, sched, odd.run_schedule(mu, nu, 4, 1, sched, odd.Params(err=1e-10))
+
+
+@pytest.mark.parametrize("newton", [1, 0])
+def test_newton_x_iteration_matches_oracle(lib, ref_spread, newton):
+    # with Newton X-iterations on, such cells take Newton steps; on or off, the
+    # result is the oracle's fixed point
+    mu, nu, sched, ref = ref_spread
+    g = lib.DD(mu, nu, 4, 1, sched, err_tol=1e-7, x_newton=newton)
+    g.run_schedule()
+    prof = g.profile()
+    rp, col, val = g.basic_marginals()
+    cost, _, _ = g.cost(with_y=False)
+    g.close()
+    assert (prof.newton_steps > 0) == bool(newton), prof.newton_steps
+    got = _dense_rows(rp, col, val, 16 * 16)
+    assert _rel_l1(got, odd.rows_to_dense(ref.rows, 16 * 16)) < PLAN_TOL
+    assert abs(cost - ref.history[-1][3].cost) / ref.history[-1][3].cost < COST_TOL
