@@ -466,12 +466,16 @@ class RunResult:
     history: list
 
 
-def run_schedule(mu_img, nu_img, b, levels, schedule, params, *, on_half_sweep=None):
+def run_schedule(mu_img, nu_img, b, levels, schedule, params, *, on_half_sweep=None,
+                 before_half_sweep=None):
     """Algorithm 2 inside the multi-scale / ε-scaling driver (§6.4).
 
     schedule: list of (eps, sweeps, level); level 0 is the coarsest image,
     levels-1 the input resolution. One sweep = a half-sweep on A then on B.
     The run starts at level 0 from the product coupling with α = 0.
+    before_half_sweep(prob, part, rows, alpha, eps) and on_half_sweep(prob,
+    part, rows, alpha, eps, info) are called around every half-sweep (rows and
+    α before, respectively after it).
     """
     mus, nus = pyramid(mu_img, levels), pyramid(nu_img, levels)
     n = mu_img.shape[0]
@@ -494,6 +498,8 @@ def run_schedule(mu_img, nu_img, b, levels, schedule, params, *, on_half_sweep=N
         eps = eps_s
         for _ in range(sweeps):
             for part in ("A", "B"):
+                if before_half_sweep is not None:
+                    before_half_sweep(prob, part, rows, alpha[part], eps)
                 rows, info = half_sweep(prob, part, rows, alpha[part], eps, params)
                 last = part
                 history.append((lev, eps, part, info))

@@ -193,3 +193,21 @@ def feasible_state(mu: np.ndarray, b: int, seed: int, *, shift_px: float = 6.0,
     row_ptr = np.zeros(nb * nb + 1, dtype=np.int64)
     row_ptr[1:] = np.cumsum([len(c) for c in rows_c])
     return nu.reshape(n, n), row_ptr, np.concatenate(rows_c), np.concatenate(rows_v)
+
+
+# sizes of the warm-start network: 1089 inputs (64 μ values, a 32×32 ν
+# histogram, log ε), two hidden layers of 256, 64 outputs
+MLP_LAYERS = ((256, 1089), (256, 256), (64, 256))
+
+
+def mlp_init(seed: int, scale: float = 1.0) -> np.ndarray:
+    """Seeded initial parameters of the warm-start network as one FP32 vector:
+    for each layer (out × in) the weights row-major, drawn uniformly in
+    ±scale·√(6/in), then `out` zero biases."""
+    rng = _rng(seed)
+    parts = []
+    for o, i in MLP_LAYERS:
+        lim = scale * math.sqrt(6.0 / i)
+        parts.append(rng.uniform(-lim, lim, size=o * i))
+        parts.append(np.zeros(o))
+    return np.concatenate(parts).astype(np.float32)
