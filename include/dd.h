@@ -81,6 +81,14 @@ typedef struct {
                             contracts slowly switches to Newton X-iterations
                             (same fixed point, same stopping rule); 0: plain
                             Sinkhorn X-iterations only. Default 1.             */
+  int32_t warm;          /* warm start of the cell solves. 0: the duals of the
+                            cell's previous solve (Algorithm 2 input u_{C,J}).
+                            1: with a network attached (dd_attach_mlp), 8×8
+                            cells also get a predicted dual at the first sweep
+                            after every change of ε or level, and start from
+                            whichever of the two has the smaller X-marginal
+                            error after one Y-iteration. 2: the same at every
+                            half-sweep. Default 0.                             */
   void* stream;          /* cudaStream_t to run on; NULL = a stream owned by
                             the context.                                       */
   uint64_t debug_flags;  /* bit 0: synchronise and check after every kernel;
@@ -107,6 +115,9 @@ typedef struct {
                                 most 64 pixels whose iteration converges slowly) */
   double hessian_fma;        /* FMAs of their Hessian accumulations,
                                 Σ over steps of 64²·N_y(J)                       */
+  int64_t learned_cells;     /* cell solves that started from the predicted
+                                duals (warm ≠ 0)                                 */
+  int64_t judged_cells;      /* cell solves for which a prediction was judged   */
 } dd_profile;
 
 /* Statistics of the last sweep run by dd_sweep / dd_run_schedule. */
@@ -252,6 +263,51 @@ dd_status dd_solve_cell_noalloc(const double* mu, int32_t b, double spacing, int
                                 const int32_t* y_row, const int32_t* y_col, const double* nu,
                                 double eps, double err_tol, int32_t max_iter, double trunc,
                                 double* alpha, double* nu_basic, void* stream);
+
+/* ---- learned warm start (no counterpart in the paper) -------------------
+ * A network of 1089 inputs, two hidden layers of 256 (ReLU) and 64 outputs,
+ * y = W3·relu(W2·relu(W1·x + b1) + b2) + b3, with bfloat16 weights (rounded
+ * to nearest even from the FP32 master copy) and FP32 sums. Its input for a
+ * cell of 8×8 pixels: 64·μ(x)/‖μ_J‖ on the cell's pixels (row-major),
+ * 1024·ν_cell(y)/‖ν_cell‖ on the 32×32 pixel window whose centre pixel (16,16)
+ * is the rounded centroid of ν_cell, and log(ε/Δ²). Its output: the cell's
+ * dual α in the frame of that centroid (anchor a = round(centroid − 3.5);
+ * α̃(i,j) = α − 2Δ²((r₀ − a_r)·i + (c₀ − a_c)·j)), divided by ε, mean zero.
+ * Parameters are one FP32 vector: W1 (256×1089 row-major), b1 (256),
+ * W2 (256×256), b2, W3 (64×256), b3 (64): dd_mlp_num_params() floats.
+ * A network is not thread-safe; calls on one network are serialised. Errors
+ * are reported by the status and dd_last_error(NULL). */
+typedef struct dd_mlp dd_mlp;
+
+int64_t dd_mlp_num_params(void);
+/* New network on the current device from host parameters (copied). */
+dd_status dd_mlp_create(const float* params, dd_mlp** out);
+void dd_mlp_destroy(dd_mlp* m);
+dd_status dd_mlp_get_params(dd_mlp* m, float* params);
+dd_status dd_mlp_set_params(dd_mlp* m, const float* params);
+/* y[n·64] = network(x[n·1089]); DEVICE pointers, run on `stream`, returns
+ * after it finished. 1 ≤ n ≤ 2^24. */
+dd_status dd_mlp_forward(dd_mlp* m, const float* x, int64_t n, float* y, void* stream);
+/* Mean squared error over the n·64 outputs against t[n·64] and its gradient
+ * with respect to the parameters (grad: HOST, dd_mlp_num_params() floats, or
+ * NULL). x, t: DEVICE. The rounding of the weights is taken as the identity
+ * in the derivative. */
+dd_status dd_mlp_loss_grad(dd_mlp* m, const float* x, const float* t, int64_t n, double* loss, float* grad,
+                           void* stream);
+/* One Adam step (β = 0.9, 0.999, ε = 1e-8) on the mean squared error of the
+ * batch; loss (nullable) receives the loss before the step. */
+dd_status dd_mlp_train_step(dd_mlp* m, const float* x, const float* t, int64_t n, float lr, double* loss,
+                            void* stream);
+/* Attach a network to a context (NULL detaches); used when options.warm ≠ 0.
+ * The context does not own it: keep it alive while attached. */
+dd_status dd_attach_mlp(dd_ctx* ctx, dd_mlp* m);
+/* Training pairs of the last half-sweep, one per composite cell of its
+ * partition (n_cells of them): features (DEVICE, n_cells·1089 floats) from
+ * the ν_cell the cells were solved with, targets (DEVICE, n_cells·64) from
+ * the duals the solves returned, ok (DEVICE, n_cells int32) = 1 for cells of
+ * 8×8 pixels (the others are not written). cap: rows the buffers hold. */
+dd_status dd_cell_training_pairs(dd_ctx* ctx, float* features, float* targets, int32_t* ok, int64_t cap,
+                                 int64_t* n_cells);
 
 /* Free the context and all device memory it owns. NULL is allowed. */
 void dd_destroy(dd_ctx* ctx);

@@ -89,6 +89,18 @@ struct dd_ctx {
   double* cell_errx = nullptr;
   int32_t* cell_iters = nullptr;
   int32_t* cell_newton = nullptr;
+  // learned warm start: the attached network (not owned), per-cell features,
+  // predictions, centroid anchors, flags; (ε, level) of each partition's last
+  // solve, to tell the first sweep after a change
+  dd_mlp* mlp = nullptr;
+  float* feat = nullptr;
+  float* pred = nullptr;
+  int2* fanc = nullptr;
+  int32_t* fok = nullptr;
+  int32_t* cell_learned = nullptr;
+  int64_t feat_cap = 0;
+  double part_eps[2] = {-1.0, -1.0};
+  int part_lev[2] = {-1, -1};
   int32_t* cell_status = nullptr;
   int32_t* order = nullptr;
   int32_t* iters_hist[2] = {nullptr, nullptr};
@@ -336,6 +348,27 @@ SweepArgs sweep_args(dd_ctx* c, int part, double eps) {
   return a;
 }
 
+void ensure_learned_buffers(dd_ctx* c, int64_t ncells) {
+  if (ncells <= c->feat_cap) return;
+  dev_free(c->feat);
+  dev_free(c->pred);
+  dev_free(c->fanc);
+  dev_free(c->fok);
+  dev_free(c->cell_learned);
+  c->feat = nullptr;
+  c->pred = nullptr;
+  c->fanc = nullptr;
+  c->fok = nullptr;
+  c->cell_learned = nullptr;
+  c->feat_cap = 0;
+  dev_alloc(c->feat, (size_t)ncells * kMlpIn);
+  dev_alloc(c->pred, (size_t)ncells * kMlpOut);
+  dev_alloc(c->fanc, (size_t)ncells);
+  dev_alloc(c->fok, (size_t)ncells);
+  dev_alloc(c->cell_learned, (size_t)ncells);
+  c->feat_cap = ncells;
+}
+
 int threads_per_cell(dd_ctx* c) {
   const int t = c->opt.threads_per_cell;
   return (t == 32 || t == 64 || t == 128 || t == 256) ? t : 128;
@@ -354,6 +387,22 @@ void half_sweep(dd_ctx* c, int part, double eps) {
   if (timing) DD_CUDA(cudaEventRecord(c->ev[0], c->stream));
   DD_CUDA(launch_gather(a, c->stream));
   check_debug(c, "gather");
+  // learned warm start: predict the duals of the 8×8 cells and keep, per
+  // cell, the better of prediction and previous duals (first sweep after a
+  // change of ε or level, or every half-sweep with warm = 2)
+  const bool fresh = eps != c->part_eps[part] || c->lev != c->part_lev[part];
+  c->part_eps[part] = eps;
+  c->part_lev[part] = c->lev;
+  a.cell_learned = nullptr;
+  if (c->mlp && c->b == 4 && (c->opt.warm == 2 || (c->opt.warm == 1 && fresh))) {
+    ensure_learned_buffers(c, a.ncells);
+    a.cell_learned = c->cell_learned;
+    DD_CUDA(launch_cell_features(a, c->feat, c->fanc, c->fok, c->stream));
+    DD_CUDA(mlp_forward(c->mlp, c->feat, a.ncells, c->pred, c->stream));
+    DD_CUDA(launch_judge(a, c->pred, c->fanc, c->fok, c->stream));
+    c->prof.launches += 7;
+    check_debug(c, "learned warm start");
+  }
   std::vector<int32_t> pred_copy;
   if (c->cell_times && std::getenv("DD_TRACE_TIMES_FILE")) {
     pred_copy.resize(a.ncells);
@@ -415,6 +464,10 @@ void half_sweep(dd_ctx* c, int part, double eps) {
   c->prof.sinkhorn_iters += (double)c->last_tot.iters_sum;
   c->prof.newton_steps += c->last_tot.newton_steps;
   c->prof.hessian_fma += c->last_tot.hessian_fma;
+  if (a.cell_learned) {
+    c->prof.learned_cells += c->last_tot.learned;
+    c->prof.judged_cells += c->last_tot.judged;
+  }
   c->prof.cells += a.ncells;
   if (c->cell_times && std::getenv("DD_TRACE_TIMES_FILE")) {
     const int nc = a.ncells;
@@ -661,7 +714,8 @@ void release(dd_ctx* c) {
   void* bufs[] = {c->ws_ytmp, c->ws_vtmp, c->ws_eta, c->ws_nu, c->ws_lognu, c->ws_g, c->tmp_col, c->tmp_val,
                   c->row_cnt, c->row_src, c->tile, c->cell_off, c->cell_ny, c->anchor_new, c->cell_cost,
                   c->cell_errx, c->cell_iters, c->cell_newton, c->cell_status, c->ydense, c->ws_counter, c->err_flag,
-                  c->totals, c->yerr, c->order, c->iters_hist[0], c->iters_hist[1], c->trace_buf, c->nbig, c->cell_times};
+                  c->totals, c->yerr, c->order, c->iters_hist[0], c->iters_hist[1], c->trace_buf, c->nbig, c->cell_times,
+                  c->feat, c->pred, c->fanc, c->fok, c->cell_learned};
   for (void* p : bufs) dev_free(p);
   if (c->h_tot) cudaFreeHost(c->h_tot);
   if (c->h_nnz) cudaFreeHost(c->h_nnz);
@@ -749,6 +803,7 @@ void dd_options_default(dd_options* opt) {
   opt->threads_per_cell = 0;
   opt->max_cluster_cells = -1;
   opt->x_newton = 1;
+  opt->warm = 0;
   opt->stream = nullptr;
   opt->debug_flags = 0;
 }
@@ -1107,6 +1162,29 @@ void dd_destroy(dd_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   release(c);
   delete c;
+}
+
+dd_status dd_attach_mlp(dd_ctx* c, dd_mlp* m) {
+  return guarded(c, [&] { c->mlp = m; });
+}
+
+dd_status dd_cell_training_pairs(dd_ctx* c, float* features, float* targets, int32_t* ok, int64_t cap,
+                                 int64_t* n_cells) {
+  return guarded(c, [&] {
+    if (!features || !targets || !ok) throw DdError{DD_ERR_ARG, "NULL buffer"};
+    if (c->last_part < 0) throw DdError{DD_ERR_STATE, "no half-sweep has run on this level yet"};
+    const LevelHost& h = c->lh[c->lev];
+    const int nc = num_cells(c->last_part, h.nb);
+    if (n_cells) *n_cells = nc;
+    if (cap < nc) throw DdError{DD_ERR_CAPACITY, "buffers hold fewer rows than the partition has cells"};
+    if (c->b != 4) throw DdError{DD_ERR_ARG, "training pairs are defined for 4×4 basic cells"};
+    SweepArgs a = sweep_args(c, c->last_part, c->eps_cur);
+    ensure_learned_buffers(c, nc);
+    DD_CUDA(cudaMemsetAsync(ok, 0, sizeof(int32_t) * (size_t)nc, c->stream));
+    DD_CUDA(launch_cell_features(a, features, c->fanc, ok, c->stream));
+    DD_CUDA(launch_cell_targets(a, c->fanc, ok, targets, c->stream));
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+  });
 }
 
 const char* dd_last_error(const dd_ctx* c) {

@@ -45,6 +45,13 @@ struct CellGeom {
   int H, W;       // size in pixels
 };
 
+// support point of a cell relative to its anchor pixel: two int16 in one word
+__device__ __forceinline__ int32_t pack_eta(int r, int c) {
+  return (int32_t)((uint32_t)(r & 0xffff) | ((uint32_t)(c & 0xffff) << 16));
+}
+__device__ __forceinline__ int eta_r(int32_t p) { return (int)(int16_t)(p & 0xffff); }
+__device__ __forceinline__ int eta_c(int32_t p) { return (int)(int16_t)((uint32_t)p >> 16); }
+
 __host__ __device__ inline int num_cells(int part, int nb) {
   int m = part == 0 ? nb / 2 : nb / 2 + 1;
   return m * m;
@@ -113,6 +120,8 @@ struct SweepArgs {
   int32_t* cell_iters;
   int32_t* cell_newton;     // Newton X-iterations of each cell solve (nullable)
   int newton;               // Newton X-iterations allowed
+  int32_t* cell_learned;    // per cell: 1 learned duals used, 0 judged and not used,
+                            // −1 not judged (nullable: no prediction this half-sweep)
   int32_t* cell_status;     // bit0 not converged, bit1 non-finite, bit2 workspace overflow
   int* err_flag;
   const int32_t* order;     // launch order of the cells (NULL: natural order)
@@ -147,6 +156,8 @@ struct SweepTotals {
   long long iters_sum;
   long long newton_steps;
   int iters_max, not_converged, nonfinite, overflow;
+  int learned;               // cells started from the learned duals
+  int judged;                // cells whose prediction was judged
 };
 cudaError_t launch_reduce_cells(const SweepArgs& a, SweepTotals* out_dev, cudaStream_t s);
 cudaError_t launch_y_error(LevelView L, const int64_t* rp, const int32_t* col, const uint64_t* val,
@@ -174,6 +185,27 @@ cudaError_t launch_refine_duals(LevelView C, LevelView F, int cpart, const float
 cudaError_t launch_plan(const SweepArgs& a, float trunc, const int64_t* xrp, int32_t* xcnt,
                         int32_t* pcol, double* pval, int write, cudaStream_t s);
 
+// ---- learned warm start (cells of 8×8 pixels) ----
+constexpr int kMlpIn = 1089, kMlpHidden = 256, kMlpOut = 64;
+// features of every 8×8 cell of the half-sweep in `a` (after the gather):
+// feat[J·1089 + …], the anchor of the ν_cell centroid frame, ok[J] ∈ {0, 1}
+cudaError_t launch_cell_features(const SweepArgs& a, float* feat, int2* fanchor, int32_t* ok,
+                                 cudaStream_t s);
+// targets of the same cells from the duals after the solve: tgt[J·64 + …]
+cudaError_t launch_cell_targets(const SweepArgs& a, const int2* fanchor, const int32_t* ok, float* tgt,
+                                cudaStream_t s);
+// judge: per 8×8 cell, the X-error after one Y-iteration from the current
+// duals and from the prediction pred[J·64 + …]; the better one is written to
+// a.alpha and a.cell_learned[J] records the choice
+cudaError_t launch_judge(const SweepArgs& a, const float* pred, const int2* fanchor, const int32_t* ok,
+                         cudaStream_t s);
+
+}  // namespace ddk
+
+struct dd_mlp;
+namespace ddk {
+// network output y[n·64] for inputs x[n·1089] (device), on stream s
+cudaError_t mlp_forward(dd_mlp* m, const float* x, int64_t n, float* y, cudaStream_t s);
 }  // namespace ddk
 
 // sets the message returned by dd_last_error(NULL) in this thread

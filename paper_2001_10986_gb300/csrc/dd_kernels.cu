@@ -77,11 +77,6 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
   return d;
 }
 
-__device__ __forceinline__ int32_t pack_eta(int r, int c) {
-  return (int32_t)((uint32_t)(r & 0xffff) | ((uint32_t)(c & 0xffff) << 16));
-}
-__device__ __forceinline__ int eta_r(int32_t p) { return (int)(int16_t)(p & 0xffff); }
-__device__ __forceinline__ int eta_c(int32_t p) { return (int)(int16_t)((uint32_t)p >> 16); }
 
 // exclusive scan of one int per thread over the block; returns the prefix,
 // writes the block total. `ws` holds ≥ 32 ints.
@@ -1532,9 +1527,13 @@ __global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals*
   __shared__ int iws[32];
   double c = 0.0, e = 0.0, ev = 0.0, hf = 0.0;
   long long its = 0, nst = 0;
-  int mx = 0, nc = 0, nf = 0, ov = 0;
+  int mx = 0, nc = 0, nf = 0, ov = 0, nl = 0, nj = 0;
   for (int J = threadIdx.x; J < a.ncells; J += blockDim.x) {
     const int st = a.cell_status[J];
+    if (a.cell_learned) {
+      nl += a.cell_learned[J] == 1 ? 1 : 0;
+      nj += a.cell_learned[J] >= 0 ? 1 : 0;
+    }
     if (st & 4) { ++ov; continue; }
     const CellGeom g = cell_geom(a.part, J, a.L.nb, a.L.b);
     ev += (double)(g.H * g.W) * (double)a.cell_ny[J] * (double)(a.cell_iters[J] + 1);
@@ -1558,6 +1557,8 @@ __global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals*
   nc = block_sum<int>(nc, iws);
   nf = block_sum<int>(nf, iws);
   ov = block_sum<int>(ov, iws);
+  nl = block_sum<int>(nl, iws);
+  nj = block_sum<int>(nj, iws);
   // max via shuffles
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   __syncthreads();
@@ -1576,6 +1577,8 @@ __global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals*
     out->not_converged = nc;
     out->nonfinite = nf;
     out->overflow = ov;
+    out->learned = nl;
+    out->judged = nj;
   }
 }
 

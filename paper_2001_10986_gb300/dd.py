@@ -29,7 +29,7 @@ class dd_eps_step(C.Structure):
 class dd_options(C.Structure):
     _fields_ = [("err_tol", C.c_double), ("trunc", C.c_double), ("max_iter", C.c_int32),
                 ("threads_per_cell", C.c_int32), ("max_cluster_cells", C.c_int32), ("x_newton", C.c_int32),
-                ("stream", C.c_void_p),
+                ("warm", C.c_int32), ("stream", C.c_void_p),
                 ("debug_flags", C.c_uint64)]
 
 
@@ -43,7 +43,8 @@ class dd_profile(C.Structure):
     _fields_ = [("launches", C.c_int64), ("half_sweeps", C.c_int64), ("solve_launches", C.c_int64),
                 ("solve_ms", C.c_double), ("gather_launches", C.c_int64), ("gather_ms", C.c_double),
                 ("cluster_ms", C.c_double), ("kernel_evals", C.c_double), ("sinkhorn_iters", C.c_double), ("cells", C.c_int64),
-                ("newton_steps", C.c_int64), ("hessian_fma", C.c_double)]
+                ("newton_steps", C.c_int64), ("hessian_fma", C.c_double), ("learned_cells", C.c_int64),
+                ("judged_cells", C.c_int64)]
 
 
 class DDError(RuntimeError):
@@ -85,15 +86,30 @@ _lib.dd_destroy.argtypes = [_P]
 _lib.dd_destroy.restype = None
 _lib.dd_last_error.argtypes = [_P]
 _lib.dd_last_error.restype = C.c_char_p
+_lib.dd_mlp_num_params.argtypes = []
+_lib.dd_mlp_num_params.restype = C.c_int64
+_lib.dd_mlp_create.argtypes = [np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS"), C.POINTER(_P)]
+_lib.dd_mlp_destroy.argtypes = [_P]
+_lib.dd_mlp_destroy.restype = None
+_lib.dd_mlp_get_params.argtypes = [_P, np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")]
+_lib.dd_mlp_set_params.argtypes = [_P, np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")]
+_lib.dd_mlp_forward.argtypes = [_P, _P, C.c_int64, _P, _P]
+_lib.dd_mlp_loss_grad.argtypes = [_P, _P, _P, C.c_int64, C.POINTER(C.c_double), _P, _P]
+_lib.dd_mlp_train_step.argtypes = [_P, _P, _P, C.c_int64, C.c_float, C.POINTER(C.c_double), _P]
+_lib.dd_attach_mlp.argtypes = [_P, _P]
+_lib.dd_cell_training_pairs.argtypes = [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_int64)]
 for _f in ("dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep", "dd_run_schedule", "dd_cost",
            "dd_get_basic_marginals", "dd_get_plan", "dd_get_duals", "dd_get_info", "dd_get_profile",
-           "dd_reset_profile", "dd_get_cell_stats"):
+           "dd_reset_profile", "dd_get_cell_stats", "dd_mlp_create", "dd_mlp_get_params", "dd_mlp_set_params",
+           "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step", "dd_attach_mlp", "dd_cell_training_pairs"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep",
             "dd_run_schedule", "dd_cost", "dd_get_basic_marginals", "dd_get_plan", "dd_get_duals",
             "dd_get_info", "dd_get_cell_stats", "dd_get_profile", "dd_reset_profile", "dd_destroy",
-            "dd_last_error", "dd_solve_cell_noalloc")
+            "dd_last_error", "dd_solve_cell_noalloc", "dd_mlp_num_params", "dd_mlp_create", "dd_mlp_destroy",
+            "dd_mlp_get_params", "dd_mlp_set_params", "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step",
+            "dd_attach_mlp", "dd_cell_training_pairs")
 
 
 def _check(ctx, st):
@@ -229,6 +245,66 @@ def dd_solve_cell_noalloc(mu, b, spacing, n_y, y_row, y_col, nu, eps, err_tol, m
                                             alpha, nu_basic, _stream_ptr(stream)))
 
 
+def dd_mlp_num_params() -> int:
+    return int(_lib.dd_mlp_num_params())
+
+
+def dd_mlp_create(params):
+    """params: host FP32 vector of dd_mlp_num_params() floats. Returns a handle."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != dd_mlp_num_params():
+        raise DDError(DD_ERR_ARG, f"expected {dd_mlp_num_params()} parameters, got {p.size}")
+    h = _P()
+    _check(None, _lib.dd_mlp_create(p, C.byref(h)))
+    return h
+
+
+def dd_mlp_destroy(mlp):
+    _lib.dd_mlp_destroy(mlp)
+
+
+def dd_mlp_get_params(mlp):
+    out = np.empty(dd_mlp_num_params(), dtype=np.float32)
+    _check(None, _lib.dd_mlp_get_params(mlp, out))
+    return out
+
+
+def dd_mlp_set_params(mlp, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != dd_mlp_num_params():
+        raise DDError(DD_ERR_ARG, "wrong number of parameters")
+    _check(None, _lib.dd_mlp_set_params(mlp, p))
+
+
+def dd_mlp_forward(mlp, x_ptr, n, y_ptr, stream=None):
+    """x_ptr, y_ptr: device addresses (n·1089 and n·64 floats)."""
+    _check(None, _lib.dd_mlp_forward(mlp, x_ptr, int(n), y_ptr, _stream_ptr(stream)))
+
+
+def dd_mlp_loss_grad(mlp, x_ptr, t_ptr, n, stream=None):
+    """Returns (loss, gradient as a host FP32 vector)."""
+    g = np.empty(dd_mlp_num_params(), dtype=np.float32)
+    loss = C.c_double()
+    _check(None, _lib.dd_mlp_loss_grad(mlp, x_ptr, t_ptr, int(n), C.byref(loss), g.ctypes.data, _stream_ptr(stream)))
+    return loss.value, g
+
+
+def dd_mlp_train_step(mlp, x_ptr, t_ptr, n, lr, stream=None):
+    loss = C.c_double()
+    _check(None, _lib.dd_mlp_train_step(mlp, x_ptr, t_ptr, int(n), float(lr), C.byref(loss), _stream_ptr(stream)))
+    return loss.value
+
+
+def dd_attach_mlp(ctx, mlp):
+    _check(ctx, _lib.dd_attach_mlp(ctx, mlp))
+
+
+def dd_cell_training_pairs(ctx, feat_ptr, tgt_ptr, ok_ptr, cap):
+    n = C.c_int64()
+    _check(ctx, _lib.dd_cell_training_pairs(ctx, feat_ptr, tgt_ptr, ok_ptr, int(cap), C.byref(n)))
+    return n.value
+
+
 def dd_get_profile(ctx) -> dd_profile:
     p = dd_profile()
     _check(ctx, _lib.dd_get_profile(ctx, C.byref(p)))
@@ -294,10 +370,71 @@ class DD:
     def reset_profile(self):
         dd_reset_profile(self.ctx)
 
+    def attach_mlp(self, mlp):
+        """Attach an MLP (or None); its handle must outlive the attachment."""
+        self._mlp = mlp
+        dd_attach_mlp(self.ctx, mlp.handle if mlp is not None else None)
+
+    def training_pairs(self):
+        """(features, targets) of the 8×8 cells of the last half-sweep as CUDA
+        tensors (n × 1089, n × 64); torch provides the device memory."""
+        import torch
+        nb = self.info()[2]
+        cap = (int(round(nb ** 0.5)) // 2 + 1) ** 2
+        dev = torch.device("cuda", torch.cuda.current_device())
+        feat = torch.empty((cap, 1089), dtype=torch.float32, device=dev)
+        tgt = torch.empty((cap, 64), dtype=torch.float32, device=dev)
+        ok = torch.zeros(cap, dtype=torch.int32, device=dev)
+        n = dd_cell_training_pairs(self.ctx, feat.data_ptr(), tgt.data_ptr(), ok.data_ptr(), cap)
+        sel = ok[:n] != 0
+        return feat[:n][sel].contiguous(), tgt[:n][sel].contiguous()
+
     def close(self):
         if self.ctx:
             dd_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """Owner of one warm-start network; tensors are CUDA float32 (torch only
+    holds the memory)."""
+
+    def __init__(self, params):
+        self.handle = dd_mlp_create(params)
+
+    @property
+    def params(self):
+        return dd_mlp_get_params(self.handle)
+
+    @params.setter
+    def params(self, p):
+        dd_mlp_set_params(self.handle, p)
+
+    def forward(self, x, stream=None):
+        import torch
+        x = x.contiguous()
+        y = torch.empty((x.shape[0], 64), dtype=torch.float32, device=x.device)
+        dd_mlp_forward(self.handle, x.data_ptr(), x.shape[0], y.data_ptr(), stream)
+        return y
+
+    def loss_grad(self, x, t, stream=None):
+        x, t = x.contiguous(), t.contiguous()
+        return dd_mlp_loss_grad(self.handle, x.data_ptr(), t.data_ptr(), x.shape[0], stream)
+
+    def train_step(self, x, t, lr, stream=None):
+        x, t = x.contiguous(), t.contiguous()
+        return dd_mlp_train_step(self.handle, x.data_ptr(), t.data_ptr(), x.shape[0], lr, stream)
+
+    def close(self):
+        if self.handle:
+            dd_mlp_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:
