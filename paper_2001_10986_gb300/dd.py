@@ -401,6 +401,13 @@ class DD:
             pass
 
 
+def _f32_cuda(t, cols):
+    import torch
+    if t.dtype != torch.float32 or not t.is_cuda or t.dim() != 2 or t.shape[1] != cols:
+        raise DDError(DD_ERR_ARG, f"expected a CUDA float32 tensor of shape (n, {cols})")
+    return t.contiguous()
+
+
 class MLP:
     """Owner of one warm-start network; tensors are CUDA float32 (torch only
     holds the memory)."""
@@ -418,17 +425,17 @@ class MLP:
 
     def forward(self, x, stream=None):
         import torch
-        x = x.contiguous()
+        x = _f32_cuda(x, 1089)
         y = torch.empty((x.shape[0], 64), dtype=torch.float32, device=x.device)
         dd_mlp_forward(self.handle, x.data_ptr(), x.shape[0], y.data_ptr(), stream)
         return y
 
     def loss_grad(self, x, t, stream=None):
-        x, t = x.contiguous(), t.contiguous()
+        x, t = _f32_cuda(x, 1089), _f32_cuda(t, 64)
         return dd_mlp_loss_grad(self.handle, x.data_ptr(), t.data_ptr(), x.shape[0], stream)
 
     def train_step(self, x, t, lr, stream=None):
-        x, t = x.contiguous(), t.contiguous()
+        x, t = _f32_cuda(x, 1089), _f32_cuda(t, 64)
         return dd_mlp_train_step(self.handle, x.data_ptr(), t.data_ptr(), x.shape[0], lr, stream)
 
     def close(self):

@@ -61,7 +61,7 @@ def test_training_lowers_the_loss(lib):
     rng = np.random.default_rng(9)
     X, _ = _inputs(3, 2048)
     A = rng.normal(size=(omlp.N_IN, omlp.N_OUT)).astype(np.float32) / np.sqrt(omlp.N_IN)
-    T = np.tanh(X @ A)
+    T = np.tanh(X @ A).astype(np.float32)
     Xd, Td = torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda")
     net = lib.MLP(syn.mlp_init(7))
     first = net.train_step(Xd, Td, 1e-3)
