@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-ttc", action="store_true", help="skip the time-to-converged runs")
+    p.add_argument("--no-learned", action="store_true", help="skip the learned warm-start arm")
     p.add_argument("--cpu-cells", type=int, default=160)
     p.add_argument("--err", type=float, default=1e-6)
     p.add_argument("--tpc", type=int, default=0, help="threads per cell solve (0: library choice)")
@@ -201,7 +202,7 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def time_to_converged(dd, syn, mu, nu, w, args, stream, max_final_sweeps=400, **opts):
+def time_to_converged(dd, syn, mu, nu, w, args, stream, max_final_sweeps=400, mlp=None, **opts):
     """Wall time from host images to a converged plan: dd_create, the whole
     coarse-to-fine schedule, then sweeps at the final ε until one sweep
     changes the FP64 transport cost by at most 1e-7 relative (the cell solves
@@ -213,6 +214,8 @@ def time_to_converged(dd, syn, mu, nu, w, args, stream, max_final_sweeps=400, **
     t = time.perf_counter()
     h = dd.DD(mu, nu, b, L, syn.paper_schedule(n, L, 1), err_tol=args.err, stream=stream,
               threads_per_cell=args.tpc, max_cluster_cells=args.clusters, **opts)
+    if mlp is not None:
+        h.attach_mlp(mlp)
     h.run_schedule()
     prev, _, _ = h.cost(with_y=False)
     k, rel = 1, None
@@ -227,8 +230,11 @@ def time_to_converged(dd, syn, mu, nu, w, args, stream, max_final_sweeps=400, **
     cost, ex, ey = h.cost()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t
+    p = h.profile()
     h.close()
     return {"seconds": dt, "final_sweeps": k, "last_rel_change": rel, "cost": cost, "err_x": ex, "err_y": ey,
+            "sinkhorn_iters": p.sinkhorn_iters, "newton_steps": p.newton_steps,
+            "learned_cells": p.learned_cells, "judged_cells": p.judged_cells,
             "criterion": "relative cost change over one final-ε sweep <= 1e-7"}
 
 
@@ -332,6 +338,28 @@ def run_cuda(args):
     ttc = None
     if not args.no_ttc:
         ttc = {"plain": time_to_converged(dd, syn, mu, nu, w, args, stream)}
+        if not args.no_learned:
+            # learned warm start: network trained on pairs logged from plain
+            # runs on 256² images (5 blobs, 3 levels), judged cell by cell
+            from paper_2001_10986_gb300 import learned
+            import torch
+            t0 = time.perf_counter()
+            fs, ts = [], []
+            for k in range(3):
+                m2 = syn.gaussian_mixture(256, 5, 1000 + 2 * k)
+                n2 = syn.gaussian_mixture(256, 5, 1001 + 2 * k)
+                f, tg = learned.log_pairs(m2, n2, 4, 3, syn.paper_schedule(256, 3, 4), min_level=1,
+                                          stream=stream)
+                fs.append(f)
+                ts.append(tg)
+            net = learned.train((torch.cat(fs), torch.cat(ts)), epochs=20, batch=512, lr=1e-3)
+            torch.cuda.synchronize()
+            t_train = time.perf_counter() - t0
+            res = time_to_converged(dd, syn, mu, nu, w, args, stream, warm=1, mlp=net)
+            res["training_seconds"] = t_train
+            res["training_pairs"] = int(sum(x.shape[0] for x in fs))
+            ttc["learned"] = res
+            net.close()
 
     if rank != 0:
         if pg:
