@@ -63,6 +63,7 @@ def parse():
     p.add_argument("--err", type=float, default=1e-6)
     p.add_argument("--tpc", type=int, default=0, help="threads per cell solve (0: library choice)")
     p.add_argument("--clusters", type=int, default=-1, help="max cells solved by 8-CTA clusters (-1: library choice)")
+    p.add_argument("--mode", type=int, default=1, help="0: per-kernel launches, 1: persistent solves + graph-replayed sweeps")
     return p.parse_args()
 
 
@@ -263,8 +264,8 @@ def run_cuda(args):
     stream = torch.cuda.current_stream()
 
     # ---- setup (untimed): coarse levels, refinement, warm-up sweeps at 2h² ----
-    g = dd.DD(mu, nu, b, L, sched, err_tol=args.err, stream=stream, debug_flags=2,
-              threads_per_cell=args.tpc, max_cluster_cells=args.clusters)
+    g = dd.DD(mu, nu, b, L, sched, err_tol=args.err, stream=stream, debug_flags=2 if args.mode == 0 else 0,
+              threads_per_cell=args.tpc, max_cluster_cells=args.clusters, mode=args.mode)
     g.run_schedule()
     torch.cuda.synchronize()
     g.reset_profile()
@@ -289,6 +290,20 @@ def run_cuda(args):
     prof = g.profile()
     cost, ex, ey = g.cost()
     g.close()
+    if args.mode != 0:
+        # kernel durations for the roofline: the same sweeps with per-kernel
+        # launches and CUDA events (a graph replay has no per-kernel events)
+        gk = dd.DD(mu, nu, b, L, sched, err_tol=args.err, stream=stream, debug_flags=2,
+                   threads_per_cell=args.tpc, max_cluster_cells=args.clusters, mode=0)
+        gk.run_schedule()
+        gk.reset_profile()
+        for _ in range(min(args.steps, 3)):
+            gk.sweep(1)
+        torch.cuda.synchronize()
+        prof_k = gk.profile()
+        gk.close()
+    else:
+        prof_k = prof
     t_rank = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
     if pg:
         pg.all_reduce(t_rank, op=pg.ReduceOp.MAX)
@@ -296,9 +311,9 @@ def run_cuda(args):
     value = world * n * n * args.steps / (ms_max * 1e-3)
 
     # ---- roofline of the cell-solve kernels (FP32 ALU) ----
-    launches = max(prof.solve_launches, 1)
-    solve_ms = prof.solve_ms / launches
-    fma = (FMA_PER_ENTRY * prof.kernel_evals + HESS_SYM * prof.hessian_fma) / launches
+    launches = max(prof_k.solve_launches, 1)
+    solve_ms = prof_k.solve_ms / launches
+    fma = (FMA_PER_ENTRY * prof_k.kernel_evals + HESS_SYM * prof_k.hessian_fma) / launches
     achieved = 2.0 * fma / (solve_ms * 1e-3) / 1e12
     peak = NUM_SM * FP32_LANES_PER_SM * 2.0 * SM_MAX_MHZ * 1e6 / 1e12
     roofline = {"bound": "alu", "kernel": "k_sinkhorn + k_sinkhorn_cluster (one half-sweep's cell solves)",
@@ -306,12 +321,12 @@ def run_cuda(args):
                 "traffic": SOLVE_TRAFFIC_BYTES,
                 "peak_source": f"FP32 FMA: {NUM_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz "
                                "(unit counts and maximum clock)",
-                "fma_per_launch": fma, "kernel_entries_per_launch": prof.kernel_evals / launches,
-                "newton_steps_per_launch": prof.newton_steps / launches, "ms_per_launch": solve_ms,
-                "solve_share": prof.solve_ms / ms_total if ms_total > 0 else None,
-                "gather_ms_per_launch": prof.gather_ms / max(prof.gather_launches, 1),
-                "cluster_ms_per_launch": prof.cluster_ms / launches,
-                "mean_sinkhorn_iters": prof.sinkhorn_iters / max(prof.cells, 1)}
+                "fma_per_launch": fma, "kernel_entries_per_launch": prof_k.kernel_evals / launches,
+                "newton_steps_per_launch": prof_k.newton_steps / launches, "ms_per_launch": solve_ms,
+                "solve_share_per_kernel_mode": prof_k.solve_ms / max(prof_k.half_sweeps, 1) * 2 / (ms_total / args.steps) if ms_total > 0 else None,
+                "gather_ms_per_launch": prof_k.gather_ms / max(prof_k.gather_launches, 1),
+                "cluster_ms_per_launch": prof_k.cluster_ms / launches,
+                "mean_sinkhorn_iters": prof_k.sinkhorn_iters / max(prof_k.cells, 1)}
 
     # ---- end to end through the C ABI from host buffers ----
     e2e = None
@@ -355,10 +370,12 @@ def run_cuda(args):
             net = learned.train((torch.cat(fs), torch.cat(ts)), epochs=20, batch=512, lr=1e-3)
             torch.cuda.synchronize()
             t_train = time.perf_counter() - t0
-            res = time_to_converged(dd, syn, mu, nu, w, args, stream, warm=1, mlp=net)
-            res["training_seconds"] = t_train
-            res["training_pairs"] = int(sum(x.shape[0] for x in fs))
-            ttc["learned"] = res
+            for mode in (1, 2):
+                res = time_to_converged(dd, syn, mu, nu, w, args, stream, warm=mode, mlp=net)
+                res["training_seconds"] = t_train
+                res["training_pairs"] = int(sum(x.shape[0] for x in fs))
+                res["warm"] = mode
+                ttc["learned" if mode == 1 else "learned_every_eps"] = res
             net.close()
 
     if rank != 0:
@@ -373,7 +390,8 @@ def run_cuda(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": args.workload, "n": n, "b": b, "levels": L, "eps_final": eps,
                       "err_tol": args.err, "nnz": nnz0, "l2": "working set larger than L2 (CSR + workspace)",
-                      "parallelism": f"replicas x{world} (independent image pairs)"},
+                      "parallelism": f"replicas x{world} (independent image pairs)",
+                      "mode": "persistent solves + graph-replayed sweeps" if args.mode == 1 else "per-kernel launches"},
            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "time_to_converged": ttc,
            "gpu_launches": int(prof.launches), "clocks": clk.summary(),
            "quality": {"cost": cost, "err_x": ex, "err_y": ey, "max_iters_last": st.max_iters,

@@ -85,10 +85,19 @@ typedef struct {
                             cell's previous solve (Algorithm 2 input u_{C,J}).
                             1: with a network attached (dd_attach_mlp), 8×8
                             cells also get a predicted dual at the first sweep
-                            after every change of ε or level, and start from
-                            whichever of the two has the smaller X-marginal
-                            error after one Y-iteration. 2: the same at every
-                            half-sweep. Default 0.                             */
+                            on a new level, and start from whichever of the
+                            two has the smaller X-marginal error after one
+                            Y-iteration. 2: the same also at the first sweep
+                            after a change of ε. 3: at every half-sweep.
+                            Default 0.                                         */
+  int32_t mode;          /* 0: every half-sweep as separate launches with a host
+                            check in between. 1: per-CTA cell solves as one
+                            persistent wave of CTAs that take cells in launch
+                            order from a counter, and every sweep at the same
+                            (level, ε) as the previous one replayed from one
+                            captured CUDA graph (A and B half-sweeps, no host
+                            synchronisation inside); the state buffers then
+                            hold twice the current entries. Default 0.         */
   void* stream;          /* cudaStream_t to run on; NULL = a stream owned by
                             the context.                                       */
   uint64_t debug_flags;  /* bit 0: synchronise and check after every kernel;

@@ -129,6 +129,14 @@ struct dd_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_c0 = nullptr, ev_c1 = nullptr;   // cluster kernel timing
   int* nbig = nullptr;
+  int* work_next = nullptr;           // persistent per-CTA solves: next cell position
+  // graph-captured sweeps (options.mode = 1): the instantiated graph of one
+  // A+B sweep and what it was captured with
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<uint64_t> graph_key;
+  SweepTotals* h_tot_g = nullptr;     // pinned, [2]: totals of the A and B half-sweeps
+  int64_t* h_nnz_g = nullptr;         // pinned, [2]: their output sizes
+  int* h_err_g = nullptr;             // pinned: the error word after the sweep
   int last_part = -1;
   bool need_init = false;  // level-0 product coupling not built yet
   double eps_cur = 0.0;
@@ -277,6 +285,7 @@ void corner_anchors(dd_ctx* c, int l, int part, int2* dst) {
 }
 
 void ensure_state(dd_ctx* c);
+void drop_graph(dd_ctx* c);
 
 void ensure_sweep_capacity(dd_ctx* c, int64_t nnz_in) {
   if (nnz_in > c->ws_cap) {
@@ -369,6 +378,20 @@ void ensure_learned_buffers(dd_ctx* c, int64_t ncells) {
   c->feat_cap = ncells;
 }
 
+int threads_per_cell(dd_ctx* c);
+
+// per-CTA cell solves: one CTA per cell, or (mode 1) a persistent wave of CTAs
+// taking cells in launch order from a counter
+void launch_cta_solves(dd_ctx* c, SweepArgs a) {
+  if (c->opt.mode == 1) {
+    DD_CUDA(cudaMemsetAsync(c->work_next, 0, sizeof(int), c->stream));
+    a.work_next = c->work_next;
+    DD_CUDA(launch_sinkhorn(a, threads_per_cell(c), c->stream, true));
+  } else {
+    DD_CUDA(launch_sinkhorn(a, threads_per_cell(c), c->stream, false));
+  }
+}
+
 int threads_per_cell(dd_ctx* c) {
   const int t = c->opt.threads_per_cell;
   return (t == 32 || t == 64 || t == 128 || t == 256) ? t : 128;
@@ -388,13 +411,15 @@ void half_sweep(dd_ctx* c, int part, double eps) {
   DD_CUDA(launch_gather(a, c->stream));
   check_debug(c, "gather");
   // learned warm start: predict the duals of the 8×8 cells and keep, per
-  // cell, the better of prediction and previous duals (first sweep after a
-  // change of ε or level, or every half-sweep with warm = 2)
-  const bool fresh = eps != c->part_eps[part] || c->lev != c->part_lev[part];
+  // cell, the better of prediction and previous duals (options.warm: 1 at the
+  // first sweep on a new level, 2 also after a change of ε, 3 every half-sweep)
+  const bool new_level = c->lev != c->part_lev[part];
+  const bool new_eps = eps != c->part_eps[part];
   c->part_eps[part] = eps;
   c->part_lev[part] = c->lev;
   a.cell_learned = nullptr;
-  if (c->mlp && c->b == 4 && (c->opt.warm == 2 || (c->opt.warm == 1 && fresh))) {
+  const int w = c->opt.warm;
+  if (c->mlp && c->b == 4 && (w == 3 || (w == 2 && (new_level || new_eps)) || (w == 1 && new_level))) {
     ensure_learned_buffers(c, a.ncells);
     a.cell_learned = c->cell_learned;
     DD_CUDA(launch_cell_features(a, c->feat, c->fanc, c->fok, c->stream));
@@ -418,7 +443,7 @@ void half_sweep(dd_ctx* c, int part, double eps) {
     if (timing) DD_CUDA(cudaEventRecord(c->ev_c0, c->stream));
     DD_CUDA(launch_sinkhorn_cluster(a, c->stream));
     if (timing) DD_CUDA(cudaEventRecord(c->ev_c1, c->stream));
-    DD_CUDA(launch_sinkhorn(a, threads_per_cell(c), c->stream));
+    launch_cta_solves(c, a);
   } else {
     DD_CUDA(cudaEventRecord(c->ev_fork, c->stream));
     DD_CUDA(cudaStreamWaitEvent(c->stream2, c->ev_fork, 0));
@@ -426,12 +451,12 @@ void half_sweep(dd_ctx* c, int part, double eps) {
     DD_CUDA(launch_sinkhorn_cluster(a, c->stream2));
     if (timing) DD_CUDA(cudaEventRecord(c->ev_c1, c->stream2));
     DD_CUDA(cudaEventRecord(c->ev_join, c->stream2));
-    DD_CUDA(launch_sinkhorn(a, threads_per_cell(c), c->stream));
+    launch_cta_solves(c, a);
     DD_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   }
   check_debug(c, "sinkhorn");
   if (timing) DD_CUDA(cudaEventRecord(c->ev[2], c->stream));
-  DD_CUDA(launch_row_scan(c->row_cnt, c->rp[other], c->tile, nrows, c->stream));
+  DD_CUDA(launch_row_scan(c->row_cnt, c->rp[other], c->tile, nrows, c->stream, c->err_flag));
   DD_CUDA(launch_reduce_cells(a, c->totals, c->stream));
   c->prof.launches += 7;
   DD_CUDA(cudaMemcpyAsync(c->h_tot, c->totals, sizeof(SweepTotals), cudaMemcpyDeviceToHost, c->stream));
@@ -717,6 +742,11 @@ void release(dd_ctx* c) {
                   c->totals, c->yerr, c->order, c->iters_hist[0], c->iters_hist[1], c->trace_buf, c->nbig, c->cell_times,
                   c->feat, c->pred, c->fanc, c->fok, c->cell_learned};
   for (void* p : bufs) dev_free(p);
+  drop_graph(c);
+  if (c->h_tot_g) cudaFreeHost(c->h_tot_g);
+  if (c->h_nnz_g) cudaFreeHost(c->h_nnz_g);
+  if (c->h_err_g) cudaFreeHost(c->h_err_g);
+  dev_free(c->work_next);
   if (c->h_tot) cudaFreeHost(c->h_tot);
   if (c->h_nnz) cudaFreeHost(c->h_nnz);
   if (c->h_err) cudaFreeHost(c->h_err);
@@ -755,6 +785,160 @@ dd_status guarded(dd_ctx* c, F&& f) {
   }
 }
 
+// ---- graph-captured sweeps (options.mode = 1) ----
+// col/val buffer k holds at least `need` entries, keeping its first `keep`
+void state_grow_keep(dd_ctx* c, int k, int64_t need, int64_t keep) {
+  if (c->cap[k] >= need && c->col[k] && c->val[k]) return;
+  const int64_t cap = std::max<int64_t>(need, 1024);
+  int32_t* col = nullptr;
+  uint64_t* val = nullptr;
+  dev_alloc(col, (size_t)cap);
+  try {
+    dev_alloc(val, (size_t)cap);
+  } catch (...) {
+    dev_free(col);
+    throw;
+  }
+  if (keep > 0) {
+    DD_CUDA(cudaMemcpyAsync(col, c->col[k], sizeof(int32_t) * (size_t)keep, cudaMemcpyDeviceToDevice, c->stream));
+    DD_CUDA(cudaMemcpyAsync(val, c->val[k], sizeof(uint64_t) * (size_t)keep, cudaMemcpyDeviceToDevice, c->stream));
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  dev_free(c->col[k]);
+  dev_free(c->val[k]);
+  c->col[k] = col;
+  c->val[k] = val;
+  c->cap[k] = cap;
+}
+
+void drop_graph(dd_ctx* c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  c->graph_exec = nullptr;
+  c->graph_key.clear();
+}
+
+// the work of one half-sweep from state buffer `in` into `out`, without host
+// synchronisation or allocation (capturable); totals and output size go to
+// the pinned slot `slot`
+void enqueue_half_sweep(dd_ctx* c, int part, double eps, int in, int out, int slot) {
+  const int nrows = c->lh[c->lev].nb * c->lh[c->lev].nb;
+  const int cur = c->cur;
+  c->cur = in;
+  SweepArgs a = sweep_args(c, part, eps);
+  c->cur = cur;
+  DD_CUDA(cudaMemsetAsync(c->ws_counter, 0, sizeof(unsigned long long), c->stream));
+  DD_CUDA(launch_gather(a, c->stream));
+  DD_CUDA(launch_order(a, c->order, c->nbig, c->stream));
+  a.order = c->order;
+  a.nbig = c->nbig;
+  DD_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+  DD_CUDA(cudaStreamWaitEvent(c->stream2, c->ev_fork, 0));
+  DD_CUDA(launch_sinkhorn_cluster(a, c->stream2));
+  DD_CUDA(cudaEventRecord(c->ev_join, c->stream2));
+  launch_cta_solves(c, a);
+  DD_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  DD_CUDA(launch_row_scan(c->row_cnt, c->rp[out], c->tile, nrows, c->stream, c->err_flag));
+  DD_CUDA(launch_reduce_cells(a, c->totals, c->stream));
+  DD_CUDA(launch_compact(c->row_cnt, c->row_src, c->tile, c->rp[out], c->tmp_col, c->tmp_val, c->col[out],
+                         c->val[out], c->cap[out], nrows, c->err_flag, c->stream));
+  DD_CUDA(cudaMemcpyAsync(c->h_tot_g + slot, c->totals, sizeof(SweepTotals), cudaMemcpyDeviceToHost, c->stream));
+  DD_CUDA(cudaMemcpyAsync(c->h_nnz_g + slot, c->rp[out] + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                          c->stream));
+}
+
+void account_half_sweep(dd_ctx* c, const SweepTotals& t, int ncells) {
+  c->prof.half_sweeps += 1;
+  c->prof.solve_launches += 1;
+  c->prof.gather_launches += 1;
+  c->prof.launches += 9;
+  c->prof.kernel_evals += t.kernel_evals;
+  c->prof.sinkhorn_iters += (double)t.iters_sum;
+  c->prof.newton_steps += t.newton_steps;
+  c->prof.hessian_fma += t.hessian_fma;
+  c->prof.cells += ncells;
+}
+
+// One A+B sweep replayed from a CUDA graph. Both state buffers get a fixed
+// capacity (twice the current entries) before the capture; a sweep whose
+// output does not fit is detected from the scan totals, the graph is dropped
+// and the sweep (or its B half) is run again with per-kernel launches.
+void graph_sweep(dd_ctx* c, double eps) {
+  ensure_state(c);
+  const LevelHost& h = c->lh[c->lev];
+  const int nrows = h.nb * h.nb;
+  const int64_t want = std::max<int64_t>(2 * c->nnz, 1 << 16);
+  const int cur = c->cur, other = 1 - c->cur;
+  if (c->cap[cur] < want || c->cap[other] < want) drop_graph(c);
+  state_grow_keep(c, cur, want, c->nnz);
+  state_grow_keep(c, other, want, 0);
+  ensure_sweep_capacity(c, std::max(c->cap[0], c->cap[1]));
+  double e = eps;
+  uint64_t eb = 0;
+  std::memcpy(&eb, &e, sizeof eb);
+  const std::vector<uint64_t> key = {
+      (uint64_t)c->lev, eb, (uint64_t)cur, (uint64_t)(uintptr_t)c->col[0], (uint64_t)(uintptr_t)c->col[1],
+      (uint64_t)(uintptr_t)c->val[0], (uint64_t)(uintptr_t)c->val[1], (uint64_t)(uintptr_t)c->rp[0],
+      (uint64_t)(uintptr_t)c->rp[1], (uint64_t)c->cap[0], (uint64_t)c->cap[1], (uint64_t)(uintptr_t)c->ws_eta,
+      (uint64_t)(uintptr_t)c->tmp_col, (uint64_t)(uintptr_t)c->alpha[0], (uint64_t)(uintptr_t)c->alpha[1],
+      (uint64_t)(uintptr_t)c->anchor[0], (uint64_t)(uintptr_t)c->anchor[1], (uint64_t)c->ws_cap,
+      (uint64_t)threads_per_cell(c), (uint64_t)(int64_t)c->opt.max_cluster_cells, (uint64_t)c->opt.x_newton,
+      (uint64_t)(uintptr_t)c->cell_off};
+  if (!c->graph_exec || key != c->graph_key) {
+    drop_graph(c);
+    cudaGraph_t graph = nullptr;
+    DD_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      DD_CUDA(cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream));
+      enqueue_half_sweep(c, 0, eps, cur, other, 0);
+      enqueue_half_sweep(c, 1, eps, other, cur, 1);
+      DD_CUDA(cudaMemcpyAsync(c->h_err_g, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    } catch (...) {
+      cudaStreamEndCapture(c->stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    DD_CUDA(cudaStreamEndCapture(c->stream, &graph));
+    const cudaError_t ie = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      c->graph_exec = nullptr;
+      throw DdError{DD_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie)};
+    }
+    c->graph_key = key;
+  }
+  DD_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
+  DD_CUDA(cudaStreamSynchronize(c->stream));
+  const int err = *c->h_err_g;
+  const int ncA = num_cells(0, h.nb), ncB = num_cells(1, h.nb);
+  if (err & 2) throw DdError{DD_ERR_NUMERIC, "a cell solve produced a non-finite value"};
+  if (err & (4 | 8)) {
+    drop_graph(c);
+    if (c->h_nnz_g[0] > c->cap[other]) {
+      // A did not fit: its input is untouched
+      half_sweep(c, 0, eps);
+      half_sweep(c, 1, eps);
+    } else {
+      // A is complete in `other`; B did not fit
+      account_half_sweep(c, c->h_tot_g[0], ncA);
+      c->cur = other;
+      c->nnz = c->h_nnz_g[0];
+      c->last_part = 0;
+      c->eps_cur = eps;
+      half_sweep(c, 1, eps);
+    }
+    return;
+  }
+  (void)nrows;
+  account_half_sweep(c, c->h_tot_g[0], ncA);
+  account_half_sweep(c, c->h_tot_g[1], ncB);
+  c->nnz = c->h_nnz_g[1];
+  c->last_part = 1;
+  c->eps_cur = eps;
+  c->last_tot = c->h_tot_g[1];
+  c->part_eps[0] = c->part_eps[1] = eps;
+  c->part_lev[0] = c->part_lev[1] = c->lev;
+}
+
 // advance the schedule by one sweep (refining first if the step asks for it)
 void one_sweep(dd_ctx* c) {
   while (c->step < c->sched.size() && c->sched[c->step].sweeps <= 0) {
@@ -764,8 +948,17 @@ void one_sweep(dd_ctx* c) {
   }
   const dd_eps_step& s = c->step < c->sched.size() ? c->sched[c->step] : c->sched.back();
   while (c->lev < s.level) refine(c);
-  half_sweep(c, 0, s.eps);
-  half_sweep(c, 1, s.eps);
+  // graph replay for a sweep at the (level, ε) of the previous one, when no
+  // learned warm start or debugging step has to run in between
+  const bool same = !c->need_init && c->last_part == 1 && c->part_lev[0] == c->lev && c->part_lev[1] == c->lev &&
+                    c->part_eps[0] == s.eps && c->part_eps[1] == s.eps;
+  if (c->opt.mode == 1 && same && c->opt.debug_flags == 0 && c->opt.warm != 3 && !c->trace_buf &&
+      !c->cell_times) {
+    graph_sweep(c, s.eps);
+  } else {
+    half_sweep(c, 0, s.eps);
+    half_sweep(c, 1, s.eps);
+  }
   ++c->sweeps_done;
   if (c->step < c->sched.size()) {
     if (++c->step_done >= c->sched[c->step].sweeps) {
@@ -804,6 +997,7 @@ void dd_options_default(dd_options* opt) {
   opt->max_cluster_cells = -1;
   opt->x_newton = 1;
   opt->warm = 0;
+  opt->mode = 0;
   opt->stream = nullptr;
   opt->debug_flags = 0;
 }
@@ -885,6 +1079,10 @@ dd_status dd_create(const double* mu, const double* nu, const dd_grid* grid, int
     DD_CUDA(cudaEventCreate(&c->ev_c0));
     DD_CUDA(cudaEventCreate(&c->ev_c1));
     dev_alloc(c->nbig, 1);
+    dev_alloc(c->work_next, 1);
+    DD_CUDA(cudaMallocHost((void**)&c->h_tot_g, 2 * sizeof(SweepTotals)));
+    DD_CUDA(cudaMallocHost((void**)&c->h_nnz_g, 2 * sizeof(int64_t)));
+    DD_CUDA(cudaMallocHost((void**)&c->h_err_g, sizeof(int)));
     if (const char* tr = std::getenv("DD_TRACE_CELL")) {
       if (std::sscanf(tr, "%d,%d", &c->trace_part, &c->trace_cell) == 2) {
         dev_alloc(c->trace_buf, 1024);

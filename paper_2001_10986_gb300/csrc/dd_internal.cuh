@@ -126,6 +126,8 @@ struct SweepArgs {
   int* err_flag;
   const int32_t* order;     // launch order of the cells (NULL: natural order)
   const int* nbig;          // the first *nbig cells of `order` are solved by clusters (NULL: none)
+  int* work_next;           // persistent per-CTA solves: next position of `order` to take
+                            // (NULL: one CTA per cell)
   int max_big;              // upper limit for *nbig (≤ 256)
   int32_t* iters_hist;      // iterations of each cell's last solve in this partition
   int trace_cell;           // debug: cell whose per-iteration error is recorded (-1: none)
@@ -137,9 +139,13 @@ struct SweepArgs {
 cudaError_t launch_gather(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_order(const SweepArgs& a, int32_t* order, int* nbig, cudaStream_t s);
 cudaError_t launch_sinkhorn_cluster(const SweepArgs& a, cudaStream_t s);
-cudaError_t launch_sinkhorn(const SweepArgs& a, int threads, cudaStream_t s);
-cudaError_t launch_row_scan(const int32_t* cnt, int64_t* rp_out, int64_t* tile_sum, int nrows,
-                            cudaStream_t s);
+// per-CTA cell solves; persistent: one wave of CTAs that take cells from
+// a.work_next (which must be 0 at launch) until none are left
+cudaError_t launch_sinkhorn(const SweepArgs& a, int threads, cudaStream_t s, bool persistent = false);
+// exclusive scan of the row lengths into rp_out[0..nrows]; skipped when
+// *err_flag (nullable) is non-zero
+cudaError_t launch_row_scan(const int32_t* cnt, int64_t* rp_out, int64_t* tile_sum, int nrows, cudaStream_t s,
+                            const int* err_flag = nullptr);
 // rp_out[i] = tile_off[tile] + prefix within the tile; with tmp_col != NULL the
 // kept entries of each row are copied to col_out/val_out (capacity cap_out)
 cudaError_t launch_compact(const int32_t* cnt, const int64_t* src, const int64_t* tile_off,

@@ -12,6 +12,7 @@
 //               next level.
 //
 // All kernels are plain launches; none of them waits on another CTA.
+#include <algorithm>
 #include <atomic>
 #include "dd_internal.cuh"
 
@@ -1358,16 +1359,37 @@ __device__ void solve_cell(const SweepArgs& a, int J, SinkSmem& sm, int rank, fl
 // one CTA per cell, for the cells after the first nbig of the launch order
 __global__ void __maxnreg__(168) k_sinkhorn(SweepArgs a) {
   __shared__ SinkSmem sm;
-  const int nbig = a.nbig ? *a.nbig : 0;
-  const int pos = nbig + blockIdx.x;
-  if (pos >= a.ncells) return;
-  const int J = a.order ? a.order[pos] : pos;
-  if (*a.err_flag & 4) return;
+  __shared__ int s_pos, s_stop;
   extern __shared__ float4 ys_small[];
-  if (a.cell_times && threadIdx.x == 0) a.cell_times[2 * J] = globaltimer();
-  // dynamic shared memory: the staged support points, then the Newton buffer
-  solve_cell<1, kMaxHW / 32>(a, J, sm, 0, ys_small, kStageSmall, reinterpret_cast<float*>(ys_small + kStageSmall));
-  if (a.cell_times && threadIdx.x == 0) a.cell_times[2 * J + 1] = globaltimer();
+  const int nbig = a.nbig ? *a.nbig : 0;
+  // one cell per CTA, or (persistent) cells taken in launch order from a
+  // counter until none are left. The capacity bits of err_flag (4: workspace,
+  // set by the gather; 8: output, set by an earlier compaction) do not change
+  // while this kernel runs: every thread reads the same value.
+  for (int round = 0;; ++round) {
+    int pos, stop;
+    if (a.work_next) {
+      if (threadIdx.x == 0) {
+        s_pos = atomicAdd(a.work_next, 1);
+        s_stop = *a.err_flag & (4 | 8);
+      }
+      __syncthreads();
+      pos = nbig + s_pos;
+      stop = s_stop;
+      __syncthreads();   // every thread has read s_pos before it is overwritten
+    } else {
+      if (round > 0) break;
+      pos = nbig + blockIdx.x;
+      stop = *a.err_flag & (4 | 8);
+    }
+    if (pos >= a.ncells || stop) break;
+    const int J = a.order ? a.order[pos] : pos;
+    if (a.cell_times && threadIdx.x == 0) a.cell_times[2 * J] = globaltimer();
+    // dynamic shared memory: the staged support points, then the Newton buffer
+    solve_cell<1, kMaxHW / 32>(a, J, sm, 0, ys_small, kStageSmall, reinterpret_cast<float*>(ys_small + kStageSmall));
+    if (a.cell_times && threadIdx.x == 0) a.cell_times[2 * J + 1] = globaltimer();
+    __syncthreads();     // the cell's shared memory is free for the next one
+  }
 }
 
 // a cluster of kClusterCTAs CTAs per cell, for the first nbig cells of the
@@ -1378,7 +1400,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256, 2) k
   if (c >= *a.nbig) return;   // uniform over the cluster
   const int rank = (int)cg::this_cluster().block_rank();
   const int J = a.order[c];
-  if (*a.err_flag & 4) return;
+  if (*a.err_flag & (4 | 8)) return;
   extern __shared__ float4 ys_big[];
   if (a.cell_times && threadIdx.x == 0 && rank == 0) a.cell_times[2 * J] = globaltimer();
   // dynamic shared memory: the staged support points, then the Newton buffer
@@ -1393,6 +1415,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256, 2) k
 // sort over 32 logarithmic buckets, one CTA.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_order(SweepArgs a, int32_t* order, int* nbig) {
+  if (*a.err_flag) return;   // an earlier step failed: nothing to order
   // buckets [0, 64): cells for clusters, [64, 128): cells for one CTA each;
   // half-octave buckets of predicted work inside each class, heaviest first
   constexpr int NB = 128;
@@ -1439,7 +1462,9 @@ __global__ void __launch_bounds__(1024) k_order(SweepArgs a, int32_t* order, int
 // ---------------------------------------------------------------------------
 constexpr int kScanTile = 1024;
 
-__global__ void __launch_bounds__(kScanTile) k_scan_tiles(const int32_t* cnt, int64_t* tile_sum, int n) {
+__global__ void __launch_bounds__(kScanTile) k_scan_tiles(const int32_t* cnt, int64_t* tile_sum, int n,
+                                                          const int* err_flag) {
+  if (err_flag && *err_flag) return;   // an earlier step failed: the rows stay as they are
   __shared__ long long ws[32];
   const int i = blockIdx.x * kScanTile + threadIdx.x;
   long long v = i < n ? cnt[i] : 0;
@@ -1448,7 +1473,8 @@ __global__ void __launch_bounds__(kScanTile) k_scan_tiles(const int32_t* cnt, in
 }
 
 __global__ void __launch_bounds__(kScanTile) k_scan_top(int64_t* tile_sum, int ntiles, int64_t* rp_out,
-                                                        int nrows) {
+                                                        int nrows, const int* err_flag) {
+  if (err_flag && *err_flag) return;
   __shared__ long long lws[32];
   long long carry = 0;
   for (int t0 = 0; t0 < ntiles; t0 += kScanTile) {
@@ -1490,6 +1516,7 @@ __global__ void __launch_bounds__(kScanTile) k_compact(const int32_t* cnt, const
                                                        int64_t cap_out, int nrows, int* err_flag) {
   __shared__ int iws[32];
   __shared__ int64_t s_start[kScanTile];
+  if (*err_flag) return;   // an earlier step failed: leave the output rows alone
   const int i = blockIdx.x * kScanTile + threadIdx.x;
   const int c = i < nrows ? cnt[i] : 0;
   int tot;
@@ -1498,7 +1525,7 @@ __global__ void __launch_bounds__(kScanTile) k_compact(const int32_t* cnt, const
   if (i < nrows) rp_out[i] = start;
   s_start[threadIdx.x] = start;
   __syncthreads();
-  if (tmp_col == nullptr || *err_flag) return;
+  if (tmp_col == nullptr) return;
   // warp-cooperative copies, one row per warp at a time
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int r = warp; r < kScanTile; r += kScanTile / 32) {
@@ -1828,13 +1855,38 @@ static cudaError_t ensure_dyn_smem(K kernel, int bytes, std::atomic<bool>* done)
   return e;
 }
 
-cudaError_t launch_sinkhorn(const SweepArgs& a, int threads, cudaStream_t s) {
+cudaError_t launch_sinkhorn(const SweepArgs& a, int threads, cudaStream_t s, bool persistent) {
   static std::atomic<bool> done[64];
   if (threads != 32 && threads != 64 && threads != 128 && threads != 256) threads = 128;
   const int smem = (int)(kStageSmall * sizeof(float4) + kNewtonFloats * sizeof(float));
-  const cudaError_t e = ensure_dyn_smem(k_sinkhorn, smem, done);
+  cudaError_t e = ensure_dyn_smem(k_sinkhorn, smem, done);
   if (e != cudaSuccess) return e;
-  k_sinkhorn<<<a.ncells, threads, smem, s>>>(a);
+  int grid = a.ncells;
+  if (persistent) {
+    // resident CTAs on the whole GPU, per device and block size, queried once
+    // (so that a launch inside a stream capture makes no query)
+    static std::atomic<int> wave[64][4];
+    if (!a.work_next) return cudaErrorInvalidValue;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    const int ti = threads == 32 ? 0 : threads == 64 ? 1 : threads == 128 ? 2 : 3;
+    int w = (dev >= 0 && dev < 64) ? wave[dev][ti].load() : 0;
+    if (w <= 0) {
+      int sms = 0, per_sm = 0;
+      if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sinkhorn, threads, smem)) != cudaSuccess)
+        return e;
+      w = sms * std::max(per_sm, 1);
+      if (dev >= 0 && dev < 64) wave[dev][ti].store(w);
+    }
+    grid = std::max(1, std::min(a.ncells, w));
+  } else {
+    SweepArgs b = a;
+    b.work_next = nullptr;
+    k_sinkhorn<<<grid, threads, smem, s>>>(b);
+    return cudaGetLastError();
+  }
+  k_sinkhorn<<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1848,10 +1900,10 @@ cudaError_t launch_sinkhorn_cluster(const SweepArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_row_scan(const int32_t* cnt, int64_t* rp_out, int64_t* tile_sum, int nrows,
-                            cudaStream_t s) {
+                            cudaStream_t s, const int* err_flag) {
   const int ntiles = (nrows + kScanTile - 1) / kScanTile;
-  k_scan_tiles<<<ntiles, kScanTile, 0, s>>>(cnt, tile_sum, nrows);
-  k_scan_top<<<1, kScanTile, 0, s>>>(tile_sum, ntiles, rp_out, nrows);
+  k_scan_tiles<<<ntiles, kScanTile, 0, s>>>(cnt, tile_sum, nrows, err_flag);
+  k_scan_top<<<1, kScanTile, 0, s>>>(tile_sum, ntiles, rp_out, nrows, err_flag);
   return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ class dd_eps_step(C.Structure):
 class dd_options(C.Structure):
     _fields_ = [("err_tol", C.c_double), ("trunc", C.c_double), ("max_iter", C.c_int32),
                 ("threads_per_cell", C.c_int32), ("max_cluster_cells", C.c_int32), ("x_newton", C.c_int32),
-                ("warm", C.c_int32), ("stream", C.c_void_p),
+                ("warm", C.c_int32), ("mode", C.c_int32), ("stream", C.c_void_p),
                 ("debug_flags", C.c_uint64)]
 
 

@@ -116,7 +116,7 @@ def test_learned_warm_start_gains_over_plain(lib):
     nu = syn.gaussian_mixture(n, 5, 301)
     res = {}
     for warm in (0, 1):
-        g = lib.DD(mu, nu, b, L, sched, err_tol=1e-7, warm=warm)
+        g = lib.DD(mu, nu, b, L, sched, err_tol=1e-7, warm=2 * warm)
         if warm:
             g.attach_mlp(net)
         g.run_schedule()

@@ -230,3 +230,23 @@ def test_newton_x_iteration_matches_oracle(lib, ref_spread, newton):
     got = _dense_rows(rp, col, val, 16 * 16)
     assert _rel_l1(got, odd.rows_to_dense(ref.rows, 16 * 16)) < PLAN_TOL
     assert abs(cost - ref.history[-1][3].cost) / ref.history[-1][3].cost < COST_TOL
+
+
+def test_graph_mode_matches_oracle_and_per_kernel_mode(lib, ref32):
+    # mode 1: persistent per-CTA solves and sweeps 2..4 replayed from a captured
+    # graph; the cells are solved by the same arithmetic, so the state equals
+    # the per-kernel mode's bit for bit
+    mu, nu, sched, ref = ref32
+    out = {}
+    for mode in (0, 1):
+        g = lib.DD(mu, nu, 4, 1, sched, err_tol=1e-7, mode=mode)
+        g.run_schedule()
+        out[mode] = (g.basic_marginals(), g.cost(with_y=False)[0], g.profile().half_sweeps)
+        g.close()
+    (rp0, c0, v0), cost0, hs0 = out[0]
+    (rp1, c1, v1), cost1, hs1 = out[1]
+    assert hs0 == hs1 == 8
+    assert np.array_equal(rp0, rp1) and np.array_equal(c0, c1) and np.array_equal(v0, v1)
+    assert cost0 == cost1
+    got = _dense_rows(rp1, c1, v1, 32 * 32)
+    assert _rel_l1(got, odd.rows_to_dense(ref.rows, 32 * 32)) < PLAN_TOL
