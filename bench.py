@@ -64,6 +64,7 @@ def parse():
     p.add_argument("--tpc", type=int, default=0, help="threads per cell solve (0: library choice)")
     p.add_argument("--clusters", type=int, default=-1, help="max cells solved by 8-CTA clusters (-1: library choice)")
     p.add_argument("--mode", type=int, default=1, help="0: per-kernel launches, 1: persistent solves + graph-replayed sweeps")
+    p.add_argument("--autotune", type=int, default=1, help="1: pick threads per cell and cluster cells by dd_autotune first")
     return p.parse_args()
 
 
@@ -267,6 +268,10 @@ def run_cuda(args):
     g = dd.DD(mu, nu, b, L, sched, err_tol=args.err, stream=stream, debug_flags=2 if args.mode == 0 else 0,
               threads_per_cell=args.tpc, max_cluster_cells=args.clusters, mode=args.mode)
     g.run_schedule()
+    tuned = None
+    if args.autotune:
+        # untimed: 9 more sweeps at the final ε, one per launch-schedule candidate
+        tuned = g.autotune(rounds=1)
     torch.cuda.synchronize()
     g.reset_profile()
     lvl, nl, _, eps, nnz0 = g.info()
@@ -294,7 +299,8 @@ def run_cuda(args):
         # kernel durations for the roofline: the same sweeps with per-kernel
         # launches and CUDA events (a graph replay has no per-kernel events)
         gk = dd.DD(mu, nu, b, L, sched, err_tol=args.err, stream=stream, debug_flags=2,
-                   threads_per_cell=args.tpc, max_cluster_cells=args.clusters, mode=0)
+                   threads_per_cell=tuned[0] if tuned else args.tpc,
+                   max_cluster_cells=tuned[1] if tuned else args.clusters, mode=0)
         gk.run_schedule()
         gk.reset_profile()
         for _ in range(min(args.steps, 3)):
@@ -391,7 +397,9 @@ def run_cuda(args):
            "config": {"workload": args.workload, "n": n, "b": b, "levels": L, "eps_final": eps,
                       "err_tol": args.err, "nnz": nnz0, "l2": "working set larger than L2 (CSR + workspace)",
                       "parallelism": f"replicas x{world} (independent image pairs)",
-                      "mode": "persistent solves + graph-replayed sweeps" if args.mode == 1 else "per-kernel launches"},
+                      "mode": "persistent solves + graph-replayed sweeps" if args.mode == 1 else "per-kernel launches",
+                      "autotuned": None if tuned is None else {"threads_per_cell": tuned[0],
+                                                                "max_cluster_cells": tuned[1]}},
            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "time_to_converged": ttc,
            "gpu_launches": int(prof.launches), "clocks": clk.summary(),
            "quality": {"cost": cost, "err_x": ex, "err_y": ey, "max_iters_last": st.max_iters,

@@ -273,6 +273,16 @@ dd_status dd_solve_cell_noalloc(const double* mu, int32_t b, double spacing, int
                                 double eps, double err_tol, int32_t max_iter, double trunc,
                                 double* alpha, double* nu_basic, void* stream);
 
+/* Autotuner of the launch schedule (no counterpart in the paper). Runs
+ * `rounds` × 9 sweeps of the schedule (real sweeps: they advance the state
+ * like dd_sweep), one per candidate of threads_per_cell ∈ {64, 128, 256} ×
+ * max_cluster_cells ∈ {0, 64, 256} in turn, times each with CUDA events,
+ * scores it by time per unit of algorithmic work (2 FMAs per kernel entry,
+ * 64·65/2 per support point of a Newton step) and keeps the best candidate in
+ * the context's options (reported in threads, clusters; nullable).
+ * 1 ≤ rounds ≤ 16. */
+dd_status dd_autotune(dd_ctx* ctx, int32_t rounds, int32_t* threads, int32_t* clusters);
+
 /* ---- learned warm start (no counterpart in the paper) -------------------
  * A network of 1089 inputs, two hidden layers of 256 (ReLU) and 64 outputs,
  * y = W3·relu(W2·relu(W1·x + b1) + b2) + b3, with bfloat16 weights (rounded

@@ -1362,6 +1362,58 @@ void dd_destroy(dd_ctx* c) {
   delete c;
 }
 
+dd_status dd_autotune(dd_ctx* c, int32_t rounds, int32_t* threads, int32_t* clusters) {
+  return guarded(c, [&] {
+    if (rounds < 1 || rounds > 16) throw DdError{DD_ERR_ARG, "rounds must be in 1..16"};
+    static const int kThreads[] = {64, 128, 256};
+    static const int kClusters[] = {0, 64, 256};
+    constexpr int NC = 9;
+    double best[NC];
+    for (double& b : best) b = 1e300;
+    const dd_options keep = c->opt;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DD_CUDA(cudaEventCreate(&e0));
+    DD_CUDA(cudaEventCreate(&e1));
+    try {
+      for (int r = 0; r < rounds; ++r)
+        for (int k = 0; k < NC; ++k) {
+          c->opt.threads_per_cell = kThreads[k / 3];
+          c->opt.max_cluster_cells = kClusters[k % 3];
+          c->opt.debug_flags = 0;
+          drop_graph(c);
+          const double w0 = 2.0 * c->prof.kernel_evals + (65.0 / 128.0) * c->prof.hessian_fma;
+          DD_CUDA(cudaEventRecord(e0, c->stream));
+          one_sweep(c);
+          DD_CUDA(cudaEventRecord(e1, c->stream));
+          DD_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          DD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          const double w1 = 2.0 * c->prof.kernel_evals + (65.0 / 128.0) * c->prof.hessian_fma;
+          // time per unit of algorithmic work: later sweeps solve faster as
+          // the decomposition converges, so raw times would favour them
+          const double score = w1 > w0 ? (double)ms / (w1 - w0) : 1e300;
+          best[k] = std::min(best[k], score);
+        }
+    } catch (...) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      c->opt = keep;
+      throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int kb = 0;
+    for (int k = 1; k < NC; ++k)
+      if (best[k] < best[kb]) kb = k;
+    c->opt = keep;
+    c->opt.threads_per_cell = kThreads[kb / 3];
+    c->opt.max_cluster_cells = kClusters[kb % 3];
+    drop_graph(c);
+    if (threads) *threads = c->opt.threads_per_cell;
+    if (clusters) *clusters = c->opt.max_cluster_cells;
+  });
+}
+
 dd_status dd_attach_mlp(dd_ctx* c, dd_mlp* m) {
   return guarded(c, [&] { c->mlp = m; });
 }

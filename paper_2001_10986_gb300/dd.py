@@ -97,11 +97,13 @@ _lib.dd_mlp_forward.argtypes = [_P, _P, C.c_int64, _P, _P]
 _lib.dd_mlp_loss_grad.argtypes = [_P, _P, _P, C.c_int64, C.POINTER(C.c_double), _P, _P]
 _lib.dd_mlp_train_step.argtypes = [_P, _P, _P, C.c_int64, C.c_float, C.POINTER(C.c_double), _P]
 _lib.dd_attach_mlp.argtypes = [_P, _P]
+_lib.dd_autotune.argtypes = [_P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
 _lib.dd_cell_training_pairs.argtypes = [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_int64)]
 for _f in ("dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep", "dd_run_schedule", "dd_cost",
            "dd_get_basic_marginals", "dd_get_plan", "dd_get_duals", "dd_get_info", "dd_get_profile",
            "dd_reset_profile", "dd_get_cell_stats", "dd_mlp_create", "dd_mlp_get_params", "dd_mlp_set_params",
-           "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step", "dd_attach_mlp", "dd_cell_training_pairs"):
+           "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step", "dd_attach_mlp", "dd_cell_training_pairs",
+           "dd_autotune"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep",
@@ -109,7 +111,7 @@ EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", 
             "dd_get_info", "dd_get_cell_stats", "dd_get_profile", "dd_reset_profile", "dd_destroy",
             "dd_last_error", "dd_solve_cell_noalloc", "dd_mlp_num_params", "dd_mlp_create", "dd_mlp_destroy",
             "dd_mlp_get_params", "dd_mlp_set_params", "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step",
-            "dd_attach_mlp", "dd_cell_training_pairs")
+            "dd_attach_mlp", "dd_cell_training_pairs", "dd_autotune")
 
 
 def _check(ctx, st):
@@ -295,6 +297,13 @@ def dd_mlp_train_step(mlp, x_ptr, t_ptr, n, lr, stream=None):
     return loss.value
 
 
+def dd_autotune(ctx, rounds=2):
+    """Returns the chosen (threads_per_cell, max_cluster_cells)."""
+    t, cl = C.c_int32(), C.c_int32()
+    _check(ctx, _lib.dd_autotune(ctx, int(rounds), C.byref(t), C.byref(cl)))
+    return t.value, cl.value
+
+
 def dd_attach_mlp(ctx, mlp):
     _check(ctx, _lib.dd_attach_mlp(ctx, mlp))
 
@@ -369,6 +378,9 @@ class DD:
 
     def reset_profile(self):
         dd_reset_profile(self.ctx)
+
+    def autotune(self, rounds=2):
+        return dd_autotune(self.ctx, rounds)
 
     def attach_mlp(self, mlp):
         """Attach an MLP (or None); its handle must outlive the attachment."""

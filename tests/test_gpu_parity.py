@@ -250,3 +250,17 @@ def test_graph_mode_matches_oracle_and_per_kernel_mode(lib, ref32):
     assert cost0 == cost1
     got = _dense_rows(rp1, c1, v1, 32 * 32)
     assert _rel_l1(got, odd.rows_to_dense(ref.rows, 32 * 32)) < PLAN_TOL
+
+
+def test_autotune_picks_a_candidate_and_keeps_the_state_feasible(lib):
+    # 9 tuning sweeps are real sweeps: the state stays feasible and converges
+    mu = syn.gaussian_mixture(32, 3, 70)
+    nu = syn.gaussian_mixture(32, 3, 71)
+    g = lib.DD(mu, nu, 4, 1, [(0.004, 2, 0)], err_tol=1e-7, mode=1)
+    g.run_schedule()
+    t, cl = g.autotune(rounds=1)
+    assert t in (64, 128, 256) and cl in (0, 64, 256)
+    assert g.profile().half_sweeps == 2 * (2 + 9)
+    cost, ex, ey = g.cost()
+    g.close()
+    assert ey < 1e-12 and ex < 1e-5 and cost > 0
