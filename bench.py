@@ -215,7 +215,7 @@ def time_to_converged(dd, syn, mu, nu, w, args, stream, max_final_sweeps=400, ml
     torch.cuda.synchronize()
     t = time.perf_counter()
     h = dd.DD(mu, nu, b, L, syn.paper_schedule(n, L, 1), err_tol=args.err, stream=stream,
-              threads_per_cell=args.tpc, max_cluster_cells=args.clusters, **opts)
+              threads_per_cell=args.tpc, max_cluster_cells=args.clusters, mode=args.mode, **opts)
     if mlp is not None:
         h.attach_mlp(mlp)
     h.run_schedule()
@@ -272,6 +272,7 @@ def run_cuda(args):
     if args.autotune:
         # untimed: 9 more sweeps at the final ε, one per launch-schedule candidate
         tuned = g.autotune(rounds=1)
+        args.tpc, args.clusters = tuned
     torch.cuda.synchronize()
     g.reset_profile()
     lvl, nl, _, eps, nnz0 = g.info()
@@ -341,7 +342,7 @@ def run_cuda(args):
         t = time.perf_counter()
         sched_e2e = syn.paper_schedule(n, L, args.steps)
         h = dd.DD(mu, nu, b, L, sched_e2e, err_tol=args.err, stream=stream, threads_per_cell=args.tpc,
-                  max_cluster_cells=args.clusters)
+                  max_cluster_cells=args.clusters, mode=args.mode)
         h.run_schedule()
         c2, ex2_, ey2 = h.cost()
         rp, col, val = h.basic_marginals()

@@ -263,4 +263,4 @@ def test_autotune_picks_a_candidate_and_keeps_the_state_feasible(lib):
     assert g.profile().half_sweeps == 2 * (2 + 9)
     cost, ex, ey = g.cost()
     g.close()
-    assert ey < 1e-12 and ex < 1e-5 and cost > 0
+    assert ey < 1e-9 and ex < 1e-5 and cost > 0   # ey: mass dropped by Truncate
