@@ -171,6 +171,8 @@ __device__ __forceinline__ uint64_t frac_to_u64(float f) {
 // ---------------------------------------------------------------------------
 // S1: gather ν_cell (Algorithm 2, line "ν_cell ← Σ_{i∈J} ν_i")
 // ---------------------------------------------------------------------------
+constexpr int kGatherStage = 3072;   // entries of a cell's rows staged in shared memory
+
 __global__ void __launch_bounds__(256) k_gather(SweepArgs a) {
   const int J = blockIdx.x;
   if (*a.err_flag) return;
@@ -178,6 +180,9 @@ __global__ void __launch_bounds__(256) k_gather(SweepArgs a) {
   const CellGeom g = cell_geom(a.part, J, L.nb, L.b);
   __shared__ int64_t rs[4];
   __shared__ int64_t rl[4];
+  __shared__ int64_t rb[4];   // start of each row in the staged copy
+  __shared__ int32_t s_col[kGatherStage];
+  __shared__ uint64_t s_val[kGatherStage];
   __shared__ int nrows;
   __shared__ int64_t s_off, s_tot;
   __shared__ int s_anchor[2];
@@ -192,6 +197,7 @@ __global__ void __launch_bounds__(256) k_gather(SweepArgs a) {
         int bi = (g.bi0 + kr) * L.nb + g.bj0 + kc;
         rs[k] = a.rp[bi];
         rl[k] = a.rp[bi + 1] - a.rp[bi];
+        rb[k] = tot;
         tot += rl[k];
         ++k;
       }
@@ -209,6 +215,19 @@ __global__ void __launch_bounds__(256) k_gather(SweepArgs a) {
   __syncthreads();
   const int64_t off = s_off, tot = s_tot;
   if (off < 0) return;
+  // the rows, concatenated, in shared memory when they fit: the binary
+  // searches below then read shared memory instead of L2
+  const bool staged = tot <= kGatherStage;
+  if (staged) {
+    for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+      int r = 0;
+      int64_t k = e;
+      while (k >= rl[r]) { k -= rl[r]; ++r; }
+      s_col[e] = a.col[rs[r] + k];
+      s_val[e] = a.val[rs[r] + k];
+    }
+    __syncthreads();
+  }
 
   // merge-path rank of every element of the ≤4 sorted rows
   float sw = 0.f, sr = 0.f, sc = 0.f;
@@ -216,12 +235,12 @@ __global__ void __launch_bounds__(256) k_gather(SweepArgs a) {
     int r = 0;
     int64_t k = e;
     while (k >= rl[r]) { k -= rl[r]; ++r; }
-    const int y = a.col[rs[r] + k];
-    const uint64_t v = a.val[rs[r] + k];
+    const int y = staged ? s_col[e] : a.col[rs[r] + k];
+    const uint64_t v = staged ? s_val[e] : a.val[rs[r] + k];
     int64_t rank = k;
     for (int r2 = 0; r2 < nrows; ++r2) {
       if (r2 == r) continue;
-      const int32_t* row = a.col + rs[r2];
+      const int32_t* row = staged ? s_col + rb[r2] : a.col + rs[r2];
       rank += (r2 < r) ? upper_bound_row(row, rl[r2], y) : lower_bound_row(row, rl[r2], y);
     }
     a.ws_ytmp[off + rank] = y;
@@ -1545,6 +1564,28 @@ __global__ void __launch_bounds__(kScanTile) k_compact(const int32_t* cnt, const
   }
 }
 
+// one warp per row: copy the row's kept entries into the output CSR at the
+// row start the scan gave (rp_out)
+__global__ void __launch_bounds__(256) k_copy_rows(const int32_t* cnt, const int64_t* src, const int64_t* rp_out,
+                                                   const int32_t* tmp_col, const uint64_t* tmp_val,
+                                                   int32_t* col_out, uint64_t* val_out, int64_t cap_out,
+                                                   int nrows, int* err_flag) {
+  const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= nrows || (*err_flag & ~8)) return;
+  const int len = cnt[row];
+  const int64_t dst = rp_out[row];
+  if (dst + len > cap_out) {
+    if (lane == 0) atomicOr(err_flag, 8);
+    return;
+  }
+  const int64_t s0 = src[row];
+  for (int k = lane; k < len; k += 32) {
+    col_out[dst + k] = tmp_col[s0 + k];
+    val_out[dst + k] = tmp_val[s0 + k];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // statistics
 // ---------------------------------------------------------------------------
@@ -1912,8 +1953,15 @@ cudaError_t launch_compact(const int32_t* cnt, const int64_t* src, const int64_t
                            int32_t* col_out, uint64_t* val_out, int64_t cap_out, int nrows,
                            int* err_flag, cudaStream_t s) {
   const int ntiles = (nrows + kScanTile - 1) / kScanTile;
-  k_compact<<<ntiles, kScanTile, 0, s>>>(cnt, src, tile_off, rp_out, tmp_col, tmp_val, col_out,
-                                         val_out, cap_out, nrows, err_flag);
+  // row starts per tile, then the copies with one warp per row (enough CTAs
+  // to cover the GPU)
+  k_compact<<<ntiles, kScanTile, 0, s>>>(cnt, src, tile_off, rp_out, nullptr, nullptr, col_out, val_out, cap_out,
+                                         nrows, err_flag);
+  if (tmp_col != nullptr) {
+    const int blocks = (int)(((int64_t)nrows * 32 + 255) / 256);
+    k_copy_rows<<<blocks, 256, 0, s>>>(cnt, src, rp_out, tmp_col, tmp_val, col_out, val_out, cap_out, nrows,
+                                       err_flag);
+  }
   return cudaGetLastError();
 }
 
