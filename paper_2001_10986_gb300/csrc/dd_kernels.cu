@@ -326,6 +326,8 @@ constexpr int kNewtonB = kNewtonZ + 64 * kNewtonN;
 constexpr int kNewtonFloats = kNewtonB + kNewtonN + 1;
 // largest |δ| of one Newton step in log u; a longer step is scaled down
 constexpr float kNewtonMaxStep = 4.0f;
+// Newton steps start only once the X-error is below this fraction of ‖μ_J‖
+constexpr float kNewtonNear = 0.05f;
 constexpr float kTwoTau = 65536.0f;   // scalings leave the band [2^-16, 2^16] → absorb
 
 struct SinkSmem {
@@ -626,13 +628,14 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   };
 
   bool stepped = false;
-  int nsteps = 0;
+  int nsteps = 0, nfail = 0;
+  float ncap = kNewtonMaxStep;   // largest |δ| of the next Newton step
   // Newton direction from the C of the last pass (each CTA's partial in its
   // nbuf): every CTA of the cluster sums the partials in the same order and
   // solves the same system, so all hold the same δ (in nbuf after the
   // matrix). Returns the step length in (0, 1], or −1 if a pivot is not
   // positive or δ is not finite.
-  auto newton_x_step = [&](float px_own) -> float {
+  auto newton_x_step = [&](float px_own, float cap) -> float {
     if constexpr (kNewtonShape) {
       float* M = nbuf;
       float* bv = nbuf + kNewtonB;
@@ -679,7 +682,7 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
         float rs = 0.f;
         for (int j = 0; j < HW; ++j)
           if (j != tid) rs += lam - M[tid * kNewtonLd + j];
-        M[tid * kNewtonLd + tid] = rs + lam + 1e-5f * px_own + 1e-7f * nuJ / (float)HW;
+        M[tid * kNewtonLd + tid] = rs + lam + 1e-4f * px_own + 1e-7f * nuJ / (float)HW;
         bv[tid] = sm.mu[tid] * mscale - px_own;
       } else if (tid < kNewtonN) {
         bv[tid] = 0.f;
@@ -724,12 +727,13 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
         }
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         fin = __all_sync(0xffffffffu, fin);
-        if (lane == 0) bv[kNewtonN] = fin ? fminf(1.0f, kNewtonMaxStep / fmaxf(m, 1e-30f)) : -1.0f;
+        if (lane == 0) bv[kNewtonN] = fin ? fminf(1.0f, cap / fmaxf(m, 1e-30f)) : -1.0f;
       }
       __syncthreads();
       return ok ? bv[kNewtonN] : -1.0f;
     } else {
       (void)px_own;
+      (void)cap;
       return -1.0f;
     }
   };
@@ -1059,18 +1063,27 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     // needs hundreds (cells whose support spreads far). The decision to take
     // it: an error below 5 % of ‖μ_J‖ and a contraction ρ > 0.75 over
     // iterations 3..6 or less than a tenfold error reduction over 16
-    // iterations. A step longer than kNewtonMaxStep in log u is scaled down;
-    // a step that does not lower the error turns Newton off for the rest of
-    // the solve.
+    // iterations. A step longer than the cap (kNewtonMaxStep in log u at
+    // first) is scaled down; after a step that does not lower the error the
+    // cap is quartered, and after three such steps the solve continues with
+    // the plain iteration.
     bool newton_step = false;
     float step_len = 0.f;
     if constexpr (kNewtonShape) {
       if (newton) {
+        bool take = true;
         if (stepped && ep > ep_before) {
-          newton = false;
-          newton_off = true;
-        } else {
-          step_len = newton_x_step(pxl[0]);
+          // the last step raised the error: shorter steps from here, and
+          // the plain iteration after three such steps
+          ncap *= 0.25f;
+          if (++nfail >= 3) {
+            newton = false;
+            newton_off = true;
+            take = false;
+          }
+        }
+        if (take) {
+          step_len = newton_x_step(pxl[0], ncap);
           newton_step = step_len > 0.f;
           if (newton_step) {
             ep_before = ep;
@@ -1084,7 +1097,7 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
       }
     }
     if (!newton_step && newton_ok && !newton_off && !newton) {
-      const bool near = ep < 0.05f * muJ;   // Newton steps from close to the solution only
+      const bool near = ep < kNewtonNear * muJ;   // not from far off: the steps are capped anyway
       if (it == 6 && rho6 > 0.75f && near) newton = true;
       if (it > 6 && (it & 15) == 0) {
         if (ep > 0.1f * e_mark && near) newton = true;
