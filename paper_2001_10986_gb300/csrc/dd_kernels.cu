@@ -1097,7 +1097,7 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
       }
     }
     if (!newton_step && newton_ok && !newton_off && !newton) {
-      const bool near = ep < kNewtonNear * muJ;   // not from far off: the steps are capped anyway
+      const bool near = ep < kNewtonNear * muJ;   // Newton steps only close to the solution
       if (it == 6 && rho6 > 0.75f && near) newton = true;
       if (it > 6 && (it & 15) == 0) {
         if (ep > 0.1f * e_mark && near) newton = true;
