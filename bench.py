@@ -176,6 +176,21 @@ def cpu_baseline(workload, n_cells):
     return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
 
 
+def replica_timing(ms_local, pg, device):
+    """The timed region's duration as the job sees it: the maximum over the
+    ranks of each rank's own duration (ms); pg is torch.distributed or None."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if pg:
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(n, steps, world, ms_max):
+    """px·sweeps/s of all replicas together: each rank sweeps its own n×n pair."""
+    return world * n * n * steps / (ms_max * 1e-3)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -311,11 +326,8 @@ def run_cuda(args):
         gk.close()
     else:
         prof_k = prof
-    t_rank = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-    if pg:
-        pg.all_reduce(t_rank, op=pg.ReduceOp.MAX)
-    ms_max = float(t_rank.item())
-    value = world * n * n * args.steps / (ms_max * 1e-3)
+    ms_max = replica_timing(ms_total, pg, "cuda")
+    value = whole_job_value(n, args.steps, world, ms_max)
 
     # ---- roofline of the cell-solve kernels (FP32 ALU) ----
     launches = max(prof_k.solve_launches, 1)
