@@ -688,60 +688,19 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
         bv[tid] = 0.f;
       }
       __syncthreads();
-      // LDLᵀ in place, in blocks of 8 columns: afterwards M(k,k) = D(k) and
-      // M(i,k) = L(i,k)·D(k) for i > k (lower triangle). Per block: warp 0
-      // factors the 8×8 diagonal block; each row below solves its 8 panel
-      // entries against it and writes them divided by D into S (the Z
-      // region, free here); the trailing lower triangle takes the rank-8
-      // update, its entries spread evenly over the threads.
-      constexpr int kB = 8;
-      float* S = nbuf + kNewtonZ;   // S[i·kB + t] = M(i, k0+t)/D(k0+t)
-      for (int k0 = 0; k0 < kNewtonN; k0 += kB) {
-        if (warp == 0) {
-          for (int kk = 0; kk < kB; ++kk) {
-            const float d = M[(k0 + kk) * kNewtonLd + k0 + kk];
-            const int a = lane;
-            if (a > kk && a < kB) {
-              const float lik = M[(k0 + a) * kNewtonLd + k0 + kk] / d;
-              for (int b = kk + 1; b <= a; ++b)
-                M[(k0 + a) * kNewtonLd + k0 + b] -= lik * M[(k0 + b) * kNewtonLd + k0 + kk];
-            }
-            __syncwarp();
-          }
-        }
-        __syncthreads();
-        const int kb = k0 + kB;
-        for (int i = kb + tid; i < kNewtonN; i += NT) {
-          float p[kB];
-#pragma unroll
-          for (int t = 0; t < kB; ++t) p[t] = M[i * kNewtonLd + k0 + t];
-#pragma unroll
-          for (int t = 0; t < kB; ++t) {
-            const float dt = M[(k0 + t) * kNewtonLd + k0 + t];
-#pragma unroll
-            for (int q = t + 1; q < kB; ++q) p[q] -= p[t] * M[(k0 + q) * kNewtonLd + k0 + t] / dt;
-            S[i * kB + t] = p[t] / dt;
-          }
-#pragma unroll
-          for (int t = 0; t < kB; ++t) M[i * kNewtonLd + k0 + t] = p[t];
-        }
-        __syncthreads();
-        const int m = kNewtonN - kb;
-        const int cnt = m * (m + 1) / 2;
-        for (int e = tid; e < cnt; e += NT) {
-          int ip = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-          while (ip * (ip + 1) / 2 > e) --ip;
-          while ((ip + 1) * (ip + 2) / 2 <= e) ++ip;
-          const int i = kb + ip, j = kb + (e - ip * (ip + 1) / 2);
-          float acc = 0.f;
-#pragma unroll
-          for (int t = 0; t < kB; ++t) acc = fmaf(M[i * kNewtonLd + k0 + t], S[j * kB + t], acc);
-          M[i * kNewtonLd + j] -= acc;
+      // LDLᵀ in place: afterwards M(k,k) = D(k), M(i,k) = L(i,k)·D(k) for i > k
+      bool ok = true;
+      for (int k = 0; k < kNewtonN; ++k) {
+        const float d = M[k * kNewtonLd + k];
+        ok = ok && d > 0.f;
+        const int i = tid & (kNewtonN - 1);
+        if (ok && i > k) {
+          const float lik = M[i * kNewtonLd + k] / d;
+          const int jstep = NT >> 6;   // thread groups of 64, one per column residue
+          for (int j = k + 1 + (tid >> 6); j <= i; j += jstep) M[i * kNewtonLd + j] -= lik * M[j * kNewtonLd + k];
         }
         __syncthreads();
       }
-      // every pivot D(k) must be positive
-      const bool ok = __syncthreads_and(tid >= kNewtonN || M[tid * kNewtonLd + tid] > 0.f) != 0;
       if (ok && warp == 0) {
         for (int k = 0; k < kNewtonN; ++k) {
           const float zk = bv[k] / M[k * kNewtonLd + k];
