@@ -395,6 +395,28 @@ def run_cuda(args):
                 res["training_pairs"] = int(sum(x.shape[0] for x in fs))
                 res["warm"] = mode
                 ttc["learned" if mode == 1 else "learned_every_eps"] = res
+            # the evaluation case of the learned warm start: 512², 6 blobs, the
+            # whole schedule with the previous duals and with the prediction
+            ev = {}
+            w5 = syn.WORKLOADS["gm512_b4"]
+            m5, n5 = syn.image_pair(w5, 0)
+            for mode in (0, 1):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                h = dd.DD(m5, n5, w5.b, w5.levels, syn.paper_schedule(w5.n, w5.levels, 3), err_tol=args.err,
+                          stream=stream, warm=mode, mode=args.mode)
+                if mode:
+                    h.attach_mlp(net)
+                h.run_schedule()
+                c5 = h.cost(with_y=False)[0]
+                torch.cuda.synchronize()
+                p5 = h.profile()
+                ev["learned" if mode else "previous_duals"] = {
+                    "seconds": time.perf_counter() - t0, "sinkhorn_iters": p5.sinkhorn_iters,
+                    "newton_steps": p5.newton_steps, "learned_cells": p5.learned_cells,
+                    "judged_cells": p5.judged_cells, "cost": c5}
+                h.close()
+            ttc["learned_eval_gm512_b4"] = ev
             net.close()
 
     if rank != 0:
