@@ -1475,7 +1475,16 @@ __global__ void __launch_bounds__(1024) k_order(SweepArgs a, int32_t* order, int
     const int b2 = min(63, (int)(2.0 * log2(fmax(w, 1.0))));
     return (w >= thr ? 0 : 64) + 63 - b2;
   };
-  for (int J = threadIdx.x; J < nc; J += blockDim.x) atomicAdd(&cnt[bucket(work(J))], 1);
+  // counts and positions with one shared-memory atomic per bucket and warp
+  // (most cells fall into a few buckets: per-cell atomics serialise)
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int base = 0; base < nc; base += blockDim.x) {
+    const int J = base + threadIdx.x;
+    const int bk = J < nc ? bucket(work(J)) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, bk);
+    if (bk >= 0 && (peers & lt) == 0) atomicAdd(&cnt[bk], __popc(peers));
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     int s = 0;
@@ -1486,7 +1495,16 @@ __global__ void __launch_bounds__(1024) k_order(SweepArgs a, int32_t* order, int
     }
   }
   __syncthreads();
-  for (int J = threadIdx.x; J < nc; J += blockDim.x) order[atomicAdd(&off[bucket(work(J))], 1)] = J;
+  for (int base = 0; base < nc; base += blockDim.x) {
+    const int J = base + threadIdx.x;
+    const int bk = J < nc ? bucket(work(J)) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, bk);
+    const int leader = __ffs(peers) - 1;
+    int pos0 = 0;
+    if (bk >= 0 && lane == leader) pos0 = atomicAdd(&off[bk], __popc(peers));
+    pos0 = __shfl_sync(0xffffffffu, pos0, leader);
+    if (bk >= 0) order[pos0 + __popc(peers & lt)] = J;
+  }
 }
 
 // ---------------------------------------------------------------------------
