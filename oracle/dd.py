@@ -260,11 +260,17 @@ def half_sweep(prob, part, rows, alpha, eps, params, plans=None, cells=None):
         cols, nu_cell = gather(rows, J)
         X = prob.cell_points(J)
         mu_x = prob.mu[X]
-        C = prob.cost(X, cols)
-        f0 = alpha[X] + eps * np.log(mu_x)
-        f, g, P, it, err_x = sinkhorn_cell(C, mu_x, nu_cell, f0, eps, params.err, params.max_iter)
-        alpha[X] = f - eps * np.log(mu_x)
-        info.cost += float((C * P).sum())
+        # the cell problem lives on the support of μ_J (§2: couplings of μ and
+        # ν); a pixel without mass carries no plan and keeps α = 0
+        live = mu_x > 0
+        C = prob.cost(X[live], cols)
+        f0 = alpha[X[live]] + eps * np.log(mu_x[live])
+        f, g, P_live, it, err_x = sinkhorn_cell(C, mu_x[live], nu_cell, f0, eps, params.err, params.max_iter)
+        alpha[X[live]] = f - eps * np.log(mu_x[live])
+        alpha[X[~live]] = 0.0
+        P = np.zeros((X.size, cols.size))
+        P[live] = P_live
+        info.cost += float((C * P_live).sum())
         info.err_x += float(err_x)
         info.iters.append(it)
         if plans is not None:

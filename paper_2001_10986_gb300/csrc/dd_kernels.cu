@@ -1348,7 +1348,8 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   for (int x = tid; x < HW; x += NT) {
     const int ar = x / g.W, ac = x - (x / g.W) * g.W;
     const int p = (g.r0 + ar) * L.n + g.c0 + ac;
-    a.alpha[p] = (sm.F[x] + lg2(sm.u[x]) - sm.l2mu[x]) * eln2;
+    // a pixel without mass has no potential (F = log2 μ = −∞): α = 0 there
+    a.alpha[p] = sm.mu[x] > 0.f ? (sm.F[x] + lg2(sm.u[x]) - sm.l2mu[x]) * eln2 : 0.f;
   }
   double cs = block_sum<double>(cost_acc, sm.dws);
   if (tid == 0) {

@@ -264,3 +264,28 @@ def test_autotune_picks_a_candidate_and_keeps_the_state_feasible(lib):
     cost, ex, ey = g.cost()
     g.close()
     assert ey < 1e-9 and ex < 1e-5 and cost > 0   # ey: mass dropped by Truncate
+
+
+def test_zero_mass_pixels(lib):
+    # pixels without mass (inside basic cells that have mass) in μ and in ν:
+    # their potentials are −∞ in the oracle; the plan must still match
+    n, b, eps = 16, 4, 0.01
+    mu = syn.gaussian_mixture(n, 2, 90)
+    nu = syn.gaussian_mixture(n, 2, 91)
+    mu[3, 5] = mu[9, 9] = mu[12, 0] = 0.0
+    nu[0, 0] = nu[7, 8] = nu[15, 15] = 0.0
+    mu /= mu.sum()
+    nu /= nu.sum()
+    sched = [(eps, 3, 0)]
+    with np.errstate(divide="ignore"):
+        ref = odd.run_schedule(mu, nu, b, 1, sched, odd.Params(err=1e-10))
+    g = lib.DD(mu, nu, b, 1, sched, err_tol=1e-7)
+    g.run_schedule()
+    rp, col, val = g.basic_marginals()
+    cost, ex, ey = g.cost()
+    g.close()
+    got = _dense_rows(rp, col, val, n * n)
+    want = odd.rows_to_dense(ref.rows, n * n)
+    assert np.all(got[:, [0, 7 * n + 8, n * n - 1]] == 0.0)
+    assert _rel_l1(got, want) < PLAN_TOL
+    assert abs(cost - ref.history[-1][3].cost) / ref.history[-1][3].cost < COST_TOL
