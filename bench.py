@@ -251,7 +251,7 @@ def time_to_converged(dd, syn, mu, nu, w, args, stream, max_final_sweeps=400, ml
     h.close()
     return {"seconds": dt, "final_sweeps": k, "last_rel_change": rel, "cost": cost, "err_x": ex, "err_y": ey,
             "sinkhorn_iters": p.sinkhorn_iters, "newton_steps": p.newton_steps,
-            "learned_cells": p.learned_cells, "judged_cells": p.judged_cells,
+            "learned_cells": p.learned_cells, "compared_cells": p.compared_cells,
             "criterion": "relative cost change over one final-ε sweep <= 1e-7"}
 
 
@@ -374,7 +374,7 @@ def run_cuda(args):
         ttc = {"plain": time_to_converged(dd, syn, mu, nu, w, args, stream)}
         if not args.no_learned:
             # learned warm start: network trained on pairs logged from plain
-            # runs on 256² images (5 blobs, 3 levels), judged cell by cell
+            # runs on 256² images (5 blobs, 3 levels), compared cell by cell
             from paper_2001_10986_gb300 import learned
             import torch
             t0 = time.perf_counter()
@@ -414,7 +414,7 @@ def run_cuda(args):
                 ev["learned" if mode else "previous_duals"] = {
                     "seconds": time.perf_counter() - t0, "sinkhorn_iters": p5.sinkhorn_iters,
                     "newton_steps": p5.newton_steps, "learned_cells": p5.learned_cells,
-                    "judged_cells": p5.judged_cells, "cost": c5}
+                    "compared_cells": p5.compared_cells, "cost": c5}
                 h.close()
             ttc["learned_eval_gm512_b4"] = ev
             net.close()

@@ -126,7 +126,8 @@ typedef struct {
                                 Σ over steps of 64²·N_y(J)                       */
   int64_t learned_cells;     /* cell solves that started from the predicted
                                 duals (warm ≠ 0)                                 */
-  int64_t judged_cells;      /* cell solves for which a prediction was judged   */
+  int64_t compared_cells;    /* cell solves whose prediction was compared with
+                                the previous duals                               */
 } dd_profile;
 
 /* Statistics of the last sweep run by dd_sweep / dd_run_schedule. */

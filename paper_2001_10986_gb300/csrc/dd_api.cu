@@ -424,7 +424,7 @@ void half_sweep(dd_ctx* c, int part, double eps) {
     a.cell_learned = c->cell_learned;
     DD_CUDA(launch_cell_features(a, c->feat, c->fanc, c->fok, c->stream));
     DD_CUDA(mlp_forward(c->mlp, c->feat, a.ncells, c->pred, c->stream));
-    DD_CUDA(launch_judge(a, c->pred, c->fanc, c->fok, c->stream));
+    DD_CUDA(launch_warm_compare(a, c->pred, c->fanc, c->fok, c->stream));
     c->prof.launches += 7;
     check_debug(c, "learned warm start");
   }
@@ -491,7 +491,7 @@ void half_sweep(dd_ctx* c, int part, double eps) {
   c->prof.hessian_fma += c->last_tot.hessian_fma;
   if (a.cell_learned) {
     c->prof.learned_cells += c->last_tot.learned;
-    c->prof.judged_cells += c->last_tot.judged;
+    c->prof.compared_cells += c->last_tot.compared;
   }
   c->prof.cells += a.ncells;
   if (c->cell_times && std::getenv("DD_TRACE_TIMES_FILE")) {

@@ -120,8 +120,8 @@ struct SweepArgs {
   int32_t* cell_iters;
   int32_t* cell_newton;     // Newton X-iterations of each cell solve (nullable)
   int newton;               // Newton X-iterations allowed
-  int32_t* cell_learned;    // per cell: 1 learned duals used, 0 judged and not used,
-                            // −1 not judged (nullable: no prediction this half-sweep)
+  int32_t* cell_learned;    // per cell: 1 learned duals used, 0 compared and not used,
+                            // −1 not compared (nullable: no prediction this half-sweep)
   int32_t* cell_status;     // bit0 not converged, bit1 non-finite, bit2 workspace overflow
   int* err_flag;
   const int32_t* order;     // launch order of the cells (NULL: natural order)
@@ -163,7 +163,7 @@ struct SweepTotals {
   long long newton_steps;
   int iters_max, not_converged, nonfinite, overflow;
   int learned;               // cells started from the learned duals
-  int judged;                // cells whose prediction was judged
+  int compared;              // cells whose prediction was compared
 };
 cudaError_t launch_reduce_cells(const SweepArgs& a, SweepTotals* out_dev, cudaStream_t s);
 cudaError_t launch_y_error(LevelView L, const int64_t* rp, const int32_t* col, const uint64_t* val,
@@ -200,10 +200,10 @@ cudaError_t launch_cell_features(const SweepArgs& a, float* feat, int2* fanchor,
 // targets of the same cells from the duals after the solve: tgt[J·64 + …]
 cudaError_t launch_cell_targets(const SweepArgs& a, const int2* fanchor, const int32_t* ok, float* tgt,
                                 cudaStream_t s);
-// judge: per 8×8 cell, the X-error after one Y-iteration from the current
+// comparison: per 8×8 cell, the X-error after one Y-iteration from the current
 // duals and from the prediction pred[J·64 + …]; the better one is written to
 // a.alpha and a.cell_learned[J] records the choice
-cudaError_t launch_judge(const SweepArgs& a, const float* pred, const int2* fanchor, const int32_t* ok,
+cudaError_t launch_warm_compare(const SweepArgs& a, const float* pred, const int2* fanchor, const int32_t* ok,
                          cudaStream_t s);
 
 }  // namespace ddk

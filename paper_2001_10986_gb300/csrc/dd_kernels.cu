@@ -1678,7 +1678,7 @@ __global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals*
     out->nonfinite = nf;
     out->overflow = ov;
     out->learned = nl;
-    out->judged = nj;
+    out->compared = nj;
   }
 }
 

@@ -6,7 +6,7 @@
 // * a network 1089 → 256 → 256 → 64 (ReLU, bfloat16 weights, FP32 sums) that
 //   predicts the cell's dual in the frame of that centroid, scaled by 1/ε;
 // * its training (forward, backward, Adam) on pairs logged from solves;
-// * the judge: the X-marginal error after one Y-iteration from the previous
+// * the comparison: the X-marginal error after one Y-iteration from the previous
 //   duals and from the prediction; the cell starts from the better one, so
 //   the plain warm start is both the fallback and the referee.
 //
@@ -38,7 +38,7 @@ constexpr int64_t oW1 = 0, ob1 = oW1 + (int64_t)kH * kIn, oW2 = ob1 + kH, ob2 = 
                   oW3 = ob2 + kH, ob3 = oW3 + (int64_t)kOut * kH, kNParams = ob3 + kOut;
 
 // ---------------------------------------------------------------------------
-// features, targets, judge
+// features, targets, comparison
 // ---------------------------------------------------------------------------
 __device__ double block_sum_d(double v, double* ws) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(64) k_cell_targets(SweepArgs a, const int2* fa
 
 // X-marginal L1 error, after one Y-iteration from the duals alpha_old (frame
 // anc_old) of one 8×8 cell; the rescaled error of the stopping rule
-__device__ float judge_error(const SweepArgs& a, const CellGeom& g, int64_t off, int ny, const float* al,
+__device__ float x_error_after_y(const SweepArgs& a, const CellGeom& g, int64_t off, int ny, const float* al,
                              int2 anc_old, int2 anc_new, float mscale, float* Fs, float* red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float d2 = (float)(a.L.spacing * a.L.spacing);
@@ -187,7 +187,7 @@ __device__ float judge_error(const SweepArgs& a, const CellGeom& g, int64_t off,
   return tot;
 }
 
-__global__ void __launch_bounds__(128) k_judge(SweepArgs a, const float* pred, const int2* fanc, const int32_t* ok) {
+__global__ void __launch_bounds__(128) k_warm_compare(SweepArgs a, const float* pred, const int2* fanc, const int32_t* ok) {
   __shared__ float Fs[kCellPx];
   __shared__ float red[4 * kCellPx];
   __shared__ float cand[2][kCellPx];
@@ -230,8 +230,8 @@ __global__ void __launch_bounds__(128) k_judge(SweepArgs a, const float* pred, c
   }
   __syncthreads();
   const float mscale = sums[1] > 0.f ? sums[0] / sums[1] : 1.f;
-  const float e0 = judge_error(a, g, off, ny, cand[0], anc_old, anc_new, mscale, Fs, red);
-  const float e1 = judge_error(a, g, off, ny, cand[1], anc_old, anc_new, mscale, Fs, red);
+  const float e0 = x_error_after_y(a, g, off, ny, cand[0], anc_old, anc_new, mscale, Fs, red);
+  const float e1 = x_error_after_y(a, g, off, ny, cand[1], anc_old, anc_new, mscale, Fs, red);
   const bool use = e1 < e0;   // NaN in e1 keeps the previous duals
   if (use && tid < kCellPx)
     a.alpha[(int64_t)(g.r0 + tid / 8) * a.L.n + g.c0 + tid % 8] = cand[1][tid];
@@ -401,9 +401,9 @@ cudaError_t launch_cell_targets(const SweepArgs& a, const int2* fanchor, const i
   return cudaGetLastError();
 }
 
-cudaError_t launch_judge(const SweepArgs& a, const float* pred, const int2* fanchor, const int32_t* ok,
+cudaError_t launch_warm_compare(const SweepArgs& a, const float* pred, const int2* fanchor, const int32_t* ok,
                          cudaStream_t s) {
-  k_judge<<<a.ncells, 128, 0, s>>>(a, pred, fanchor, ok);
+  k_warm_compare<<<a.ncells, 128, 0, s>>>(a, pred, fanchor, ok);
   return cudaGetLastError();
 }
 

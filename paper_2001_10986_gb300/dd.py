@@ -44,7 +44,7 @@ class dd_profile(C.Structure):
                 ("solve_ms", C.c_double), ("gather_launches", C.c_int64), ("gather_ms", C.c_double),
                 ("cluster_ms", C.c_double), ("kernel_evals", C.c_double), ("sinkhorn_iters", C.c_double), ("cells", C.c_int64),
                 ("newton_steps", C.c_int64), ("hessian_fma", C.c_double), ("learned_cells", C.c_int64),
-                ("judged_cells", C.c_int64)]
+                ("compared_cells", C.c_int64)]
 
 
 class DDError(RuntimeError):

@@ -98,7 +98,7 @@ def test_features_and_targets_match_oracle(lib):
 
 def test_learned_warm_start_gains_over_plain(lib):
     # train on pairs logged from plain runs on other images, then solve new
-    # pairs with the plain warm start and with the learned one (judged against
+    # pairs with the plain warm start and with the learned one (compared with
     # the plain one cell by cell): fewer Sinkhorn iterations, same result
     import torch
     from paper_2001_10986_gb300 import learned
@@ -112,9 +112,9 @@ def test_learned_warm_start_gains_over_plain(lib):
         Fs.append(f)
         Ts.append(t)
     net = learned.train((torch.cat(Fs), torch.cat(Ts)), epochs=40, batch=256, lr=1e-3)
-    # three new pairs; the prediction is judged at the first sweep on each new level
+    # three new pairs; the prediction is compared at the first sweep on each new level
     iters = {0: 0.0, 1: 0.0}
-    taken = judged = 0
+    taken = compared = 0
     costs = {0: [], 1: []}
     for pair in range(3):
         mu = syn.gaussian_mixture(n, 5, 300 + 2 * pair)
@@ -128,13 +128,13 @@ def test_learned_warm_start_gains_over_plain(lib):
             iters[warm] += p.sinkhorn_iters
             if warm:
                 taken += p.learned_cells
-                judged += p.judged_cells
+                compared += p.compared_cells
             costs[warm].append(g.cost(with_y=False)[0])
             g.close()
     net.close()
-    print("plain iterations %d, learned iterations %d (%d of %d judged cells took the prediction)"
-          % (iters[0], iters[1], taken, judged))
-    assert judged > 0 and taken > 0
+    print("plain iterations %d, learned iterations %d (%d of %d compared cells took the prediction)"
+          % (iters[0], iters[1], taken, compared))
+    assert compared > 0 and taken > 0
     assert iters[1] < iters[0]
     for c0, c1 in zip(costs[0], costs[1]):
         assert abs(c1 - c0) / c0 < 1e-5
