@@ -172,8 +172,9 @@ __device__ __forceinline__ uint64_t frac_to_u64(float f) {
 // S1: gather ν_cell (Algorithm 2, line "ν_cell ← Σ_{i∈J} ν_i")
 // ---------------------------------------------------------------------------
 constexpr int kGatherStage = 3072;   // entries of a cell's rows staged in shared memory
+constexpr int kGatherThreads = 256;  // threads of a gather CTA
 
-__global__ void __launch_bounds__(256) k_gather(SweepArgs a) {
+__global__ void __launch_bounds__(kGatherThreads) k_gather(SweepArgs a) {
   const int J = blockIdx.x;
   if (*a.err_flag) return;
   const LevelView& L = a.L;
@@ -229,27 +230,53 @@ __global__ void __launch_bounds__(256) k_gather(SweepArgs a) {
     __syncthreads();
   }
 
-  // merge-path rank of every element of the ≤4 sorted rows
+  // merge-path rank of every element of the ≤4 sorted rows; staged: the
+  // merged order replaces the staged copy in shared memory
   float sw = 0.f, sr = 0.f, sc = 0.f;
-  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+  auto rank_of = [&](int64_t e, int& y, uint64_t& v) {
     int r = 0;
     int64_t k = e;
     while (k >= rl[r]) { k -= rl[r]; ++r; }
-    const int y = staged ? s_col[e] : a.col[rs[r] + k];
-    const uint64_t v = staged ? s_val[e] : a.val[rs[r] + k];
+    y = staged ? s_col[e] : a.col[rs[r] + k];
+    v = staged ? s_val[e] : a.val[rs[r] + k];
     int64_t rank = k;
     for (int r2 = 0; r2 < nrows; ++r2) {
       if (r2 == r) continue;
       const int32_t* row = staged ? s_col + rb[r2] : a.col + rs[r2];
       rank += (r2 < r) ? upper_bound_row(row, rl[r2], y) : lower_bound_row(row, rl[r2], y);
     }
-    a.ws_ytmp[off + rank] = y;
-    a.ws_vtmp[off + rank] = v;
     const float vf = (float)v * kFixToFloat;
     const int yr = y / L.n, yc = y - (y / L.n) * L.n;
     sw += vf;
     sr += vf * (float)yr;
     sc += vf * (float)yc;
+    return rank;
+  };
+  if (staged) {
+    constexpr int kPer = kGatherStage / kGatherThreads;
+    int my_y[kPer], my_rank[kPer];
+    uint64_t my_v[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int64_t e = threadIdx.x + (int64_t)q * kGatherThreads;
+      my_rank[q] = -1;
+      if (e < tot) my_rank[q] = (int)rank_of(e, my_y[q], my_v[q]);
+    }
+    __syncthreads();   // every search of the staged rows is done
+#pragma unroll
+    for (int q = 0; q < kPer; ++q)
+      if (my_rank[q] >= 0) {
+        s_col[my_rank[q]] = my_y[q];
+        s_val[my_rank[q]] = my_v[q];
+      }
+  } else {
+    for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+      int y;
+      uint64_t v;
+      const int64_t rank = rank_of(e, y, v);
+      a.ws_ytmp[off + rank] = y;
+      a.ws_vtmp[off + rank] = v;
+    }
   }
   sw = block_sum(sw, fred);
   sr = block_sum(sr, fred);
@@ -271,15 +298,17 @@ __global__ void __launch_bounds__(256) k_gather(SweepArgs a) {
     const int64_t p = base + threadIdx.x;
     int head = 0;
     int y = 0;
+    const int32_t* my = staged ? s_col : a.ws_ytmp + off;
+    const uint64_t* mv = staged ? s_val : a.ws_vtmp + off;
     if (p < tot) {
-      y = a.ws_ytmp[off + p];
-      head = (p == 0) || (a.ws_ytmp[off + p - 1] != y);
+      y = my[p];
+      head = (p == 0) || (my[p - 1] != y);
     }
     int chunk_total;
     int u = block_exscan(head, iws, chunk_total);
     if (head) {
-      uint64_t s = a.ws_vtmp[off + p];
-      for (int64_t q = p + 1; q < tot && a.ws_ytmp[off + q] == y; ++q) s += a.ws_vtmp[off + q];
+      uint64_t s = mv[p];
+      for (int64_t q = p + 1; q < tot && my[q] == y; ++q) s += mv[q];
       const int64_t w = off + carry + u;
       const int yr = y / L.n, yc = y - (y / L.n) * L.n;
       a.ws_eta[w] = pack_eta(yr - ya, yc - yc0);
@@ -1905,7 +1934,7 @@ __global__ void __launch_bounds__(256) k_plan(SweepArgs a, float trunc, const in
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_gather(const SweepArgs& a, cudaStream_t s) {
-  k_gather<<<a.ncells, 256, 0, s>>>(a);
+  k_gather<<<a.ncells, kGatherThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
