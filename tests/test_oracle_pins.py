@@ -73,6 +73,33 @@ def test_converged_dd_equals_global_sinkhorn():
     assert np.abs(P - Pr).sum() / Pr.sum() < 1e-8
 
 
+def test_converged_dd_with_massless_pixels_equals_global_sinkhorn():
+    # pixels without mass in μ and in ν: the cells are solved on the support
+    # of μ_J, and the converged decomposition still equals the global
+    # scaling-form Sinkhorn (which gives those rows and columns zero mass)
+    prob = _grid(8, 2, 2, 1)
+    mu, nu = prob.mu.copy(), prob.nu.copy()
+    mu[[5, 18, 41]] = 0.0
+    nu[[0, 27, 63]] = 0.0
+    mu /= mu.sum()
+    nu /= nu.sum()
+    prob = dd.GridProblem(mu.reshape(8, 8), nu.reshape(8, 8), 2, 1.0 / 8)
+    eps = 0.03
+    Pr, _, _ = referees.sinkhorn_scaling(prob.mu, prob.nu, _full_cost(prob), eps)
+    rows = dd.product_state(prob)
+    rows = [(c[v > 0], v[v > 0]) for c, v in rows]
+    alpha = {"A": np.zeros(64), "B": np.zeros(64)}
+    par = dd.Params(err=1e-12, trunc=0.0, max_iter=5000)
+    with np.errstate(divide="ignore"):
+        for _ in range(60):
+            for part in "AB":
+                rows, _ = dd.half_sweep(prob, part, rows, alpha[part], eps, par)
+        P = dd.partition_plan(prob, "B", rows, alpha["B"], eps)
+    assert np.all(np.isfinite(alpha["A"])) and np.all(np.isfinite(alpha["B"]))
+    assert np.abs(P - Pr).sum() / Pr.sum() < 1e-8
+    assert P[[5, 18, 41]].sum() == 0.0 and P[:, [0, 27, 63]].sum() == 0.0
+
+
 # --------------------------------------------------------------------------
 # ε → 0: entropic cost is within ε·min(H(μ),H(ν)) above the LP optimum
 # --------------------------------------------------------------------------
