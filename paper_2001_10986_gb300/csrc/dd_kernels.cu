@@ -1487,22 +1487,24 @@ __global__ void __launch_bounds__(1024) k_order(SweepArgs a, int32_t* order, int
   __shared__ double s_thr;
   const int nc = a.ncells;
   for (int k = threadIdx.x; k < NB; k += blockDim.x) cnt[k] = 0;
+  // FP32 work estimates and logarithms: this kernel runs on one SM, where
+  // FP64 arithmetic would dominate its time
   auto work = [&](int J) {
-    if (a.cell_off[J] < 0) return 1.0;
+    if (a.cell_off[J] < 0) return 1.0f;
     const CellGeom g = cell_geom(a.part, J, a.L.nb, a.L.b);
     const int it = a.iters_hist ? max(a.iters_hist[J], 1) : 1;
-    return (double)it * (double)max(a.cell_ny[J], 1) * (double)(g.H * g.W);
+    return (float)it * (float)max(a.cell_ny[J], 1) * (float)(g.H * g.W);
   };
   double tot = 0.0;
-  for (int J = threadIdx.x; J < nc; J += blockDim.x) tot += work(J);
+  for (int J = threadIdx.x; J < nc; J += blockDim.x) tot += (double)work(J);
   tot = block_sum<double>(tot, dws);
   // an eighth of one SM's fair share: a single CTA runs such a cell long
   // enough to stretch the launch
   if (threadIdx.x == 0) s_thr = a.max_big > 0 ? tot / (8.0 * 152.0) : 3.0e300;
   __syncthreads();
-  const double thr = s_thr;
-  auto bucket = [&](double w) {
-    const int b2 = min(63, (int)(2.0 * log2(fmax(w, 1.0))));
+  const float thr = (float)fmin(s_thr, 3.0e38);
+  auto bucket = [&](float w) {
+    const int b2 = min(63, (int)(2.0f * log2f(fmaxf(w, 1.0f))));
     return (w >= thr ? 0 : 64) + 63 - b2;
   };
   // counts and positions with one shared-memory atomic per bucket and warp
