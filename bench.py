@@ -43,9 +43,9 @@ SM_MAX_MHZ = 2070.0
 FMA_PER_ENTRY = 2.0
 HESS_SYM = 65.0 / 128.0
 # DRAM bytes per launch of the two cell-solve kernels from the last ncu
-# capture of the current kernels (profiles/k_sinkhorn_gm512_b4.md: 56.1 MB at
+# capture of the current kernels (profiles/k_sinkhorn_gm512_b4.md: 56.6 MB at
 # 512², scaled by the 4× cell count to 1024²); None if not captured
-SOLVE_TRAFFIC_BYTES = 4 * 56.1e6
+SOLVE_TRAFFIC_BYTES = 4 * 56.6e6
 
 
 def parse():
