@@ -207,6 +207,31 @@ dd_status dd_get_basic_marginals(dd_ctx* ctx, int64_t* nnz, int64_t* row_ptr,
 dd_status dd_get_plan(dd_ctx* ctx, double trunc, int64_t* nnz, int64_t* row_ptr,
                       int32_t* col, double* val, int64_t cap);
 
+/* Objective of a coupling π, summed cell by cell as §6.3 describes: with
+ * partition = -1 the coupling of dd_get_plan (the partition solved last, at
+ * its ε; eps is ignored), with partition 0 (A) or 1 (B) the coupling that
+ * the current basic marginals and that partition's α give at ε = eps (on
+ * every cell f from α and one Y-iteration against ν_cell). K = e^{−c/ε}·μ⊗ν:
+ *   primal  = KL(π|K) − ‖K‖ = Σ π·(log π − log K − 1), the primal score of
+ *             eq. RelPDGap (Lemma 4.2 evaluates it from the scalings);
+ *   gap     = Σ_J gap_J and gap_abs = Σ_J |gap_J|, where gap_J =
+ *             KL(π_J|K_J) − J_J(u_J, v_J) is the primal-dual gap of the cell
+ *             problem on X_J × supp ν_cell with marginals μ_J and ν_cell
+ *             (J_J: eq. EntropicOTDualObjective, Prop. 2.5). π_J meets ν_cell
+ *             exactly and μ_J only approximately (up to the Sinkhorn
+ *             tolerance after a solve), so gap_J has no fixed sign; it is
+ *             zero at the cell's optimum and does not
+ *             depend on the per-cell constants of the duals beyond
+ *             (‖ν_cell‖ − ‖μ_J‖)·constant/ε, the mass lost to Truncate.
+ * Entries are FP32 exponentials (as in dd_get_plan), logs and sums FP64. The
+ * global primal-dual gap of eq. RelPDGap needs the glued duals of §6.3 and
+ * is not computed. Allocates (and frees) 16 bytes per composite cell of
+ * device memory; synchronises the stream. Any output pointer may be NULL.
+ * DD_ERR_STATE for partition -1 before the first half-sweep of a level;
+ * DD_ERR_ARG for another partition or a non-positive eps. */
+dd_status dd_objective(dd_ctx* ctx, int32_t partition, double eps, double* primal, double* gap,
+                       double* gap_abs);
+
 /* α = ε·log u_{C,J} of `partition` on every pixel of the current level, up to
  * one additive constant per composite cell (the gauge of Prop. 2.3 (ii)). */
 dd_status dd_get_duals(dd_ctx* ctx, int32_t partition, double* alpha);

@@ -21,7 +21,10 @@ optimal transport":
   quad-tree parent map, fine basic marginals are initialised by eq.
   FineBasicMarginals, and ε·log u is kept fixed when ε changes;
 * basic/composite partitions for images (§7.1): s×s basic cells, partition A
-  of 2×2 blocks, partition B the same blocks shifted by one basic cell.
+  of 2×2 blocks, partition B the same blocks shifted by one basic cell;
+* objective values (Lemma 4.2, Prop. 2.5, §6.3): KL(π|K) − ‖K‖ of a
+  partition's coupling summed cell by cell, and the primal-dual gaps of the
+  cell problems.
 
 Potentials are kept in the counting-measure form f = α + ε·log μ,
 g = β + ε·log ν with π(x,y) = exp((f(x) + g(y) − c(x,y))/ε); α = ε·log u and
@@ -358,6 +361,44 @@ def partition_plan_sparse(prob, part, rows, alpha, eps, trunc=0.0):
         cs.append(c)
         vs.append(v)
     return row_ptr, np.concatenate(cs), np.concatenate(vs)
+
+
+def cell_objectives(prob, part, rows, alpha, eps):
+    """Objective values of the coupling of partition_plan, cell by cell (§6.3:
+    the primal score is summed over the composite cells of the last loop).
+
+    On a cell J, f = α + ε·log μ on the pixels with mass and one Y-iteration
+    against ν_cell give π_J = u_J ⊗ v_J · K on X_J × supp ν_cell with
+    log u_J = α/ε and log v_J = β_J/ε, β_J = g − ε·log ν. Per cell:
+
+    * primal_J = Σ π_J·(log π_J − log K − 1), the cell's share of
+      KL(π|K) − ‖K‖ (the denominator of eq. RelPDGap);
+    * gap_J = KL(π_J|K_J) − J_J(u_J, v_J), the primal-dual gap of the cell
+      problem: marginals μ_J and ν_cell, kernel K_J = K restricted to
+      X_J × supp ν_cell, J_J the dual objective of eq. EntropicOTDualObjective
+      on that problem (Prop. 2.5). π_J meets ν_cell exactly and μ_J only up to
+      the Sinkhorn tolerance, so gap_J has no fixed sign; it is zero at the
+      cell's optimum.
+
+    Returns (primal, gap): FP64 arrays in the order of prob.parts[part].
+    """
+    primal, gap = [], []
+    for J in prob.parts[part]:
+        cols, nu_cell = gather(rows, J)
+        X = prob.cell_points(J)
+        X = X[prob.mu[X] > 0]
+        C = prob.cost(X, cols)
+        mu_x, nu_y = prob.mu[X], prob.nu[cols]
+        a = alpha[X]
+        f = a + eps * np.log(mu_x)
+        g = eps * np.log(nu_cell) - eps * logsumexp((f[:, None] - C) / eps, axis=0)
+        P = np.exp((f[:, None] + g[None, :] - C) / eps)
+        beta = g - eps * np.log(nu_y)
+        pj = kl_minus_mass(P, C, mu_x, nu_y, eps)
+        kl = pj + kernel_mass(C, mu_x, nu_y, eps)
+        primal.append(pj)
+        gap.append(kl - dual_objective(a, beta, mu_x, nu_cell, C, mu_x, nu_y, eps))
+    return np.array(primal), np.array(gap)
 
 
 def kl_minus_mass(P, C, mu, nu, eps):

@@ -1294,6 +1294,46 @@ dd_status dd_get_plan(dd_ctx* c, double trunc, int64_t* nnz, int64_t* row_ptr, i
   });
 }
 
+dd_status dd_objective(dd_ctx* c, int32_t partition, double eps, double* primal, double* gap, double* gap_abs) {
+  return guarded(c, [&] {
+    int part = partition;
+    if (partition == -1) {
+      if (c->last_part < 0) throw DdError{DD_ERR_STATE, "no half-sweep has run at this level"};
+      part = c->last_part;
+      eps = c->eps_cur;
+    } else if (partition != 0 && partition != 1) {
+      throw DdError{DD_ERR_ARG, "partition must be -1, 0 or 1"};
+    } else if (!(eps > 0.0) || !std::isfinite(eps)) {
+      throw DdError{DD_ERR_ARG, "eps must be positive and finite"};
+    }
+    ensure_state(c);
+    ensure_sweep_capacity(c, c->nnz);
+    DD_CUDA(cudaMemsetAsync(c->ws_counter, 0, sizeof(unsigned long long), c->stream));
+    DD_CUDA(cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream));
+    SweepArgs a = sweep_args(c, part, eps);
+    DD_CUDA(launch_gather(a, c->stream));
+    double* cell_obj = nullptr;
+    double* out = nullptr;
+    double h[3] = {0.0, 0.0, 0.0};
+    try {
+      dev_alloc(cell_obj, 2 * (size_t)std::max(a.ncells, 1));
+      dev_alloc(out, 3);
+      DD_CUDA(launch_objective(a, cell_obj, out, c->stream));
+      DD_CUDA(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+      DD_CUDA(cudaStreamSynchronize(c->stream));
+    } catch (...) {
+      dev_free(cell_obj);
+      dev_free(out);
+      throw;
+    }
+    dev_free(cell_obj);
+    dev_free(out);
+    if (primal) *primal = h[0];
+    if (gap) *gap = h[1];
+    if (gap_abs) *gap_abs = h[2];
+  });
+}
+
 dd_status dd_get_duals(dd_ctx* c, int32_t partition, double* alpha) {
   return guarded(c, [&] {
     if ((partition != 0 && partition != 1) || !alpha) throw DdError{DD_ERR_ARG, "bad argument"};

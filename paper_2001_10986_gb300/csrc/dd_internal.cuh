@@ -188,6 +188,9 @@ cudaError_t launch_refine_duals(LevelView C, LevelView F, int cpart, const float
                                 cudaStream_t s);
 
 // plan reconstruction: counts per X pixel, then values
+// objective of the last partition's coupling: per cell (primal, gap) into
+// cell_obj[2·ncells], then out[3] = {Σ primal, Σ gap, Σ |gap|}
+cudaError_t launch_objective(const SweepArgs& a, double* cell_obj, double* out, cudaStream_t s);
 cudaError_t launch_plan(const SweepArgs& a, float trunc, const int64_t* xrp, int32_t* xcnt,
                         int32_t* pcol, double* pval, int write, cudaStream_t s);
 

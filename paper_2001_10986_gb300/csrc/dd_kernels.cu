@@ -1933,6 +1933,153 @@ __global__ void __launch_bounds__(256) k_plan(SweepArgs a, float trunc, const in
 }
 
 // ---------------------------------------------------------------------------
+// objective of the last partition's coupling, cell by cell (dd_objective)
+// ---------------------------------------------------------------------------
+// π_J from the stored duals and one Y-iteration (the coupling of k_plan),
+// written as π_J = u ⊗ v · K with K = e^{−c/ε}·μ⊗ν and the true cost c. In
+// the cell's frame (pixel x = (r0+ar, c0+ac), support point y = anchor +
+// (er, ec), D = corner − anchor) the kernel evaluates 2^(F + G − κ c̃) with
+// c̃ = (ar−er)² + (ac−ec)², while c/(ε ln 2) = κ((D_r+ar−er)² + (D_c+ac−ec)²);
+// the difference is a term in x plus a term in y, so
+//   log2 u(x) = F(x) − log2 μ(x) + κ(D_r² + D_c² + 2D_r·ar + 2D_c·ac),
+//   log2 v(y) = G(y) − log2 ν(y) − 2κ(D_r·er + D_c·ec).
+// Per cell (Lemma 4.2 on the cell, §6.3):
+//   primal_J = ⟨P_X π_J, log u⟩ + ⟨P_Y π_J, log v⟩ − ‖π_J‖
+//            = Σ π_J (log π_J − log K − 1),
+//   gap_J    = ⟨P_X π_J − μ_J, log u⟩ + ⟨P_Y π_J − ν_cell, log v⟩
+//            = KL(π_J|K_J) − J_J(u, v)   (eq. EntropicOTDualObjective).
+// log u is shifted by its μ-weighted mean and log v by the opposite amount
+// (a change of gauge: primal_J is unchanged, gap_J moves by the mean times
+// ‖ν_cell‖ − ‖μ_J‖, the mass lost to Truncate), so that the residuals
+// multiply the spread of log u rather than its level. Entries are FP32
+// exponentials as in k_plan; logs, residuals and sums are FP64.
+__global__ void __launch_bounds__(256) k_objective(SweepArgs a, double* cell_obj) {
+  const int J = blockIdx.x;
+  const LevelView& L = a.L;
+  const CellGeom g = cell_geom(a.part, J, L.nb, L.b);
+  const int64_t off = a.cell_off[J];
+  if (off < 0) {
+    if (threadIdx.x == 0) {
+      cell_obj[2 * (int64_t)J] = 0.0;
+      cell_obj[2 * (int64_t)J + 1] = 0.0;
+    }
+    return;
+  }
+  const int ny = a.cell_ny[J];
+  const int2 anc_old = a.anchor[J], anc = a.anchor_new[J];
+  const float d2 = (float)(L.spacing * L.spacing);
+  const float inv_eln2 = 1.0f / (a.eps * kLn2);
+  const float kappa = (float)(L.spacing * L.spacing / ((double)a.eps * 0.69314718055994530942));
+  const double kap = L.spacing * L.spacing / ((double)a.eps * 0.69314718055994530942);
+  const double ln2 = 0.69314718055994530942;
+  const double fix = 1.0 / kFixOne;
+  const int shr = anc.x - anc_old.x, shc = anc.y - anc_old.y;
+  const int Dr = g.r0 - anc.x, Dc = g.c0 - anc.y;
+  const int HW = g.H * g.W;
+  __shared__ float F[kMaxHW];
+  __shared__ double lu[kMaxHW];
+  __shared__ double dws[32];
+  for (int x = threadIdx.x; x < HW; x += blockDim.x) {
+    const int ar = x / g.W, ac = x - (x / g.W) * g.W;
+    const int p = (g.r0 + ar) * L.n + g.c0 + ac;
+    F[x] = (a.alpha[p] + 2.0f * d2 * (float)(shr * ar + shc * ac)) * inv_eln2 + L.log2mu[p];
+  }
+  __syncthreads();
+  // Y-iteration: G(y) = log2 ν_cell(y) − LSE_x(F − κc̃), into ws_g
+  for (int k = threadIdx.x; k < ny; k += blockDim.x) {
+    const int32_t e = a.ws_eta[off + k];
+    const int er = eta_r(e), ec = eta_c(e);
+    float m = kNegBig;
+    for (int x = 0; x < HW; ++x) {
+      const float tr = (float)(x / g.W - er), tc = (float)(x % g.W - ec);
+      m = fmaxf(m, F[x] - kappa * (tr * tr + tc * tc));
+    }
+    float s = 0.f;
+    for (int x = 0; x < HW; ++x) {
+      const float tr = (float)(x / g.W - er), tc = (float)(x % g.W - ec);
+      s += ex2(F[x] - kappa * (tr * tr + tc * tc) - m);
+    }
+    a.ws_g[off + k] = a.ws_lognu[off + k] - m - lg2(s);
+  }
+  // log u in the true frame (natural log; 0 on pixels without mass), gauge
+  double wl = 0.0, wm = 0.0;
+  for (int x = threadIdx.x; x < HW; x += blockDim.x) {
+    const int ar = x / g.W, ac = x - (x / g.W) * g.W;
+    const int p = (g.r0 + ar) * L.n + g.c0 + ac;
+    const double mu = (double)L.mu_q[p] * fix;
+    const double l = mu > 0.0 ? ln2 * ((double)F[x] - (double)L.log2mu[p] +
+                                       kap * (double)(Dr * Dr + Dc * Dc + 2 * Dr * ar + 2 * Dc * ac))
+                              : 0.0;
+    lu[x] = l;
+    wl += mu * l;
+    wm += mu;
+  }
+  wl = block_sum<double>(wl, dws);   // contains the barriers after lu and ws_g
+  wm = block_sum<double>(wm, dws);
+  const double lbar = wm > 0.0 ? wl / wm : 0.0;
+  double prim = 0.0, gap = 0.0;
+  // the support points: P_Y π(y) and log v(y)
+  for (int k = threadIdx.x; k < ny; k += blockDim.x) {
+    const int32_t e = a.ws_eta[off + k];
+    const int er = eta_r(e), ec = eta_c(e);
+    const float G = a.ws_g[off + k];
+    const double nuc = (double)a.ws_nu[off + k] * fix;
+    const int y = (anc.x + er) * L.n + anc.y + ec;
+    const double nuy = (double)L.nu_q[y] * fix;
+    if (!(nuc > 0.0 && nuy > 0.0)) continue;   // no coupling mass at y
+    double sy = 0.0;
+    for (int x = 0; x < HW; ++x) {
+      const float tr = (float)(x / g.W - er), tc = (float)(x % g.W - ec);
+      sy += (double)ex2(F[x] + G - kappa * (tr * tr + tc * tc));
+    }
+    const double lv = ln2 * ((double)G - log2(nuy) - 2.0 * kap * (double)(Dr * er + Dc * ec)) + lbar;
+    prim += sy * lv;
+    gap += (sy - nuc) * lv;
+  }
+  // the pixels: P_X π(x) and log u(x)
+  for (int x = threadIdx.x; x < HW; x += blockDim.x) {
+    const int ar = x / g.W, ac = x - (x / g.W) * g.W;
+    const int p = (g.r0 + ar) * L.n + g.c0 + ac;
+    const double mu = (double)L.mu_q[p] * fix;
+    if (!(mu > 0.0)) continue;   // π(x, ·) = 0 and log u = 0
+    double sx = 0.0;
+    for (int k = 0; k < ny; ++k) {
+      const int32_t e = a.ws_eta[off + k];
+      const float tr = (float)(ar - eta_r(e)), tc = (float)(ac - eta_c(e));
+      sx += (double)ex2(F[x] + a.ws_g[off + k] - kappa * (tr * tr + tc * tc));
+    }
+    const double l = lu[x] - lbar;
+    prim += sx * l - sx;
+    gap += (sx - mu) * l;
+  }
+  prim = block_sum<double>(prim, dws);
+  gap = block_sum<double>(gap, dws);
+  if (threadIdx.x == 0) {
+    cell_obj[2 * (int64_t)J] = prim;
+    cell_obj[2 * (int64_t)J + 1] = gap;
+  }
+}
+
+// Σ_J primal_J, Σ_J gap_J and Σ_J |gap_J| in a fixed order (one block)
+__global__ void __launch_bounds__(1024) k_objective_sum(const double* cell_obj, int ncells, double* out) {
+  __shared__ double dws[32];
+  double p = 0.0, gs = 0.0, ga = 0.0;
+  for (int J = threadIdx.x; J < ncells; J += blockDim.x) {
+    p += cell_obj[2 * (int64_t)J];
+    gs += cell_obj[2 * (int64_t)J + 1];
+    ga += fabs(cell_obj[2 * (int64_t)J + 1]);
+  }
+  p = block_sum<double>(p, dws);
+  gs = block_sum<double>(gs, dws);
+  ga = block_sum<double>(ga, dws);
+  if (threadIdx.x == 0) {
+    out[0] = p;
+    out[1] = gs;
+    out[2] = ga;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_gather(const SweepArgs& a, cudaStream_t s) {
@@ -2070,6 +2217,12 @@ cudaError_t launch_refine_duals(LevelView C, LevelView F, int cpart, const float
   const int n2 = F.n * F.n;
   k_refine_duals<<<(n2 + 255) / 256, 256, 0, s>>>(C, F, cpart, alpha_c, anchor_c, fpart, alpha_f,
                                                   anchor_f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_objective(const SweepArgs& a, double* cell_obj, double* out, cudaStream_t s) {
+  k_objective<<<a.ncells, 256, 0, s>>>(a, cell_obj);
+  k_objective_sum<<<1, 1024, 0, s>>>(cell_obj, a.ncells, out);
   return cudaGetLastError();
 }
 

@@ -74,6 +74,8 @@ _lib.dd_cost.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POI
 _lib.dd_get_basic_marginals.argtypes = [_P, C.POINTER(C.c_int64), _P, _P, _P, C.c_int64]
 _lib.dd_get_plan.argtypes = [_P, C.c_double, C.POINTER(C.c_int64), _P, _P, _P, C.c_int64]
 _lib.dd_get_duals.argtypes = [_P, C.c_int32, _pd]
+_lib.dd_objective.argtypes = [_P, C.c_int32, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                              C.POINTER(C.c_double)]
 _lib.dd_get_info.argtypes = [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                              C.POINTER(C.c_double), C.POINTER(C.c_int64)]
 _lib.dd_solve_cell_noalloc.argtypes = [_P, C.c_int32, C.c_double, C.c_int32, _P, _P, _P, C.c_double,
@@ -103,7 +105,7 @@ for _f in ("dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep", "dd_run_sch
            "dd_get_basic_marginals", "dd_get_plan", "dd_get_duals", "dd_get_info", "dd_get_profile",
            "dd_reset_profile", "dd_get_cell_stats", "dd_mlp_create", "dd_mlp_get_params", "dd_mlp_set_params",
            "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step", "dd_attach_mlp", "dd_cell_training_pairs",
-           "dd_autotune"):
+           "dd_autotune", "dd_objective"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep",
@@ -111,7 +113,7 @@ EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", 
             "dd_get_info", "dd_get_cell_stats", "dd_get_profile", "dd_reset_profile", "dd_destroy",
             "dd_last_error", "dd_solve_cell_noalloc", "dd_mlp_num_params", "dd_mlp_create", "dd_mlp_destroy",
             "dd_mlp_get_params", "dd_mlp_set_params", "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step",
-            "dd_attach_mlp", "dd_cell_training_pairs", "dd_autotune")
+            "dd_attach_mlp", "dd_cell_training_pairs", "dd_autotune", "dd_objective")
 
 
 def _check(ctx, st):
@@ -217,6 +219,15 @@ def dd_get_plan(ctx, trunc=0.0):
     _check(ctx, _lib.dd_get_plan(ctx, float(trunc), C.byref(nnz), rp.ctypes.data, col.ctypes.data,
                                  val.ctypes.data, col.size))
     return rp, col[:nnz.value], val[:nnz.value]
+
+
+def dd_objective(ctx, partition=-1, eps=0.0):
+    """(primal, gap, gap_abs): KL(π|K) − ‖K‖ summed over the composite cells,
+    and the sum and absolute sum of the cell problems' primal-dual gaps, for
+    the last partition's coupling (partition -1) or for partition 0/1 at ε."""
+    p, g, ga = C.c_double(), C.c_double(), C.c_double()
+    _check(ctx, _lib.dd_objective(ctx, int(partition), float(eps), C.byref(p), C.byref(g), C.byref(ga)))
+    return p.value, g.value, ga.value
 
 
 def dd_get_duals(ctx, partition):
@@ -369,6 +380,9 @@ class DD:
 
     def duals(self, partition):
         return dd_get_duals(self.ctx, partition)
+
+    def objective(self, partition=-1, eps=0.0):
+        return dd_objective(self.ctx, partition, eps)
 
     def cell_stats(self):
         return dd_get_cell_stats(self.ctx)

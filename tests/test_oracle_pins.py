@@ -401,3 +401,68 @@ def test_partitions_cover_and_graph_connected():
         for m in adj[k] - seen:
             seen.add(m); todo.append(m)
     assert len(seen) == nb * nb
+
+
+# --------------------------------------------------------------------------
+# cell-by-cell objective (§6.3) and the cell problems' primal-dual gaps
+# --------------------------------------------------------------------------
+def _state_after(prob, eps, sweeps, err, max_iter=20000, trunc=0.0):
+    rows = dd.product_state(prob)
+    alpha = {"A": np.zeros(prob.mu.size), "B": np.zeros(prob.mu.size)}
+    par = dd.Params(err=err, trunc=trunc, max_iter=max_iter)
+    for l in range(2 * sweeps):
+        part = "AB"[l % 2]
+        rows, _ = dd.half_sweep(prob, part, rows, alpha[part], eps, par)
+    return rows, alpha
+
+
+def test_cell_primals_sum_to_kl_of_the_partition_plan():
+    prob = _grid(16, 4, 3, 14)
+    eps = 0.01
+    rows, alpha = _state_after(prob, eps, 2, 1e-6)
+    primal, _ = dd.cell_objectives(prob, "B", rows, alpha["B"], eps)
+    P = dd.partition_plan(prob, "B", rows, alpha["B"], eps)
+    kl = dd.kl_minus_mass(P, _full_cost(prob), prob.mu, prob.nu, eps)
+    assert primal.sum() == pytest.approx(kl, rel=1e-12)
+
+
+def test_cell_gap_is_the_marginal_residual_form():
+    # π_J = u ⊗ v · K: the gap KL(π_J|K_J) − J_J(u, v) equals
+    # ⟨P_X π_J − μ_J, log u⟩ + ⟨P_Y π_J − ν_cell, log v⟩ (Lemma 4.2 on the
+    # cell); log v is read off the plan itself, not from the oracle's β
+    prob = _grid(16, 4, 3, 15)
+    eps = 0.01
+    rows, alpha = _state_after(prob, eps, 1, 1e-6, max_iter=3)
+    primal, gap = dd.cell_objectives(prob, "B", rows, alpha["B"], eps)
+    assert np.abs(gap).max() > 1e-6          # an unconverged state has a gap
+    for j, J in enumerate(prob.parts["B"]):
+        cols, nu_cell = dd.gather(rows, J)
+        X = prob.cell_points(J)
+        C = prob.cost(X, cols)
+        f = alpha["B"][X] + eps * np.log(prob.mu[X])
+        g = eps * np.log(nu_cell) - eps * dd.logsumexp((f[:, None] - C) / eps, axis=0)
+        P = np.exp((f[:, None] + g[None, :] - C) / eps)
+        logK = -C / eps + np.log(prob.mu[X])[:, None] + np.log(prob.nu[cols])[None, :]
+        logu = alpha["B"][X] / eps
+        logv = (np.log(P) - logK - logu[:, None]).mean(axis=0)
+        res = (P.sum(1) - prob.mu[X]) @ logu + (P.sum(0) - nu_cell) @ logv
+        assert gap[j] == pytest.approx(res, rel=1e-8, abs=1e-14)
+        lemma = P.sum(1) @ logu + P.sum(0) @ logv - P.sum()
+        assert primal[j] == pytest.approx(lemma, rel=1e-10)
+
+
+def test_cell_gap_vanishes_at_the_optimum_and_ignores_cell_constants():
+    prob = _grid(16, 4, 3, 16)
+    eps = 0.01
+    rows, alpha = _state_after(prob, eps, 2, 1e-13)
+    primal, gap = dd.cell_objectives(prob, "B", rows, alpha["B"], eps)
+    assert np.abs(gap).max() < 1e-10 * np.abs(primal).sum()
+    # a constant added to α on one cell moves β by the opposite constant:
+    # the gap changes by c/ε·(‖ν_cell‖ − ‖μ_J‖), which is zero here (no
+    # truncation, BalanceMeasures makes the masses equal)
+    rows2, alpha2 = _state_after(prob, eps, 1, 1e-6, max_iter=3)
+    _, g0 = dd.cell_objectives(prob, "B", rows2, alpha2["B"], eps)
+    shifted = alpha2["B"].copy()
+    shifted[prob.cell_points(prob.parts["B"][3])] += 7.0 * eps
+    _, g1 = dd.cell_objectives(prob, "B", rows2, shifted, eps)
+    assert g1 == pytest.approx(g0, rel=1e-9, abs=1e-13)
