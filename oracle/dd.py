@@ -501,6 +501,126 @@ def refine_duals(coarse, fine, alpha_c, part):
 
 
 # ----------------------------------------------------------------------------
+# dual gluing (§6.3, "Estimating the primal-dual gap") and eq. RelPDGap
+# ----------------------------------------------------------------------------
+def gluing_graph(prob):
+    """Edges of the gluing graph of §6.3: the vertices are the cells of
+    partition A; for every cell J_B of B and every ordered pair (J1, J2) of
+    distinct A cells that both meet J_B there is one edge (J1, J2) labelled
+    J_B (an edge per orientation, and several edges between two vertices when
+    several B cells connect them). Returns [(j1, j2, jb, X1, X2)] with j1, j2
+    indices into prob.parts["A"], jb into prob.parts["B"], X1 = the pixels of
+    J1 ∩ J_B and X2 those of J2 ∩ J_B."""
+    A, B = prob.parts["A"], prob.parts["B"]
+    a_of = {i: j for j, J in enumerate(A) for i in J}
+    edges = []
+    for jb, JB in enumerate(B):
+        meet = {}
+        for i in JB:
+            meet.setdefault(a_of[i], []).append(i)
+        for j1 in sorted(meet):
+            for j2 in sorted(meet):
+                if j1 != j2:
+                    X1 = np.concatenate([prob.basic[i] for i in meet[j1]])
+                    X2 = np.concatenate([prob.basic[i] for i in meet[j2]])
+                    edges.append((j1, j2, jb, X1, X2))
+    return edges
+
+
+def _log_mu_mean_exp(mu, t):
+    """log of the μ-weighted mean of exp(t) (the ⨍ … dμ of §6.3), stably."""
+    live = mu > 0
+    return float(logsumexp(t[live] + np.log(mu[live]), axis=0) - np.log(mu[live].sum()))
+
+
+def glue_duals(prob, alpha_A, alpha_B, eps):
+    """Glued X-dual of §6.3 from the composite duals of both partitions.
+
+    Edge weights, with u = exp(α/ε):
+        q(J1,J2) = ⨍_{J1∩J_B} u_{A,J1}/u_{B,J_B} dμ · ⨍_{J2∩J_B} u_{B,J_B}/u_{A,J2} dμ.
+    A potential V on the A cells solves the least-squares problem
+        min Σ_edges ((V(J1) − V(J2)) + log q(J1,J2))²,   Σ_J V(J) = 0,
+    and û_J = exp(V(J))·u_{A,J}. The sign in front of log q is the reading
+    under which this agrees with the path-product construction of the same
+    section (û_J = Π_k q(J_k, J_{k+1})·u_{A,J} along a path J_0 … J_n = J):
+    for consistent duals u_{A,J} = λ_J u*, u_{B,J} = κ_J u*, log q(J1,J2) =
+    log λ_{J1} − log λ_{J2} and both give û ∝ u*.
+    Returns (alpha_hat, V) with alpha_hat = ε·log û on every pixel (α_A + ε·V
+    on each A cell; 0 on pixels without mass, like α)."""
+    A = prob.parts["A"]
+    edges = gluing_graph(prob)
+    mu = prob.mu
+    D = np.zeros((len(edges) + 1, len(A)))
+    rhs = np.zeros(len(edges) + 1)
+    for e, (j1, j2, _, X1, X2) in enumerate(edges):
+        lq = (_log_mu_mean_exp(mu[X1], (alpha_A[X1] - alpha_B[X1]) / eps) +
+              _log_mu_mean_exp(mu[X2], (alpha_B[X2] - alpha_A[X2]) / eps))
+        D[e, j1], D[e, j2] = 1.0, -1.0
+        rhs[e] = -lq
+    D[-1, :] = 1.0           # the gauge Σ V = 0; edge residuals do not see it
+    V = np.linalg.lstsq(D, rhs, rcond=None)[0]
+    alpha_hat = np.asarray(alpha_A, dtype=np.float64).copy()
+    for j, J in enumerate(A):
+        X = prob.cell_points(J)
+        alpha_hat[X] += eps * V[j]
+    alpha_hat[mu == 0] = 0.0
+    return alpha_hat, V
+
+
+def best_y_dual(prob, alpha_hat, eps):
+    """β̂ = ε·log v̂ for the Y-scaling that maximises J(û, ·) (one Y-iteration
+    on the whole problem, Remark 2.4): v̂(y) = 1 / Σ_x û(x) e^{−c(x,y)/ε} μ(x).
+    The paper glues the cells' v_J like û; this v̂ is at least as good a dual
+    candidate for the given û. Dense (small problems)."""
+    live = prob.mu > 0
+    X = np.flatnonzero(live)
+    C = prob.cost(X, np.arange(prob.nu.size))
+    t = (alpha_hat[X][:, None] - C) / eps + np.log(prob.mu[X])[:, None]
+    return -eps * logsumexp(t, axis=0)
+
+
+def relative_pd_gap(prob, P, alpha_hat, beta_hat, eps):
+    """eq. RelPDGap: (KL(π|K) − J(û,v̂)) / (KL(π|K) − ‖K‖) for a coupling P
+    (dense |X|×|Y|) and duals log û = α̂/ε, log v̂ = β̂/ε (J of eq.
+    EntropicOTDualObjective; ‖K‖ cancels in the numerator). Returns
+    (relative gap, gap, primal score KL(π|K) − ‖K‖)."""
+    live = prob.mu > 0
+    X = np.flatnonzero(live)
+    Y = np.arange(prob.nu.size)
+    C = prob.cost(X, Y)
+    primal = kl_minus_mass(P[X], C, prob.mu[X], prob.nu, eps)
+    uvK = np.exp((alpha_hat[X][:, None] + beta_hat[None, :] - C) / eps) * prob.mu[X][:, None] * prob.nu[None, :]
+    dual_minus_K = prob.mu[X] @ (alpha_hat[X] / eps) + prob.nu @ (beta_hat / eps) - uvK.sum()
+    gap = primal - dual_minus_K
+    return gap / primal, gap, primal
+
+
+def refine_duals_glued(coarse, fine, alpha_hat_c):
+    """Dual initialisation at the next level as §6.4 describes it: the glued
+    coarse X-dual, interpolated linearly in log space (on α̂ = ε·log û)
+    onto the fine pixel centres. Coarse centres sit at coarse indices k;
+    fine pixel I of a level twice as fine sits at t = I/2 − 1/4 in coarse
+    index units, so every fine pixel lies between two coarse centres at
+    fractions 1/4 and 3/4 per axis (bilinear weights); the outermost fine
+    pixels lie a quarter step outside the outermost centres and take the
+    linear extrapolation of the last two. Affine α̂ is reproduced exactly.
+    The same α is used for both partitions."""
+    nc, nf = coarse.n, fine.n
+    A2 = np.asarray(alpha_hat_c, dtype=np.float64).reshape(nc, nc)
+
+    def weights(I):
+        t = I / 2.0 - 0.25
+        k0 = np.clip(np.floor(t).astype(np.int64), 0, nc - 2)
+        return k0, t - k0
+
+    I = np.arange(nf)
+    k0, w = weights(I)
+    rows = A2[k0, :] * (1.0 - w)[:, None] + A2[k0 + 1, :] * w[:, None]        # nf × nc
+    full = rows[:, k0] * (1.0 - w)[None, :] + rows[:, k0 + 1] * w[None, :]    # nf × nf
+    return full.ravel()
+
+
+# ----------------------------------------------------------------------------
 # the full coarse-to-fine run
 # ----------------------------------------------------------------------------
 @dataclass
@@ -514,7 +634,7 @@ class RunResult:
 
 
 def run_schedule(mu_img, nu_img, b, levels, schedule, params, *, on_half_sweep=None,
-                 before_half_sweep=None):
+                 before_half_sweep=None, dual_refinement="cell"):
     """Algorithm 2 inside the multi-scale / ε-scaling driver (§6.4).
 
     schedule: list of (eps, sweeps, level); level 0 is the coarsest image,
@@ -523,6 +643,9 @@ def run_schedule(mu_img, nu_img, b, levels, schedule, params, *, on_half_sweep=N
     before_half_sweep(prob, part, rows, alpha, eps) and on_half_sweep(prob,
     part, rows, alpha, eps, info) are called around every half-sweep (rows and
     α before, respectively after it).
+    dual_refinement: "cell" refines the last partition's α cell by cell
+    (refine_duals); "glued" glues α_A and α_B (glue_duals) and interpolates
+    the glued dual (refine_duals_glued), as §6.4 describes.
     """
     mus, nus = pyramid(mu_img, levels), pyramid(nu_img, levels)
     n = mu_img.shape[0]
@@ -539,7 +662,12 @@ def run_schedule(mu_img, nu_img, b, levels, schedule, params, *, on_half_sweep=N
         while lev < L:
             fine = level_problem(lev + 1)
             rows = refine_basic_marginals(prob, fine, rows)
-            a0 = refine_duals(prob, fine, alpha[last], last)
+            if dual_refinement == "glued" and eps is not None:
+                a_hat, _ = glue_duals(prob, alpha["A"], alpha["B"], eps)
+                a0 = refine_duals_glued(prob, fine, a_hat)
+                a0[fine.mu == 0] = 0.0
+            else:
+                a0 = refine_duals(prob, fine, alpha[last], last)
             alpha = {"A": a0.copy(), "B": a0.copy()}
             prob, lev = fine, lev + 1
         eps = eps_s

@@ -289,4 +289,3 @@ def test_zero_mass_pixels(lib):
     assert np.all(got[:, [0, 7 * n + 8, n * n - 1]] == 0.0)
     assert _rel_l1(got, want) < PLAN_TOL
     assert abs(cost - ref.history[-1][3].cost) / ref.history[-1][3].cost < COST_TOL
-

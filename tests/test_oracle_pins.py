@@ -466,3 +466,106 @@ def test_cell_gap_vanishes_at_the_optimum_and_ignores_cell_constants():
     shifted[prob.cell_points(prob.parts["B"][3])] += 7.0 * eps
     _, g1 = dd.cell_objectives(prob, "B", rows2, shifted, eps)
     assert g1 == pytest.approx(g0, rel=1e-9, abs=1e-13)
+
+
+# --------------------------------------------------------------------------
+# dual gluing (§6.3), eq. RelPDGap, glued dual refinement (§6.4)
+# --------------------------------------------------------------------------
+def test_gluing_graph_connects_the_a_cells():
+    prob = _grid(16, 2, 2, 20)            # 8×8 basic cells: 4×4 A cells, 5×5 B cells
+    edges = dd.gluing_graph(prob)
+    nA = len(prob.parts["A"])
+    seen = {0}
+    frontier = [0]
+    while frontier:
+        j = frontier.pop()
+        for j1, j2, *_ in edges:
+            if j1 == j and j2 not in seen:
+                seen.add(j2)
+                frontier.append(j2)
+    assert seen == set(range(nA))
+    for j1, j2, jb, X1, X2 in edges:       # X1, X2 lie in J1 ∩ J_B and J2 ∩ J_B
+        assert set(X1) <= set(prob.cell_points(prob.parts["A"][j1]))
+        assert set(X1) <= set(prob.cell_points(prob.parts["B"][jb]))
+        assert set(X2) <= set(prob.cell_points(prob.parts["A"][j2]))
+        assert (j2, j1, jb) in {(a, b, c) for a, b, c, *_ in edges}
+
+
+def test_glued_duals_of_consistent_rescalings_are_one_dual():
+    # u_{A,J} = λ_J u*, u_{B,J} = κ_J u*: the glued û is a constant multiple
+    # of u* (the path-product construction of §6.3); the sign of log q in the
+    # least-squares problem decides this (the opposite sign gives λ_J² u*)
+    prob = _grid(16, 2, 2, 21)
+    eps = 0.02
+    rng = np.random.default_rng(5)
+    a_star = eps * rng.normal(0.0, 2.0, prob.mu.size)
+    aA, aB = a_star.copy(), a_star.copy()
+    for J in prob.parts["A"]:
+        aA[prob.cell_points(J)] += eps * rng.normal(0.0, 3.0)
+    for J in prob.parts["B"]:
+        aB[prob.cell_points(J)] += eps * rng.normal(0.0, 3.0)
+    a_hat, _ = dd.glue_duals(prob, aA, aB, eps)
+    assert np.ptp(a_hat - a_star) / eps < 1e-9
+
+
+def test_glued_duals_at_convergence_close_the_gap():
+    # converged DD = global Sinkhorn: the glued duals are the global scaling
+    # up to a constant and eq. RelPDGap vanishes
+    prob = _grid(16, 4, 3, 22)
+    eps = 0.02
+    rows, alpha = _state_after(prob, eps, 40, 1e-13)
+    a_hat, _ = dd.glue_duals(prob, alpha["A"], alpha["B"], eps)
+    C = _full_cost(prob)
+    _, u, _ = referees.sinkhorn_scaling(prob.mu, prob.nu, C, eps, tol=1e-14)
+    assert np.ptp(a_hat - eps * np.log(u)) / eps < 1e-6
+    b_hat = dd.best_y_dual(prob, a_hat, eps)
+    P = dd.partition_plan(prob, "B", rows, alpha["B"], eps)
+    rel, gap, primal = dd.relative_pd_gap(prob, P, a_hat, b_hat, eps)
+    assert abs(rel) < 1e-8
+
+
+def test_glued_duals_keep_weak_duality_before_convergence():
+    # Prop. 2.5 (ii): J(û, v̂) ≤ KL(π|K) for every coupling π of μ and ν, here
+    # the optimal one and the product μ⊗ν, with the glued duals of an
+    # unconverged state; the gap is strictly positive there
+    prob = _grid(16, 4, 3, 23)
+    eps = 0.02
+    rows, alpha = _state_after(prob, eps, 1, 1e-6, max_iter=3)
+    a_hat, _ = dd.glue_duals(prob, alpha["A"], alpha["B"], eps)
+    b_hat = dd.best_y_dual(prob, a_hat, eps)
+    C = _full_cost(prob)
+    Pstar, _, _ = referees.sinkhorn_scaling(prob.mu, prob.nu, C, eps, tol=1e-14)
+    _, gap_star, _ = dd.relative_pd_gap(prob, Pstar, a_hat, b_hat, eps)
+    _, gap_prod, _ = dd.relative_pd_gap(prob, np.outer(prob.mu, prob.nu), a_hat, b_hat, eps)
+    assert gap_star > 1e-8
+    assert gap_prod > gap_star
+
+
+def test_glued_refinement_interpolates_linearly():
+    # fine pixel I sits at t = I/2 − 1/4 in coarse index units: an affine α̂
+    # is reproduced exactly, and α̂ = k² becomes t² + w(1 − w) with
+    # w ∈ {1/4, 3/4} inside (3/16) and w ∈ {−1/4, 5/4} at the two borders (−5/16)
+    coarse = _grid(8, 2, 2, 24)
+    fine = _grid(16, 2, 2, 25)
+    k = np.arange(8.0)
+    t = np.arange(16) / 2.0 - 0.25
+    aff = (0.3 + 0.7 * k[:, None] - 1.1 * k[None, :]).ravel()
+    got = dd.refine_duals_glued(coarse, fine, aff).reshape(16, 16)
+    assert np.allclose(got, 0.3 + 0.7 * t[:, None] - 1.1 * t[None, :], rtol=0, atol=1e-12)
+    quad = np.repeat((k ** 2)[:, None], 8, axis=1).ravel()
+    got = dd.refine_duals_glued(coarse, fine, quad).reshape(16, 16)[:, 5]
+    want = t ** 2 + 3.0 / 16.0
+    want[[0, -1]] = t[[0, -1]] ** 2 - 5.0 / 16.0
+    assert np.allclose(got, want, rtol=0, atol=1e-12)
+
+
+def test_glued_refinement_reaches_the_same_fixed_point():
+    mu = syn.gaussian_mixture(16, 3, 60)
+    nu = syn.gaussian_mixture(16, 3, 61)
+    sched = [(0.02, 3, 0), (0.01, 25, 1)]
+    par = dd.Params(err=1e-12, trunc=0.0)
+    r_cell = dd.run_schedule(mu, nu, 4, 2, sched, par)
+    r_glue = dd.run_schedule(mu, nu, 4, 2, sched, par, dual_refinement="glued")
+    a = dd.rows_to_dense(r_cell.rows, 256)
+    b = dd.rows_to_dense(r_glue.rows, 256)
+    assert np.abs(a - b).sum() < 1e-8
