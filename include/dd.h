@@ -226,7 +226,9 @@ dd_status dd_get_plan(dd_ctx* ctx, double trunc, int64_t* nnz, int64_t* row_ptr,
  * Entries are FP32 exponentials (as in dd_get_plan), logs and sums FP64. The
  * global primal-dual gap of eq. RelPDGap needs the glued duals of §6.3 and
  * is not computed. Allocates (and frees) 16 bytes per composite cell of
- * device memory; synchronises the stream. Any output pointer may be NULL.
+ * device memory; synchronises the stream; leaves the state and the
+ * statistics of the last half-sweep as they were. Any output pointer may be
+ * NULL.
  * DD_ERR_STATE for partition -1 before the first half-sweep of a level;
  * DD_ERR_ARG for another partition or a non-positive eps. */
 dd_status dd_objective(dd_ctx* ctx, int32_t partition, double eps, double* primal, double* gap,

@@ -1328,6 +1328,14 @@ dd_status dd_objective(dd_ctx* c, int32_t partition, double eps, double* primal,
     }
     dev_free(cell_obj);
     dev_free(out);
+    if (c->last_part >= 0 && part != c->last_part) {
+      // the per-cell workspace (supports, offsets, anchors) again describes
+      // the last half-sweep, as dd_get_cell_stats and dd_cell_training_pairs
+      // expect
+      DD_CUDA(cudaMemsetAsync(c->ws_counter, 0, sizeof(unsigned long long), c->stream));
+      DD_CUDA(launch_gather(sweep_args(c, c->last_part, c->eps_cur), c->stream));
+      DD_CUDA(cudaStreamSynchronize(c->stream));
+    }
     if (primal) *primal = h[0];
     if (gap) *gap = h[1];
     if (gap_abs) *gap_abs = h[2];
