@@ -645,7 +645,9 @@ def run_schedule(mu_img, nu_img, b, levels, schedule, params, *, on_half_sweep=N
     α before, respectively after it).
     dual_refinement: "cell" refines the last partition's α cell by cell
     (refine_duals); "glued" glues α_A and α_B (glue_duals) and interpolates
-    the glued dual (refine_duals_glued), as §6.4 describes.
+    the glued dual (refine_duals_glued), as §6.4 describes; "hybrid" starts
+    the A cells from the cell-wise refinement and the B cells from the glued
+    one (both are feasible starts; only the iteration counts differ).
     """
     mus, nus = pyramid(mu_img, levels), pyramid(nu_img, levels)
     n = mu_img.shape[0]
@@ -662,13 +664,15 @@ def run_schedule(mu_img, nu_img, b, levels, schedule, params, *, on_half_sweep=N
         while lev < L:
             fine = level_problem(lev + 1)
             rows = refine_basic_marginals(prob, fine, rows)
-            if dual_refinement == "glued" and eps is not None:
+            if dual_refinement in ("glued", "hybrid") and eps is not None:
                 a_hat, _ = glue_duals(prob, alpha["A"], alpha["B"], eps)
                 a0 = refine_duals_glued(prob, fine, a_hat)
                 a0[fine.mu == 0] = 0.0
+                a_cell = refine_duals(prob, fine, alpha[last], last) if dual_refinement == "hybrid" else a0
+                alpha = {"A": a_cell.copy(), "B": a0.copy()}
             else:
                 a0 = refine_duals(prob, fine, alpha[last], last)
-            alpha = {"A": a0.copy(), "B": a0.copy()}
+                alpha = {"A": a0.copy(), "B": a0.copy()}
             prob, lev = fine, lev + 1
         eps = eps_s
         for _ in range(sweeps):

@@ -565,7 +565,7 @@ def test_glued_refinement_reaches_the_same_fixed_point():
     sched = [(0.02, 3, 0), (0.01, 25, 1)]
     par = dd.Params(err=1e-12, trunc=0.0)
     r_cell = dd.run_schedule(mu, nu, 4, 2, sched, par)
-    r_glue = dd.run_schedule(mu, nu, 4, 2, sched, par, dual_refinement="glued")
     a = dd.rows_to_dense(r_cell.rows, 256)
-    b = dd.rows_to_dense(r_glue.rows, 256)
-    assert np.abs(a - b).sum() < 1e-8
+    for mode in ("glued", "hybrid"):
+        r = dd.run_schedule(mu, nu, 4, 2, sched, par, dual_refinement=mode)
+        assert np.abs(a - dd.rows_to_dense(r.rows, 256)).sum() < 1e-8, mode
