@@ -3,17 +3,18 @@
 This module holds no arithmetic of the domain-decomposition method. It only
 produces problem data:
 
-* Gaussian-mixture images standing in for the paper's test images, which are
-  "randomly generated mixtures of Gaussians with random variances and
-  magnitudes" (Bonafini & Schmitzer, §7.1 "Test data"). The images themselves
-  are not available, so the recipe below is used instead (isotropic or
-  anisotropic blobs plus a floor, normalised to mass 1).
+* Gaussian-mixture images standing in for the paper's test images (§7.1,
+  test data: sums of Gaussian blobs whose widths and heights are drawn at
+  random). The images themselves are not available, so the recipe below is
+  used instead (isotropic or anisotropic blobs plus a floor, normalised to
+  mass 1).
 * A feasible starting state (basic Y-marginals whose sums reproduce ν and whose
   masses match μ), the input that Algorithm 2 takes besides μ and ν. It is used
   for sampled comparisons at full size, where the coarse-to-fine run of the
   oracle would take too long.
-* The ε schedule of the paper's multi-scale protocol (§7.1 "Multi-scale and
-  ε-scaling"), expressed in [0,1]² units, ending at ε = 2h² at the finest level.
+* ε schedules of the paper's multi-scale protocol (§7.1, multi-scale and
+  ε-scaling) in [0,1]² units: the protocol of the Table 1 runs, and a variant
+  that ends at ε = 2h² on the finest level.
 
 Pixel (i, j) of an n×n image has centre ((i+½)h, (j+½)h) with h = 1/n; the
 flat index is i·n + j.
@@ -129,6 +130,22 @@ def paper_schedule(n: int, levels: int, final_sweeps: int, *, coarse_sweeps=(2, 
         else:
             steps.append((2.0 * d * d, int(final_sweeps), lev))
     return steps
+
+
+def table1_schedule(n: int):
+    """The iteration protocol of the paper's quantitative runs (§7.1, Table 1)
+    in [0,1]² units: layers from 8×8 up to n×n; on each layer with pixel
+    spacing Δ, 2 sweeps at ε = 2Δ², 1 at Δ², 1 at Δ²/2; on the finest layer 1
+    more sweep at Δ²/4 — (log2 n − 2)·8 + 2 half-sweeps in all. Returns
+    (schedule, levels) with schedule a list of (eps, sweeps, level)."""
+    levels = int(round(math.log2(n))) - 2
+    steps = []
+    d = 1.0 / 8
+    for lev in range(levels):
+        d = 1.0 / (8 * 2 ** lev)
+        steps += [(2.0 * d * d, 2, lev), (d * d, 1, lev), (0.5 * d * d, 1, lev)]
+    steps.append((0.25 * d * d, 1, levels - 1))
+    return steps, levels
 
 
 def halving_schedule(eps_start: float, eps_end: float, sweeps_each: int, level: int = 0):

@@ -569,3 +569,39 @@ def test_glued_refinement_reaches_the_same_fixed_point():
     for mode in ("glued", "hybrid"):
         r = dd.run_schedule(mu, nu, 4, 2, sched, par, dual_refinement=mode)
         assert np.abs(a - dd.rows_to_dense(r.rows, 256)).sum() < 1e-8, mode
+
+
+def test_table1_protocol_magnitudes_at_64():
+    # the paper's protocol on a 64² pair of synthetic mixtures: magnitudes of
+    # Table 1's 64×64 column (its images are not available, so the bands are
+    # wide): relative PD gap with glued duals (eq. RelPDGap), marginal errors
+    # within the stopping criterion, entries per pixel at the largest ε of the
+    # finest layer and at the end
+    with open(os.path.join(GOLDEN, "table1_64.json")) as f:
+        ref = json.load(f)
+    n = 64
+    sched, levels = syn.table1_schedule(n)
+    assert 2 * sum(s for _, s, _ in sched) == (6 - 2) * 8 + 2
+    mu = syn.gaussian_mixture(n, 6, 0, floor=1e-4)
+    nu = syn.gaussian_mixture(n, 6, 1, floor=1e-4)
+    nnz = []
+
+    def count(prob, part, rows, alpha, eps, info):
+        if prob.n == n:
+            nnz.append(sum(r[0].size for r in rows))
+
+    r = dd.run_schedule(mu, nu, 4, levels, sched, dd.Params(err=ref["err"]), on_half_sweep=count)
+    prob = r.prob
+    a_hat, _ = dd.glue_duals(prob, r.alpha["A"], r.alpha["B"], r.eps)
+    b_hat = dd.best_y_dual(prob, a_hat, r.eps)
+    P = dd.partition_plan(prob, r.last_part, r.rows, r.alpha[r.last_part], r.eps)
+    rel, _, _ = dd.relative_pd_gap(prob, P, a_hat, b_hat, r.eps)
+    err_x = np.abs(P.sum(axis=1) - prob.mu).sum()
+    err_y = dd.y_marginal_error(prob, r.rows)
+    assert 0.0 < rel < 10 * ref["relative_pd_gap"][0]
+    assert err_x <= ref["err"]
+    assert err_y < ref["l1_marginal_error_y"][0] + ref["l1_marginal_error_y"][1]
+    per_px_max = ref["entries_max"][0] / ref["pixels"]
+    per_px_final = ref["entries_final"][0] / ref["pixels"]
+    assert 0.5 * per_px_max < max(nnz) / n**2 < 2.0 * per_px_max
+    assert 0.4 * per_px_final < nnz[-1] / n**2 < 2.5 * per_px_final
