@@ -15,7 +15,7 @@ optimal transport":
   Y-marginals ν_i = P_Y(π_cell restricted to X_i × Y), BalanceMeasures and
   Truncate;
 * the Sinkhorn solver and its stopping rule (§6.2): start with a Y-iteration,
-  stop when the L1 error of the X-marginal after a Y-iteration is at most
+  stop once, right after a Y-iteration, Σ_x |P_X π − μ| is at most
   ‖μ_J‖·Err, so the last step is always a Y-iteration;
 * the multi-scale scheme (§6.4): coarse images are push-forwards under the
   quad-tree parent map, fine basic marginals are initialised by eq.
