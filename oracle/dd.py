@@ -313,7 +313,7 @@ def rows_to_dense(rows, ny):
 
 
 def y_marginal_error(prob, rows):
-    """Σ_y |Σ_i ν_i(y) − ν(y)| (L1 error of the Y-marginal)."""
+    """Σ_y |Σ_i ν_i(y) − ν(y)| (the Y-marginal error in L1)."""
     s = np.zeros(prob.nu.size)
     for c, v in rows:
         np.add.at(s, c, v)
