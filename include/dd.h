@@ -43,7 +43,8 @@ typedef enum {
   DD_ERR_OOM = 3,          /* device allocation failed                         */
   DD_ERR_CAPACITY = 4,     /* a caller buffer is too small (see *nnz)          */
   DD_ERR_NUMERIC = 5,      /* a cell solve produced a non-finite value         */
-  DD_ERR_STATE = 6         /* context unusable or call out of order            */
+  DD_ERR_STATE = 6,        /* context unusable or call out of order            */
+  DD_ERR_NOT_CONVERGED = 7 /* an iterative host solve missed its tolerance     */
 } dd_status;
 
 /* Image size and number of multi-scale levels (§6.4, §7.1 "Multi-scale"). */
@@ -233,6 +234,26 @@ dd_status dd_get_plan(dd_ctx* ctx, double trunc, int64_t* nnz, int64_t* row_ptr,
  * DD_ERR_ARG for another partition or a non-positive eps. */
 dd_status dd_objective(dd_ctx* ctx, int32_t partition, double eps, double* primal, double* gap,
                        double* gap_abs);
+
+/* The least-squares step of the dual gluing (§6.3, "Estimating the
+ * primal-dual gap"): on a graph of n_nodes vertices (the cells of partition
+ * A) with n_edges directed edges (j1[e], j2[e]) carrying the values logq[e]
+ * (log of the edge weights q), V[n_nodes] minimises
+ *     Σ_e ((V[j1[e]] − V[j2[e]]) + logq[e])²
+ * and has mean zero on every connected component (on a connected graph the
+ * gauge Σ V = 0). The sign in front of logq makes the result agree with the
+ * section's path-product construction (û_J = Π q along a path · u_{A,J}), so
+ * that û_J = exp(V[J])·u_{A,J}. Edges with j1 = j2 are ignored. Solved by
+ * conjugate gradients on the graph Laplacian with degree (Jacobi)
+ * preconditioning until ‖residual‖ ≤ tol·‖right-hand side‖ or max_iter
+ * iterations; *iters and *rel_residual (either may be NULL) report the run.
+ * Host code, FP64; needs no GPU and no context. DD_ERR_ARG for indices out
+ * of range, non-finite logq or negative sizes; DD_ERR_NOT_CONVERGED (V then
+ * holds the last iterate) when the tolerance was not reached; DD_ERR_OOM when
+ * host memory runs out. */
+dd_status dd_glue_potential(int32_t n_nodes, int64_t n_edges, const int32_t* j1, const int32_t* j2,
+                            const double* logq, double tol, int32_t max_iter, double* V,
+                            int32_t* iters, double* rel_residual);
 
 /* α = ε·log u_{C,J} of `partition` on every pixel of the current level, up to
  * one additive constant per composite cell (the gauge of Prop. 2.3 (ii)). */

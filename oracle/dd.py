@@ -533,6 +533,21 @@ def _log_mu_mean_exp(mu, t):
     return float(logsumexp(t[live] + np.log(mu[live]), axis=0) - np.log(mu[live].sum()))
 
 
+def helmholtz_potential(n_nodes, j1, j2, logq):
+    """The least-squares step of §6.3 (discrete Helmholtz decomposition of the
+    edge values): V minimising Σ_e ((V(j1_e) − V(j2_e)) + logq_e)² with
+    Σ V = 0 (sign reading: see glue_duals), as a dense least-squares problem
+    with the gauge as one more row (the edge residuals do not see it)."""
+    D = np.zeros((len(j1) + 1, n_nodes))
+    rhs = np.zeros(len(j1) + 1)
+    for e in range(len(j1)):
+        D[e, j1[e]] += 1.0
+        D[e, j2[e]] -= 1.0
+        rhs[e] = -logq[e]
+    D[-1, :] = 1.0
+    return np.linalg.lstsq(D, rhs, rcond=None)[0]
+
+
 def glue_duals(prob, alpha_A, alpha_B, eps):
     """Glued X-dual of §6.3 from the composite duals of both partitions.
 
@@ -550,15 +565,12 @@ def glue_duals(prob, alpha_A, alpha_B, eps):
     A = prob.parts["A"]
     edges = gluing_graph(prob)
     mu = prob.mu
-    D = np.zeros((len(edges) + 1, len(A)))
-    rhs = np.zeros(len(edges) + 1)
-    for e, (j1, j2, _, X1, X2) in enumerate(edges):
-        lq = (_log_mu_mean_exp(mu[X1], (alpha_A[X1] - alpha_B[X1]) / eps) +
-              _log_mu_mean_exp(mu[X2], (alpha_B[X2] - alpha_A[X2]) / eps))
-        D[e, j1], D[e, j2] = 1.0, -1.0
-        rhs[e] = -lq
-    D[-1, :] = 1.0           # the gauge Σ V = 0; edge residuals do not see it
-    V = np.linalg.lstsq(D, rhs, rcond=None)[0]
+    j1 = np.array([e[0] for e in edges], dtype=np.int64)
+    j2 = np.array([e[1] for e in edges], dtype=np.int64)
+    logq = np.array([_log_mu_mean_exp(mu[X1], (alpha_A[X1] - alpha_B[X1]) / eps) +
+                     _log_mu_mean_exp(mu[X2], (alpha_B[X2] - alpha_A[X2]) / eps)
+                     for _, _, _, X1, X2 in edges])
+    V = helmholtz_potential(len(A), j1, j2, logq)
     alpha_hat = np.asarray(alpha_A, dtype=np.float64).copy()
     for j, J in enumerate(A):
         X = prob.cell_points(J)

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libddot.so")
-SOURCES = ["dd_kernels.cu", "dd_api.cu", "dd_noalloc.cu", "dd_mlp.cu"]
+SOURCES = ["dd_kernels.cu", "dd_api.cu", "dd_noalloc.cu", "dd_mlp.cu", "dd_glue.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -1,0 +1,125 @@
+// Dual gluing (§6.3, "Estimating the primal-dual gap"): the least-squares
+// step that turns the edge values log q of the gluing graph into a potential
+// V on its vertices (a discrete Helmholtz decomposition: the gradient part of
+// the edge values). Host code in FP64; the graph has one vertex per cell of
+// partition A (16 384 at 1024² with 4×4 basic cells) and at most 12 edges
+// per B cell, so one solve costs well under a millisecond per iteration.
+//
+// Normal equations: with D the edge–vertex incidence matrix (row e has +1 at
+// j1_e and −1 at j2_e), V minimises ‖D V + log q‖², i.e. L V = −Dᵀ log q with
+// the graph Laplacian L = DᵀD (edge multiplicities counted). The right-hand
+// side lies in the range of L, so conjugate gradients (Jacobi-preconditioned
+// by the vertex degrees) converge; the solution is then shifted to mean zero
+// on every connected component, which is the minimum-norm least-squares
+// solution and, on a connected graph, the gauge Σ V = 0.
+#include <cmath>
+#include <cstdint>
+#include <numeric>
+#include <vector>
+
+#include "dd.h"
+
+namespace {
+
+int find_root(std::vector<int32_t>& parent, int32_t v) {
+  while (parent[v] != v) {
+    parent[v] = parent[parent[v]];
+    v = parent[v];
+  }
+  return v;
+}
+
+double dot(const std::vector<double>& a, const std::vector<double>& b) {
+  double s = 0.0;
+  for (size_t i = 0; i < a.size(); ++i) s += a[i] * b[i];
+  return s;
+}
+
+}  // namespace
+
+extern "C" dd_status dd_glue_potential(int32_t n_nodes, int64_t n_edges, const int32_t* j1, const int32_t* j2,
+                                       const double* logq, double tol, int32_t max_iter, double* V,
+                                       int32_t* iters, double* rel_residual) {
+  if (n_nodes < 1 || n_edges < 0 || !V || !(tol >= 0.0) || max_iter < 0) return DD_ERR_ARG;
+  if (n_edges > 0 && (!j1 || !j2 || !logq)) return DD_ERR_ARG;
+  for (int64_t e = 0; e < n_edges; ++e)
+    if (j1[e] < 0 || j1[e] >= n_nodes || j2[e] < 0 || j2[e] >= n_nodes || !std::isfinite(logq[e]))
+      return DD_ERR_ARG;
+  const size_t n = (size_t)n_nodes;
+  try {
+    std::vector<double> b(n, 0.0), deg(n, 0.0), x(n, 0.0), r, z(n), p(n), q(n);
+    // a loop edge (j1 = j2) has the constant residual log q and adds nothing
+    for (int64_t e = 0; e < n_edges; ++e) {
+      if (j1[e] == j2[e]) continue;
+      b[j1[e]] -= logq[e];
+      b[j2[e]] += logq[e];
+      deg[j1[e]] += 1.0;
+      deg[j2[e]] += 1.0;
+    }
+    auto laplacian = [&](const std::vector<double>& v, std::vector<double>& out) {
+      std::fill(out.begin(), out.end(), 0.0);
+      for (int64_t e = 0; e < n_edges; ++e) {
+        if (j1[e] == j2[e]) continue;
+        const double d = v[j1[e]] - v[j2[e]];
+        out[j1[e]] += d;
+        out[j2[e]] -= d;
+      }
+    };
+    auto precondition = [&](const std::vector<double>& in, std::vector<double>& out) {
+      for (size_t i = 0; i < n; ++i) out[i] = deg[i] > 0.0 ? in[i] / deg[i] : 0.0;
+    };
+    r = b;
+    const double bnorm = std::sqrt(dot(b, b));
+    double rnorm = bnorm;
+    int32_t it = 0;
+    bool converged = bnorm == 0.0;
+    if (!converged) {
+      precondition(r, z);
+      p = z;
+      double rz = dot(r, z);
+      for (; it < max_iter; ++it) {
+        laplacian(p, q);
+        const double pq = dot(p, q);
+        if (!(pq > 0.0)) break;
+        const double a = rz / pq;
+        for (size_t i = 0; i < n; ++i) {
+          x[i] += a * p[i];
+          r[i] -= a * q[i];
+        }
+        rnorm = std::sqrt(dot(r, r));
+        if (rnorm <= tol * bnorm) {
+          converged = true;
+          ++it;
+          break;
+        }
+        precondition(r, z);
+        const double rz_new = dot(r, z);
+        const double beta = rz_new / rz;
+        rz = rz_new;
+        for (size_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+      }
+    }
+    // mean zero on every connected component
+    std::vector<int32_t> parent(n);
+    std::iota(parent.begin(), parent.end(), 0);
+    for (int64_t e = 0; e < n_edges; ++e) {
+      const int32_t ra = find_root(parent, j1[e]), rb = find_root(parent, j2[e]);
+      if (ra != rb) parent[ra] = rb;
+    }
+    std::vector<double> csum(n, 0.0), ccount(n, 0.0);
+    for (size_t i = 0; i < n; ++i) {
+      const int32_t root = find_root(parent, (int32_t)i);
+      csum[root] += x[i];
+      ccount[root] += 1.0;
+    }
+    for (size_t i = 0; i < n; ++i) {
+      const int32_t root = find_root(parent, (int32_t)i);
+      V[i] = x[i] - csum[root] / ccount[root];
+    }
+    if (iters) *iters = it;
+    if (rel_residual) *rel_residual = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+    return converged ? DD_OK : DD_ERR_NOT_CONVERGED;
+  } catch (...) {
+    return DD_ERR_OOM;
+  }
+}

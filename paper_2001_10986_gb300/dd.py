@@ -13,9 +13,10 @@ import numpy as np
 
 from .build import LIB
 
-DD_OK, DD_ERR_ARG, DD_ERR_CUDA, DD_ERR_OOM, DD_ERR_CAPACITY, DD_ERR_NUMERIC, DD_ERR_STATE = range(7)
+(DD_OK, DD_ERR_ARG, DD_ERR_CUDA, DD_ERR_OOM, DD_ERR_CAPACITY, DD_ERR_NUMERIC, DD_ERR_STATE,
+ DD_ERR_NOT_CONVERGED) = range(8)
 _STATUS = {0: "DD_OK", 1: "DD_ERR_ARG", 2: "DD_ERR_CUDA", 3: "DD_ERR_OOM", 4: "DD_ERR_CAPACITY",
-           5: "DD_ERR_NUMERIC", 6: "DD_ERR_STATE"}
+           5: "DD_ERR_NUMERIC", 6: "DD_ERR_STATE", 7: "DD_ERR_NOT_CONVERGED"}
 
 
 class dd_grid(C.Structure):
@@ -74,6 +75,8 @@ _lib.dd_cost.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POI
 _lib.dd_get_basic_marginals.argtypes = [_P, C.POINTER(C.c_int64), _P, _P, _P, C.c_int64]
 _lib.dd_get_plan.argtypes = [_P, C.c_double, C.POINTER(C.c_int64), _P, _P, _P, C.c_int64]
 _lib.dd_get_duals.argtypes = [_P, C.c_int32, _pd]
+_lib.dd_glue_potential.argtypes = [C.c_int32, C.c_int64, _P, _P, _P, C.c_double, C.c_int32, _P,
+                                   C.POINTER(C.c_int32), C.POINTER(C.c_double)]
 _lib.dd_objective.argtypes = [_P, C.c_int32, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
                               C.POINTER(C.c_double)]
 _lib.dd_get_info.argtypes = [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -105,7 +108,7 @@ for _f in ("dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep", "dd_run_sch
            "dd_get_basic_marginals", "dd_get_plan", "dd_get_duals", "dd_get_info", "dd_get_profile",
            "dd_reset_profile", "dd_get_cell_stats", "dd_mlp_create", "dd_mlp_get_params", "dd_mlp_set_params",
            "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step", "dd_attach_mlp", "dd_cell_training_pairs",
-           "dd_autotune", "dd_objective"):
+           "dd_autotune", "dd_objective", "dd_glue_potential"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep",
@@ -113,7 +116,7 @@ EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", 
             "dd_get_info", "dd_get_cell_stats", "dd_get_profile", "dd_reset_profile", "dd_destroy",
             "dd_last_error", "dd_solve_cell_noalloc", "dd_mlp_num_params", "dd_mlp_create", "dd_mlp_destroy",
             "dd_mlp_get_params", "dd_mlp_set_params", "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step",
-            "dd_attach_mlp", "dd_cell_training_pairs", "dd_autotune", "dd_objective")
+            "dd_attach_mlp", "dd_cell_training_pairs", "dd_autotune", "dd_objective", "dd_glue_potential")
 
 
 def _check(ctx, st):
@@ -228,6 +231,24 @@ def dd_objective(ctx, partition=-1, eps=0.0):
     p, g, ga = C.c_double(), C.c_double(), C.c_double()
     _check(ctx, _lib.dd_objective(ctx, int(partition), float(eps), C.byref(p), C.byref(g), C.byref(ga)))
     return p.value, g.value, ga.value
+
+
+def dd_glue_potential(n_nodes, j1, j2, logq, tol=1e-12, max_iter=100000):
+    """Least-squares potential V of the dual gluing on a graph of n_nodes
+    vertices and edges (j1, j2) with values logq (host solve, no GPU).
+    Returns (V, iterations, relative residual)."""
+    a = np.ascontiguousarray(j1, dtype=np.int32)
+    b = np.ascontiguousarray(j2, dtype=np.int32)
+    q = np.ascontiguousarray(logq, dtype=np.float64)
+    if not (a.shape == b.shape == q.shape and a.ndim == 1):
+        raise DDError(DD_ERR_ARG, "j1, j2 and logq must be 1-D arrays of one length")
+    V = np.zeros(int(n_nodes), dtype=np.float64)
+    it, res = C.c_int32(), C.c_double()
+    st = _lib.dd_glue_potential(int(n_nodes), a.size, a.ctypes.data, b.ctypes.data, q.ctypes.data, float(tol),
+                                int(max_iter), V.ctypes.data, C.byref(it), C.byref(res))
+    if st != DD_OK:
+        raise DDError(st, _STATUS.get(st, "unknown status"))
+    return V, it.value, res.value
 
 
 def dd_get_duals(ctx, partition):

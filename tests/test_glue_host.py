@@ -1,0 +1,64 @@
+"""dd_glue_potential, the least-squares step of the dual gluing (§6.3), is
+host code of the C ABI: it runs here without a GPU and is compared with the
+oracle's dense least squares (oracle.dd.helmholtz_potential) and with closed
+forms."""
+import numpy as np
+import pytest
+
+from oracle import dd as odd
+from paper_2001_10986_gb300 import synthetic as syn
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2001_10986_gb300 import build
+    build.build()
+    from paper_2001_10986_gb300 import dd
+    return dd
+
+
+def _gluing_edges(n, b):
+    prob = odd.GridProblem(syn.gaussian_mixture(n, 2, 0), syn.gaussian_mixture(n, 2, 1), b, 1.0 / n)
+    edges = odd.gluing_graph(prob)
+    j1 = np.array([e[0] for e in edges], dtype=np.int32)
+    j2 = np.array([e[1] for e in edges], dtype=np.int32)
+    return len(prob.parts["A"]), j1, j2
+
+
+def test_matches_the_oracle_on_the_gluing_graph(lib):
+    nA, j1, j2 = _gluing_edges(64, 2)               # 16×16 A cells, 17×17 B cells
+    rng = np.random.default_rng(11)
+    logq = rng.normal(0.0, 1.0, j1.size)
+    V, it, res = lib.dd_glue_potential(nA, j1, j2, logq)
+    want = odd.helmholtz_potential(nA, j1, j2, logq)
+    assert res <= 1e-12 and it > 0
+    assert np.abs(V - want).max() <= 1e-9 * np.abs(want).max()
+
+
+def test_exact_gradient_is_recovered(lib):
+    # log q(j1, j2) = φ(j2) − φ(j1): the residuals vanish at V = φ − mean φ
+    nA, j1, j2 = _gluing_edges(32, 2)
+    phi = np.random.default_rng(12).normal(0.0, 3.0, nA)
+    V, _, _ = lib.dd_glue_potential(nA, j1, j2, phi[j2] - phi[j1])
+    assert np.abs(V - (phi - phi.mean())).max() < 1e-9
+
+
+def test_components_loops_and_errors(lib):
+    # two components (a path 0-1-2 and an edge 3-4) and a loop edge: each
+    # component has mean zero, as the minimum-norm least-squares solution
+    j1 = np.array([0, 1, 3, 2, 1], dtype=np.int32)
+    j2 = np.array([1, 2, 4, 2, 0], dtype=np.int32)
+    logq = np.array([0.5, -1.0, 2.0, 7.0, 0.25])
+    V, _, _ = lib.dd_glue_potential(5, j1, j2, logq)
+    want = odd.helmholtz_potential(5, j1, j2, logq)
+    assert abs(V[:3].sum()) < 1e-12 and abs(V[3:].sum()) < 1e-12
+    assert np.abs(V - want).max() < 1e-10
+    with pytest.raises(lib.DDError) as e:
+        lib.dd_glue_potential(5, np.array([0], np.int32), np.array([5], np.int32), np.array([1.0]))
+    assert e.value.status == lib.DD_ERR_ARG
+    with pytest.raises(lib.DDError) as e:
+        lib.dd_glue_potential(5, np.array([0], np.int32), np.array([1], np.int32), np.array([np.nan]))
+    assert e.value.status == lib.DD_ERR_ARG
+    with pytest.raises(lib.DDError) as e:
+        lib.dd_glue_potential(5, j1, j2, logq, max_iter=0)
+    assert e.value.status == lib.DD_ERR_NOT_CONVERGED

@@ -605,3 +605,13 @@ def test_table1_protocol_magnitudes_at_64():
     per_px_final = ref["entries_final"][0] / ref["pixels"]
     assert 0.5 * per_px_max < max(nnz) / n**2 < 2.0 * per_px_max
     assert 0.4 * per_px_final < nnz[-1] / n**2 < 2.5 * per_px_final
+
+
+def test_helmholtz_potential_of_an_exact_gradient():
+    # log q(j1, j2) = φ(j2) − φ(j1) on a cycle with both orientations: the
+    # least-squares potential is φ up to its mean (closed form)
+    j1 = np.array([0, 1, 2, 3, 1, 2, 3, 0])
+    j2 = np.array([1, 2, 3, 0, 0, 1, 2, 3])
+    phi = np.array([0.3, -1.2, 2.5, 0.1])
+    V = dd.helmholtz_potential(4, j1, j2, phi[j2] - phi[j1])
+    assert np.allclose(V, phi - phi.mean(), atol=1e-12)
