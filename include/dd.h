@@ -255,6 +255,21 @@ dd_status dd_glue_potential(int32_t n_nodes, int64_t n_edges, const int32_t* j1,
                             const double* logq, double tol, int32_t max_iter, double* V,
                             int32_t* iters, double* rel_residual);
 
+/* The glued X-dual of §6.3 from the duals of both partitions, on the host:
+ * n×n pixels, b×b basic cells (n/b even), μ and α_A, α_B = ε·log u per pixel
+ * (n² FP64 each, as dd_get_duals returns them; μ in any normalisation). For
+ * every basic cell i the μ-weighted means of exp(±(α_A − α_B)/ε) over its
+ * pixels give the edge values log q = s⁺_i + s⁻_{i'} of the ordered pairs
+ * of distinct basic cells (i, i') of each B cell (the A cells containing
+ * them are the vertices); V = dd_glue_potential(…) (tolerance 1e-13) and
+ * alpha_hat = α_A + ε·V[A cell] (n² FP64; 0 on pixels without mass).
+ * V (may be NULL) receives the (n/2b)² potentials in row-major order of the
+ * A cells. Host code; needs no GPU and no context. DD_ERR_ARG for bad sizes,
+ * non-finite or negative input, or a basic cell without mass;
+ * DD_ERR_NOT_CONVERGED / DD_ERR_OOM from the solve. */
+dd_status dd_glue_duals_host(int32_t n, int32_t b, const double* mu, const double* alpha_A,
+                             const double* alpha_B, double eps, double* alpha_hat, double* V);
+
 /* α = ε·log u_{C,J} of `partition` on every pixel of the current level, up to
  * one additive constant per composite cell (the gauge of Prop. 2.3 (ii)). */
 dd_status dd_get_duals(dd_ctx* ctx, int32_t partition, double* alpha);

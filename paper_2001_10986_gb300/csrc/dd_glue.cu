@@ -123,3 +123,88 @@ extern "C" dd_status dd_glue_potential(int32_t n_nodes, int64_t n_edges, const i
     return DD_ERR_OOM;
   }
 }
+
+// The glued X-dual of §6.3 on an n×n grid with b×b basic cells, from the
+// duals of both partitions (α = ε·log u, FP64, as dd_get_duals returns them).
+// A cell of A and a cell of B meet in at most one basic cell i; on it
+//   s⁺_i = log ⨍_i exp((α_A − α_B)/ε) dμ,   s⁻_i = log ⨍_i exp((α_B − α_A)/ε) dμ
+// (μ-weighted means), and every ordered pair (i, i') of distinct basic cells
+// of one B cell gives the edge (A(i), A(i')) with log q = s⁺_i + s⁻_{i'}.
+// Then V = dd_glue_potential(edges) and α̂ = α_A + ε·V on every A cell (0 on
+// pixels without mass).
+extern "C" dd_status dd_glue_duals_host(int32_t n, int32_t b, const double* mu, const double* alpha_A,
+                                        const double* alpha_B, double eps, double* alpha_hat, double* V) {
+  if (n < 2 || b < 1 || n % b != 0 || (n / b) % 2 != 0 || !mu || !alpha_A || !alpha_B || !alpha_hat ||
+      !(eps > 0.0) || !std::isfinite(eps))
+    return DD_ERR_ARG;
+  const int nb = n / b, na = nb / 2, nbB = nb / 2 + 1;
+  const size_t n2 = (size_t)n * n;
+  for (size_t p = 0; p < n2; ++p)
+    if (!std::isfinite(mu[p]) || mu[p] < 0.0 || !std::isfinite(alpha_A[p]) || !std::isfinite(alpha_B[p]))
+      return DD_ERR_ARG;
+  try {
+    // per basic cell: log of the μ-weighted means of exp(±(α_A − α_B)/ε)
+    std::vector<double> sp((size_t)nb * nb), sm((size_t)nb * nb);
+    for (int bi = 0; bi < nb; ++bi)
+      for (int bj = 0; bj < nb; ++bj) {
+        double mp = -INFINITY, mm = -INFINITY, mass = 0.0;
+        for (int r = bi * b; r < (bi + 1) * b; ++r)
+          for (int c = bj * b; c < (bj + 1) * b; ++c) {
+            const size_t p = (size_t)r * n + c;
+            if (!(mu[p] > 0.0)) continue;
+            const double d = (alpha_A[p] - alpha_B[p]) / eps;
+            mp = std::fmax(mp, d);
+            mm = std::fmax(mm, -d);
+            mass += mu[p];
+          }
+        if (!(mass > 0.0)) return DD_ERR_ARG;   // a basic cell needs positive mass (Def. 3.1)
+        double tp = 0.0, tm = 0.0;
+        for (int r = bi * b; r < (bi + 1) * b; ++r)
+          for (int c = bj * b; c < (bj + 1) * b; ++c) {
+            const size_t p = (size_t)r * n + c;
+            if (!(mu[p] > 0.0)) continue;
+            const double d = (alpha_A[p] - alpha_B[p]) / eps;
+            tp += mu[p] * std::exp(d - mp);
+            tm += mu[p] * std::exp(-d - mm);
+          }
+        sp[(size_t)bi * nb + bj] = mp + std::log(tp / mass);
+        sm[(size_t)bi * nb + bj] = mm + std::log(tm / mass);
+      }
+    // edges through the cells of B (B cell (R, C) holds basic rows 2R−1, 2R
+    // and columns 2C−1, 2C that exist)
+    std::vector<int32_t> j1, j2;
+    std::vector<double> lq;
+    for (int R = 0; R < nbB; ++R)
+      for (int Cc = 0; Cc < nbB; ++Cc) {
+        int cells[4], k = 0;
+        for (int di = 0; di < 2; ++di)
+          for (int dj = 0; dj < 2; ++dj) {
+            const int bi = 2 * R - 1 + di, bj = 2 * Cc - 1 + dj;
+            if (bi >= 0 && bi < nb && bj >= 0 && bj < nb) cells[k++] = bi * nb + bj;
+          }
+        for (int u = 0; u < k; ++u)
+          for (int w = 0; w < k; ++w) {
+            if (u == w) continue;
+            const int iu = cells[u], iw = cells[w];
+            j1.push_back((iu / nb / 2) * na + (iu % nb) / 2);
+            j2.push_back((iw / nb / 2) * na + (iw % nb) / 2);
+            lq.push_back(sp[iu] + sm[iw]);
+          }
+      }
+    std::vector<double> pot((size_t)na * na);
+    const dd_status st = dd_glue_potential(na * na, (int64_t)j1.size(), j1.data(), j2.data(), lq.data(), 1e-13,
+                                           100000, pot.data(), nullptr, nullptr);
+    if (st != DD_OK) return st;
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < n; ++c) {
+        const size_t p = (size_t)r * n + c;
+        const int ja = (r / b / 2) * na + (c / b) / 2;
+        alpha_hat[p] = mu[p] > 0.0 ? alpha_A[p] + eps * pot[ja] : 0.0;
+      }
+    if (V)
+      for (int j = 0; j < na * na; ++j) V[j] = pot[j];
+    return DD_OK;
+  } catch (...) {
+    return DD_ERR_OOM;
+  }
+}

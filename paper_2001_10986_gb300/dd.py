@@ -77,6 +77,7 @@ _lib.dd_get_plan.argtypes = [_P, C.c_double, C.POINTER(C.c_int64), _P, _P, _P, C
 _lib.dd_get_duals.argtypes = [_P, C.c_int32, _pd]
 _lib.dd_glue_potential.argtypes = [C.c_int32, C.c_int64, _P, _P, _P, C.c_double, C.c_int32, _P,
                                    C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+_lib.dd_glue_duals_host.argtypes = [C.c_int32, C.c_int32, _P, _P, _P, C.c_double, _P, _P]
 _lib.dd_objective.argtypes = [_P, C.c_int32, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
                               C.POINTER(C.c_double)]
 _lib.dd_get_info.argtypes = [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -108,7 +109,7 @@ for _f in ("dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep", "dd_run_sch
            "dd_get_basic_marginals", "dd_get_plan", "dd_get_duals", "dd_get_info", "dd_get_profile",
            "dd_reset_profile", "dd_get_cell_stats", "dd_mlp_create", "dd_mlp_get_params", "dd_mlp_set_params",
            "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step", "dd_attach_mlp", "dd_cell_training_pairs",
-           "dd_autotune", "dd_objective", "dd_glue_potential"):
+           "dd_autotune", "dd_objective", "dd_glue_potential", "dd_glue_duals_host"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep",
@@ -116,7 +117,8 @@ EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", 
             "dd_get_info", "dd_get_cell_stats", "dd_get_profile", "dd_reset_profile", "dd_destroy",
             "dd_last_error", "dd_solve_cell_noalloc", "dd_mlp_num_params", "dd_mlp_create", "dd_mlp_destroy",
             "dd_mlp_get_params", "dd_mlp_set_params", "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step",
-            "dd_attach_mlp", "dd_cell_training_pairs", "dd_autotune", "dd_objective", "dd_glue_potential")
+            "dd_attach_mlp", "dd_cell_training_pairs", "dd_autotune", "dd_objective", "dd_glue_potential",
+            "dd_glue_duals_host")
 
 
 def _check(ctx, st):
@@ -249,6 +251,25 @@ def dd_glue_potential(n_nodes, j1, j2, logq, tol=1e-12, max_iter=100000):
     if st != DD_OK:
         raise DDError(st, _STATUS.get(st, "unknown status"))
     return V, it.value, res.value
+
+
+def dd_glue_duals_host(mu, alpha_A, alpha_B, b, eps):
+    """Glued X-dual α̂ (n×n, FP64) and the A-cell potentials V from the duals
+    of both partitions (host solve, no GPU)."""
+    m = np.ascontiguousarray(mu, dtype=np.float64)
+    n = m.shape[0]
+    if m.shape != (n, n):
+        raise DDError(DD_ERR_ARG, "mu must be n×n")
+    a = np.ascontiguousarray(alpha_A, dtype=np.float64).reshape(n, n)
+    bb = np.ascontiguousarray(alpha_B, dtype=np.float64).reshape(n, n)
+    out = np.zeros((n, n), dtype=np.float64)
+    na = max(n // max(int(b), 1) // 2, 1)
+    V = np.zeros(na * na, dtype=np.float64)
+    st = _lib.dd_glue_duals_host(n, int(b), m.ctypes.data, a.ctypes.data, bb.ctypes.data, float(eps),
+                                 out.ctypes.data, V.ctypes.data)
+    if st != DD_OK:
+        raise DDError(st, _STATUS.get(st, "unknown status"))
+    return out, V
 
 
 def dd_get_duals(ctx, partition):

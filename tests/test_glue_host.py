@@ -62,3 +62,40 @@ def test_components_loops_and_errors(lib):
     with pytest.raises(lib.DDError) as e:
         lib.dd_glue_potential(5, j1, j2, logq, max_iter=0)
     assert e.value.status == lib.DD_ERR_NOT_CONVERGED
+
+
+def _duals(n, eps, seed):
+    rng = np.random.default_rng(seed)
+    k = np.arange(n)
+    smooth = 0.002 * ((k[:, None] - n / 2.0) ** 2 + 0.5 * (k[None, :] - n / 3.0) ** 2)
+    return (smooth + eps * rng.normal(0.0, 1.0, (n, n))).ravel()
+
+
+def test_glued_duals_match_the_oracle(lib):
+    n, b, eps = 32, 4, 0.01
+    mu = syn.gaussian_mixture(n, 3, 30)
+    mu[3, 5] = 0.0                    # a pixel without mass keeps α̂ = 0
+    nu = syn.gaussian_mixture(n, 3, 31)
+    aA, aB = _duals(n, eps, 1), _duals(n, eps, 2)
+    prob = odd.GridProblem(mu, nu, b, 1.0 / n)
+    want, Vw = odd.glue_duals(prob, aA, aB, eps)
+    got, V = lib.dd_glue_duals_host(mu, aA, aB, b, eps)
+    assert got[3, 5] == 0.0
+    assert np.abs(got.ravel() - want).max() <= 1e-9 * np.abs(want).max()
+    assert np.abs(V - Vw).max() <= 1e-9 * max(1.0, np.abs(Vw).max())
+
+
+def test_glued_duals_of_consistent_rescalings(lib):
+    # u_{A,J} = λ_J u*, u_{B,J} = κ_J u*: α̂ − α* is one constant
+    n, b, eps = 32, 2, 0.02
+    mu = syn.gaussian_mixture(n, 2, 32)
+    a_star = _duals(n, eps, 3)
+    rng = np.random.default_rng(4)
+    nb = n // b
+    lamA = rng.normal(0.0, 3.0, (nb // 2, nb // 2))
+    lamB = rng.normal(0.0, 3.0, (nb // 2 + 1, nb // 2 + 1))
+    r = np.arange(n) // b
+    aA = a_star + eps * lamA[(r // 2)[:, None], (r // 2)[None, :]].ravel()
+    aB = a_star + eps * lamB[((r + 1) // 2)[:, None], ((r + 1) // 2)[None, :]].ravel()
+    got, _ = lib.dd_glue_duals_host(mu, aA, aB, b, eps)
+    assert np.ptp(got.ravel() - a_star) / eps < 1e-9
