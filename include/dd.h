@@ -91,6 +91,12 @@ typedef struct {
                             Y-iteration. 2: the same also at the first sweep
                             after a change of ε. 3: at every half-sweep.
                             Default 0.                                         */
+  int32_t dual_refine;   /* duals at a new level. 0: both partitions start
+                            from the last partition's duals refined cell by
+                            cell (first-order, within each coarse cell).
+                            1 (hybrid): A as 0; B from the glued coarse dual
+                            of both partitions (§6.3, on the host) interpolated
+                            linearly (§6.4). Default 0.                        */
   int32_t mode;          /* 0: every half-sweep as separate launches with a host
                             check in between. 1: per-CTA cell solves as one
                             persistent wave of CTAs that take cells in launch
@@ -269,6 +275,15 @@ dd_status dd_glue_potential(int32_t n_nodes, int64_t n_edges, const int32_t* j1,
  * DD_ERR_NOT_CONVERGED / DD_ERR_OOM from the solve. */
 dd_status dd_glue_duals_host(int32_t n, int32_t b, const double* mu, const double* alpha_A,
                              const double* alpha_B, double eps, double* alpha_hat, double* V);
+
+/* Dual refinement of §6.4 on the host: alpha_c (n_coarse² FP64, a glued
+ * dual α̂ = ε·log û of one level) interpolated linearly onto the level
+ * twice as fine, alpha_f ((2·n_coarse)² FP64). Fine pixel I sits at
+ * t = I/2 − 1/4 in coarse index units (bilinear weights 1/4 and 3/4; linear
+ * extrapolation over the outermost quarter step), so affine α is reproduced
+ * exactly. Host code; no GPU, no context. DD_ERR_ARG for n_coarse < 2 or a
+ * NULL pointer. */
+dd_status dd_interpolate_dual_host(int32_t n_coarse, const double* alpha_c, double* alpha_f);
 
 /* α = ε·log u_{C,J} of `partition` on every pixel of the current level, up to
  * one additive constant per composite cell (the gauge of Prop. 2.3 (ii)). */

@@ -531,9 +531,77 @@ void half_sweep(dd_ctx* c, int part, double eps) {
 }
 
 // move the state one level finer (§6.4)
+// α = ε·log u of partition `part` at the current level in the absolute frame
+// (the conversion of dd_get_duals), FP64 on the host
+std::vector<double> host_duals(dd_ctx* c, int part) {
+  const LevelHost& h = c->lh[c->lev];
+  const int n2 = h.n * h.n;
+  const int nc = num_cells(part, h.nb);
+  std::vector<float> at((size_t)n2);
+  std::vector<int2> an((size_t)nc);
+  DD_CUDA(cudaMemcpyAsync(at.data(), c->alpha[part], 4 * (size_t)n2, cudaMemcpyDeviceToHost, c->stream));
+  DD_CUDA(cudaMemcpyAsync(an.data(), c->anchor[part], sizeof(int2) * nc, cudaMemcpyDeviceToHost, c->stream));
+  DD_CUDA(cudaStreamSynchronize(c->stream));
+  const double d2 = h.spacing * h.spacing;
+  std::vector<double> out((size_t)n2, 0.0);
+  for (int J = 0; J < nc; ++J) {
+    const CellGeom g = cell_geom(part, J, h.nb, c->b);
+    const int Dr = g.r0 - an[J].x, Dc = g.c0 - an[J].y;
+    for (int i = 0; i < g.H; ++i)
+      for (int j = 0; j < g.W; ++j) {
+        const size_t p = (size_t)(g.r0 + i) * h.n + g.c0 + j;
+        out[p] = (double)at[p] + 2 * d2 * ((double)Dr * i + (double)Dc * j);
+      }
+  }
+  return out;
+}
+
+// α (absolute frame, FP64, one value per pixel of level `lev`) into the cell
+// frames of partition `part` (the reduction of dd_set_state: per cell an
+// anchor from the mean slope, the cell's first value removed), written to the
+// device arrays alpha and anchor
+void upload_duals(dd_ctx* c, int lev, int part, const double* al, float* alpha, int2* anchor) {
+  const LevelHost& h = c->lh[lev];
+  const int n2 = h.n * h.n;
+  const int nc = num_cells(part, h.nb);
+  const double d2 = h.spacing * h.spacing;
+  std::vector<float> at((size_t)n2, 0.f);
+  std::vector<int2> an((size_t)nc);
+  for (int J = 0; J < nc; ++J) {
+    const CellGeom g = cell_geom(part, J, h.nb, c->b);
+    const double a00 = al[(size_t)g.r0 * h.n + g.c0];
+    const double sr = (al[(size_t)(g.r0 + g.H - 1) * h.n + g.c0] - a00) / (g.H - 1);
+    const double sc = (al[(size_t)g.r0 * h.n + g.c0 + g.W - 1] - a00) / (g.W - 1);
+    const int Dr = (int)std::lround(sr / (2 * d2));
+    const int Dc = (int)std::lround(sc / (2 * d2));
+    for (int i = 0; i < g.H; ++i)
+      for (int j = 0; j < g.W; ++j) {
+        const size_t p = (size_t)(g.r0 + i) * h.n + g.c0 + j;
+        at[p] = (float)(al[p] - a00 - 2 * d2 * ((double)Dr * i + (double)Dc * j));
+      }
+    an[J] = make_int2(g.r0 - Dr, g.c0 - Dc);
+  }
+  DD_CUDA(cudaMemcpyAsync(alpha, at.data(), 4 * (size_t)n2, cudaMemcpyHostToDevice, c->stream));
+  DD_CUDA(cudaMemcpyAsync(anchor, an.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, c->stream));
+  DD_CUDA(cudaStreamSynchronize(c->stream));
+}
+
 void refine(dd_ctx* c) {
   ensure_state(c);
   const int lc = c->lev, lf = lc + 1;
+  // hybrid dual refinement: the coarse duals of both partitions glued on the
+  // host (§6.3) before the coarse buffers go away
+  std::vector<double> glued;
+  if (c->opt.dual_refine == 1 && c->eps_cur > 0.0) {
+    const LevelHost& h0 = c->lh[lc];
+    const std::vector<double> aA = host_duals(c, 0), aB = host_duals(c, 1);
+    std::vector<double> mu((size_t)h0.n * h0.n);
+    for (size_t p = 0; p < mu.size(); ++p) mu[p] = (double)h0.mu_q[p] / kFixOne;
+    glued.resize(mu.size());
+    const dd_status st =
+        dd_glue_duals_host(h0.n, c->b, mu.data(), aA.data(), aB.data(), c->eps_cur, glued.data(), nullptr);
+    if (st != DD_OK) throw DdError{st, "dual gluing at the refinement failed"};
+  }
   const LevelHost& hc = c->lh[lc];
   const LevelHost& hf = c->lh[lf];
   LevelDev fine = upload_level(c, lf);
@@ -547,7 +615,6 @@ void refine(dd_ctx* c) {
   F.mu_f = fine.mu_f;
   F.log2mu = fine.log2mu;
   F.M_q = fine.M_q;
-  (void)hc;
 
   // keep the coarse state and duals alive while the fine buffers are created
   const int cpart = c->last_part < 0 ? 1 : c->last_part;
@@ -604,6 +671,15 @@ void refine(dd_ctx* c) {
   c->prof.launches += 7;
   check_debug(c, "refine_duals");
   DD_CUDA(cudaStreamSynchronize(c->stream));
+  if (!glued.empty()) {
+    // B starts from the glued coarse dual interpolated linearly (§6.4)
+    std::vector<double> af((size_t)hf.n * hf.n);
+    const dd_status st = dd_interpolate_dual_host(hc.n, glued.data(), af.data());
+    if (st != DD_OK) throw DdError{st, "dual interpolation at the refinement failed"};
+    for (size_t p = 0; p < af.size(); ++p)
+      if (hf.mu_q[p] == 0) af[p] = 0.0;
+    upload_duals(c, lf, 1, af.data(), a1, n1);
+  }
   dev_free(rp_c);
   dev_free(col_c);
   dev_free(val_c);

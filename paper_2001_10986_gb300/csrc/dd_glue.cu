@@ -208,3 +208,37 @@ extern "C" dd_status dd_glue_duals_host(int32_t n, int32_t b, const double* mu, 
     return DD_ERR_OOM;
   }
 }
+
+// Linear interpolation in log space (on α = ε·log û) from an n_c×n_c level to
+// the 2n_c×2n_c level (§6.4): fine pixel I lies at t = I/2 − 1/4 in coarse
+// index units, between coarse centres k₀ = ⌊t⌋ and k₀ + 1 with weight t − k₀
+// (1/4 or 3/4) per axis; the outermost fine pixels lie a quarter step
+// outside the outermost centres and take the linear extrapolation of the
+// last two (weights −1/4 and 5/4). Affine α is reproduced exactly.
+extern "C" dd_status dd_interpolate_dual_host(int32_t n_coarse, const double* alpha_c, double* alpha_f) {
+  if (n_coarse < 2 || !alpha_c || !alpha_f) return DD_ERR_ARG;
+  const int nc = n_coarse, nf = 2 * n_coarse;
+  try {
+    std::vector<int> k0(nf);
+    std::vector<double> w(nf);
+    for (int I = 0; I < nf; ++I) {
+      const double t = 0.5 * I - 0.25;
+      int k = (int)std::floor(t);
+      k = k < 0 ? 0 : (k > nc - 2 ? nc - 2 : k);
+      k0[I] = k;
+      w[I] = t - k;
+    }
+    std::vector<double> rows((size_t)nf * nc);   // interpolated along the rows first
+    for (int I = 0; I < nf; ++I)
+      for (int c = 0; c < nc; ++c)
+        rows[(size_t)I * nc + c] = alpha_c[(size_t)k0[I] * nc + c] * (1.0 - w[I]) +
+                                   alpha_c[(size_t)(k0[I] + 1) * nc + c] * w[I];
+    for (int I = 0; I < nf; ++I)
+      for (int J = 0; J < nf; ++J)
+        alpha_f[(size_t)I * nf + J] = rows[(size_t)I * nc + k0[J]] * (1.0 - w[J]) +
+                                      rows[(size_t)I * nc + k0[J] + 1] * w[J];
+    return DD_OK;
+  } catch (...) {
+    return DD_ERR_OOM;
+  }
+}

@@ -30,7 +30,7 @@ class dd_eps_step(C.Structure):
 class dd_options(C.Structure):
     _fields_ = [("err_tol", C.c_double), ("trunc", C.c_double), ("max_iter", C.c_int32),
                 ("threads_per_cell", C.c_int32), ("max_cluster_cells", C.c_int32), ("x_newton", C.c_int32),
-                ("warm", C.c_int32), ("mode", C.c_int32), ("stream", C.c_void_p),
+                ("warm", C.c_int32), ("dual_refine", C.c_int32), ("mode", C.c_int32), ("stream", C.c_void_p),
                 ("debug_flags", C.c_uint64)]
 
 
@@ -78,6 +78,7 @@ _lib.dd_get_duals.argtypes = [_P, C.c_int32, _pd]
 _lib.dd_glue_potential.argtypes = [C.c_int32, C.c_int64, _P, _P, _P, C.c_double, C.c_int32, _P,
                                    C.POINTER(C.c_int32), C.POINTER(C.c_double)]
 _lib.dd_glue_duals_host.argtypes = [C.c_int32, C.c_int32, _P, _P, _P, C.c_double, _P, _P]
+_lib.dd_interpolate_dual_host.argtypes = [C.c_int32, _P, _P]
 _lib.dd_objective.argtypes = [_P, C.c_int32, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
                               C.POINTER(C.c_double)]
 _lib.dd_get_info.argtypes = [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -109,7 +110,8 @@ for _f in ("dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep", "dd_run_sch
            "dd_get_basic_marginals", "dd_get_plan", "dd_get_duals", "dd_get_info", "dd_get_profile",
            "dd_reset_profile", "dd_get_cell_stats", "dd_mlp_create", "dd_mlp_get_params", "dd_mlp_set_params",
            "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step", "dd_attach_mlp", "dd_cell_training_pairs",
-           "dd_autotune", "dd_objective", "dd_glue_potential", "dd_glue_duals_host"):
+           "dd_autotune", "dd_objective", "dd_glue_potential", "dd_glue_duals_host",
+           "dd_interpolate_dual_host"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep",
@@ -118,7 +120,7 @@ EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", 
             "dd_last_error", "dd_solve_cell_noalloc", "dd_mlp_num_params", "dd_mlp_create", "dd_mlp_destroy",
             "dd_mlp_get_params", "dd_mlp_set_params", "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step",
             "dd_attach_mlp", "dd_cell_training_pairs", "dd_autotune", "dd_objective", "dd_glue_potential",
-            "dd_glue_duals_host")
+            "dd_glue_duals_host", "dd_interpolate_dual_host")
 
 
 def _check(ctx, st):
@@ -270,6 +272,19 @@ def dd_glue_duals_host(mu, alpha_A, alpha_B, b, eps):
     if st != DD_OK:
         raise DDError(st, _STATUS.get(st, "unknown status"))
     return out, V
+
+
+def dd_interpolate_dual_host(alpha_c):
+    """α on the level twice as fine from an n_c×n_c glued α (host, no GPU)."""
+    a = np.ascontiguousarray(alpha_c, dtype=np.float64)
+    nc = a.shape[0]
+    if a.shape != (nc, nc):
+        raise DDError(DD_ERR_ARG, "alpha_c must be n×n")
+    out = np.zeros((2 * nc, 2 * nc), dtype=np.float64)
+    st = _lib.dd_interpolate_dual_host(nc, a.ctypes.data, out.ctypes.data)
+    if st != DD_OK:
+        raise DDError(st, _STATUS.get(st, "unknown status"))
+    return out
 
 
 def dd_get_duals(ctx, partition):

@@ -74,5 +74,6 @@ def test_options_default(lib):
     o = lib.dd_options_default()
     assert o.err_tol == 1e-6 and o.trunc == 1e-15 and o.max_iter == 2000
     assert o.x_newton == 1 and o.max_cluster_cells == -1 and o.threads_per_cell == 0
+    assert o.dual_refine == 0
     with pytest.raises(TypeError):
         lib.dd_options_default(no_such_option=1)

@@ -99,3 +99,18 @@ def test_glued_duals_of_consistent_rescalings(lib):
     aB = a_star + eps * lamB[((r + 1) // 2)[:, None], ((r + 1) // 2)[None, :]].ravel()
     got, _ = lib.dd_glue_duals_host(mu, aA, aB, b, eps)
     assert np.ptp(got.ravel() - a_star) / eps < 1e-9
+
+
+def test_interpolation_matches_the_oracle(lib):
+    coarse = odd.GridProblem(syn.gaussian_mixture(16, 2, 40), syn.gaussian_mixture(16, 2, 41), 2, 1.0 / 16)
+    fine = odd.GridProblem(syn.gaussian_mixture(32, 2, 40), syn.gaussian_mixture(32, 2, 41), 2, 1.0 / 32)
+    a = np.random.default_rng(13).normal(0.0, 1.0, (16, 16))
+    got = lib.dd_interpolate_dual_host(a)
+    want = odd.refine_duals_glued(coarse, fine, a.ravel()).reshape(32, 32)
+    assert np.abs(got - want).max() < 1e-12
+    k = np.arange(16.0)
+    t = np.arange(32) / 2.0 - 0.25
+    aff = 0.5 - 2.0 * k[:, None] + 0.25 * k[None, :]
+    assert np.abs(lib.dd_interpolate_dual_host(aff) - (0.5 - 2.0 * t[:, None] + 0.25 * t[None, :])).max() < 1e-12
+    with pytest.raises(lib.DDError):
+        lib.dd_interpolate_dual_host(np.zeros((1, 1)))
