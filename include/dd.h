@@ -285,6 +285,21 @@ dd_status dd_glue_duals_host(int32_t n, int32_t b, const double* mu, const doubl
  * NULL pointer. */
 dd_status dd_interpolate_dual_host(int32_t n_coarse, const double* alpha_c, double* alpha_f);
 
+/* Relative primal-dual gap of eq. RelPDGap on the host, for a coupling π
+ * given as the CSR of dd_get_plan (row_ptr[n²+1] over X pixels, col = Y
+ * pixel, val = mass, total 1) and an X-dual alpha_hat (n² FP64, e.g. from
+ * dd_glue_duals_host) on an n×n level with pixel spacing 1/n (c = |x−y|²,
+ * K = e^{−c/ε}·μ⊗ν; μ, ν (n² FP64, ≥ 0) are normalised to mass 1 here).
+ * The Y-dual is the one that maximises J(û, ·) for the kernel restricted
+ * to the support of π: v̂(y) = 1 / Σ_{x: π(x,y)>0} û(x) μ(x) e^{−c/ε}.
+ * Outputs (each may be NULL): *primal = KL(π|K) − ‖K‖, *gap = KL(π|K) −
+ * J(û, v̂), *rel = gap / primal. Host code; no GPU, no context. DD_ERR_ARG
+ * for bad sizes, negative or non-finite input, an entry of π where ν = 0 or
+ * a y with ν(y) > 0 that π does not reach. */
+dd_status dd_relative_pd_gap_host(int32_t n, const double* mu, const double* nu, double eps,
+                                  const int64_t* row_ptr, const int32_t* col, const double* val,
+                                  const double* alpha_hat, double* rel, double* gap, double* primal);
+
 /* α = ε·log u_{C,J} of `partition` on every pixel of the current level, up to
  * one additive constant per composite cell (the gauge of Prop. 2.3 (ii)). */
 dd_status dd_get_duals(dd_ctx* ctx, int32_t partition, double* alpha);

@@ -242,3 +242,83 @@ extern "C" dd_status dd_interpolate_dual_host(int32_t n_coarse, const double* al
     return DD_ERR_OOM;
   }
 }
+
+// eq. RelPDGap for a coupling π (sparse, one row per X pixel: the output of
+// dd_get_plan) and a glued X-dual α̂ = ε·log û on an n×n level (pixel
+// spacing 1/n, c = |x − y|²). K = e^{−c/ε}·μ⊗ν with μ, ν normalised to mass 1.
+//   primal = KL(π|K) − ‖K‖ = Σ_entries π (log π − log K − 1);
+//   v̂(y)  = 1 / S(y), S(y) = Σ_{x: π(x,y) > 0} û(x) μ(x) e^{−c(x,y)/ε}, the
+//           Y-dual that maximises J(û, ·) for the kernel restricted to the
+//           support of π (every y with ν(y) > 0 carries entries of π);
+//   J − ‖K‖ = ⟨μ, log û⟩ + ⟨ν, log v̂⟩ − Σ_{supp π} û v̂ K
+//           = Σ_x μ α̂/ε − Σ_y ν log S(y) − Σ_{y covered} ν(y);
+//   gap = primal − (J − ‖K‖), rel = gap / primal.
+extern "C" dd_status dd_relative_pd_gap_host(int32_t n, const double* mu, const double* nu, double eps,
+                                             const int64_t* row_ptr, const int32_t* col, const double* val,
+                                             const double* alpha_hat, double* rel, double* gap, double* primal) {
+  if (n < 1 || !mu || !nu || !row_ptr || !alpha_hat || !(eps > 0.0) || !std::isfinite(eps)) return DD_ERR_ARG;
+  const size_t n2 = (size_t)n * n;
+  if (row_ptr[0] != 0) return DD_ERR_ARG;
+  for (size_t x = 0; x < n2; ++x)
+    if (row_ptr[x + 1] < row_ptr[x]) return DD_ERR_ARG;
+  const int64_t nnz = row_ptr[n2];
+  if (nnz > 0 && (!col || !val)) return DD_ERR_ARG;
+  double smu = 0.0, snu = 0.0;
+  for (size_t p = 0; p < n2; ++p) {
+    if (!std::isfinite(mu[p]) || mu[p] < 0.0 || !std::isfinite(nu[p]) || nu[p] < 0.0) return DD_ERR_ARG;
+    smu += mu[p];
+    snu += nu[p];
+  }
+  if (!(smu > 0.0) || !(snu > 0.0)) return DD_ERR_ARG;
+  for (int64_t e = 0; e < nnz; ++e)
+    if (col[e] < 0 || (size_t)col[e] >= n2 || !std::isfinite(val[e]) || val[e] < 0.0) return DD_ERR_ARG;
+  try {
+    const double h2 = 1.0 / ((double)n * n);
+    auto cost_over_eps = [&](size_t x, int32_t y) {
+      const double dr = (double)((long)(x / n) - (long)(y / n)), dc = (double)((long)(x % n) - (long)(y % n));
+      return h2 * (dr * dr + dc * dc) / eps;
+    };
+    // S(y) in log form: the largest exponent per y, then the sum
+    std::vector<double> m(n2, -INFINITY), s(n2, 0.0);
+    double pr = 0.0, dual_mu = 0.0;
+    for (size_t x = 0; x < n2; ++x) {
+      const double mx = mu[x] / smu;
+      if (!(mx > 0.0)) continue;
+      dual_mu += mx * alpha_hat[x] / eps;
+      for (int64_t e = row_ptr[x]; e < row_ptr[x + 1]; ++e) {
+        if (!(val[e] > 0.0)) continue;
+        const int32_t y = col[e];
+        const double ny = nu[y] / snu;
+        if (!(ny > 0.0)) return DD_ERR_ARG;   // π has mass where ν has none
+        const double coe = cost_over_eps(x, y);
+        pr += val[e] * (std::log(val[e]) + coe - std::log(mx) - std::log(ny) - 1.0);
+        m[y] = std::fmax(m[y], alpha_hat[x] / eps + std::log(mx) - coe);
+      }
+    }
+    for (size_t x = 0; x < n2; ++x) {
+      const double mx = mu[x] / smu;
+      if (!(mx > 0.0)) continue;
+      for (int64_t e = row_ptr[x]; e < row_ptr[x + 1]; ++e) {
+        if (!(val[e] > 0.0)) continue;
+        const int32_t y = col[e];
+        s[y] += std::exp(alpha_hat[x] / eps + std::log(mx) - cost_over_eps(x, y) - m[y]);
+      }
+    }
+    double dual_nu = 0.0, covered = 0.0;
+    for (size_t y = 0; y < n2; ++y) {
+      const double ny = nu[y] / snu;
+      if (!(ny > 0.0)) continue;
+      if (!(s[y] > 0.0)) return DD_ERR_ARG;    // ν(y) > 0 but no entry of π at y
+      dual_nu -= ny * (m[y] + std::log(s[y]));
+      covered += ny;
+    }
+    const double dual_minus_K = dual_mu + dual_nu - covered;
+    const double g = pr - dual_minus_K;
+    if (primal) *primal = pr;
+    if (gap) *gap = g;
+    if (rel) *rel = g / pr;
+    return DD_OK;
+  } catch (...) {
+    return DD_ERR_OOM;
+  }
+}

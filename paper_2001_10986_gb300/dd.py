@@ -79,6 +79,8 @@ _lib.dd_glue_potential.argtypes = [C.c_int32, C.c_int64, _P, _P, _P, C.c_double,
                                    C.POINTER(C.c_int32), C.POINTER(C.c_double)]
 _lib.dd_glue_duals_host.argtypes = [C.c_int32, C.c_int32, _P, _P, _P, C.c_double, _P, _P]
 _lib.dd_interpolate_dual_host.argtypes = [C.c_int32, _P, _P]
+_lib.dd_relative_pd_gap_host.argtypes = [C.c_int32, _P, _P, C.c_double, _P, _P, _P, _P,
+                                         C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
 _lib.dd_objective.argtypes = [_P, C.c_int32, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
                               C.POINTER(C.c_double)]
 _lib.dd_get_info.argtypes = [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -111,7 +113,7 @@ for _f in ("dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep", "dd_run_sch
            "dd_reset_profile", "dd_get_cell_stats", "dd_mlp_create", "dd_mlp_get_params", "dd_mlp_set_params",
            "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step", "dd_attach_mlp", "dd_cell_training_pairs",
            "dd_autotune", "dd_objective", "dd_glue_potential", "dd_glue_duals_host",
-           "dd_interpolate_dual_host"):
+           "dd_interpolate_dual_host", "dd_relative_pd_gap_host"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep",
@@ -120,7 +122,7 @@ EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", 
             "dd_last_error", "dd_solve_cell_noalloc", "dd_mlp_num_params", "dd_mlp_create", "dd_mlp_destroy",
             "dd_mlp_get_params", "dd_mlp_set_params", "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step",
             "dd_attach_mlp", "dd_cell_training_pairs", "dd_autotune", "dd_objective", "dd_glue_potential",
-            "dd_glue_duals_host", "dd_interpolate_dual_host")
+            "dd_glue_duals_host", "dd_interpolate_dual_host", "dd_relative_pd_gap_host")
 
 
 def _check(ctx, st):
@@ -287,6 +289,27 @@ def dd_interpolate_dual_host(alpha_c):
     return out
 
 
+def dd_relative_pd_gap_host(mu, nu, eps, plan, alpha_hat):
+    """(rel, gap, primal) of eq. RelPDGap for plan = (row_ptr, col, val) as
+    dd_get_plan returns it and a glued X-dual (host, no GPU)."""
+    m = np.ascontiguousarray(mu, dtype=np.float64)
+    n = m.shape[0]
+    v = np.ascontiguousarray(nu, dtype=np.float64).reshape(n, n)
+    rp = np.ascontiguousarray(plan[0], dtype=np.int64)
+    cl = np.ascontiguousarray(plan[1], dtype=np.int32)
+    vl = np.ascontiguousarray(plan[2], dtype=np.float64)
+    a = np.ascontiguousarray(alpha_hat, dtype=np.float64).reshape(n, n)
+    if m.shape != (n, n) or rp.size != n * n + 1 or cl.size != vl.size or cl.size < rp[-1]:
+        raise DDError(DD_ERR_ARG, "inconsistent sizes")
+    r, g, p = C.c_double(), C.c_double(), C.c_double()
+    st = _lib.dd_relative_pd_gap_host(n, m.ctypes.data, v.ctypes.data, float(eps), rp.ctypes.data,
+                                      cl.ctypes.data if cl.size else None, vl.ctypes.data if vl.size else None,
+                                      a.ctypes.data, C.byref(r), C.byref(g), C.byref(p))
+    if st != DD_OK:
+        raise DDError(st, _STATUS.get(st, "unknown status"))
+    return r.value, g.value, p.value
+
+
 def dd_get_duals(ctx, partition):
     _, nl, _, _, _ = dd_get_info(ctx)
     out = np.zeros(nl * nl, dtype=np.float64)
@@ -440,6 +463,15 @@ class DD:
 
     def objective(self, partition=-1, eps=0.0):
         return dd_objective(self.ctx, partition, eps)
+
+    def relative_pd_gap(self, mu, nu):
+        """eq. RelPDGap of the current state (§6.3): the duals of both
+        partitions glued on the host, the coupling of the last partition from
+        the GPU. mu, nu: the images at the current level. Returns
+        (rel, gap, primal)."""
+        _, nl, _, eps, _ = dd_get_info(self.ctx)
+        a_hat, _ = dd_glue_duals_host(mu, self.duals(0), self.duals(1), self.b, eps)
+        return dd_relative_pd_gap_host(mu, nu, eps, self.plan(0.0), a_hat)
 
     def cell_stats(self):
         return dd_get_cell_stats(self.ctx)

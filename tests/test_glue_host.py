@@ -114,3 +114,43 @@ def test_interpolation_matches_the_oracle(lib):
     assert np.abs(lib.dd_interpolate_dual_host(aff) - (0.5 - 2.0 * t[:, None] + 0.25 * t[None, :])).max() < 1e-12
     with pytest.raises(lib.DDError):
         lib.dd_interpolate_dual_host(np.zeros((1, 1)))
+
+
+def _csr(P):
+    rp = np.zeros(P.shape[0] + 1, dtype=np.int64)
+    cols, vals = [], []
+    for x in range(P.shape[0]):
+        nz = np.flatnonzero(P[x] > 0)
+        cols.append(nz)
+        vals.append(P[x, nz])
+        rp[x + 1] = rp[x] + nz.size
+    return rp, np.concatenate(cols).astype(np.int32), np.concatenate(vals)
+
+
+@pytest.mark.parametrize("sweeps,err,max_iter", [(2, 1e-6, 5), (40, 1e-13, 20000)])
+def test_relative_pd_gap_matches_the_oracle(lib, sweeps, err, max_iter):
+    # without truncation the coupling of the last partition reaches every
+    # (x, y), so the restricted kernel is the whole kernel and the host gap
+    # equals the oracle's dense eq. RelPDGap; at convergence it vanishes
+    n, b, eps = 16, 4, 0.01
+    mu = syn.gaussian_mixture(n, 3, 50)
+    nu = syn.gaussian_mixture(n, 3, 51)
+    prob = odd.GridProblem(mu, nu, b, 1.0 / n)
+    rows = odd.product_state(prob)
+    alpha = {"A": np.zeros(n * n), "B": np.zeros(n * n)}
+    par = odd.Params(err=err, trunc=0.0, max_iter=max_iter)
+    for l in range(2 * sweeps):
+        part = "AB"[l % 2]
+        rows, _ = odd.half_sweep(prob, part, rows, alpha[part], eps, par)
+    a_hat, _ = odd.glue_duals(prob, alpha["A"], alpha["B"], eps)
+    P = odd.partition_plan(prob, "B", rows, alpha["B"], eps)
+    assert (P > 0).all()
+    b_hat = odd.best_y_dual(prob, a_hat, eps)
+    rel_w, gap_w, prim_w = odd.relative_pd_gap(prob, P, a_hat, b_hat, eps)
+    rel, gap, prim = lib.dd_relative_pd_gap_host(mu, nu, eps, _csr(P), a_hat)
+    assert prim == pytest.approx(prim_w, rel=1e-10)
+    assert gap == pytest.approx(gap_w, rel=1e-7, abs=1e-12 * abs(prim_w))
+    if sweeps == 40:
+        assert abs(rel) < 1e-8
+    else:
+        assert rel > 1e-6

@@ -1,7 +1,9 @@
-"""The hybrid dual refinement (dd_options.dual_refine = 1: A cells from the
-cell-wise refinement, B cells from the glued coarse dual interpolated
-linearly, §6.3–6.4) against the oracle's run with the same refinement. This
-file is collected last so that a failure here does not hide other tests.
+"""Dual gluing on GPU runs (§6.3–6.4): the hybrid dual refinement
+(dd_options.dual_refine = 1: A cells from the cell-wise refinement, B cells
+from the glued coarse dual interpolated linearly) against the oracle's run
+with the same refinement, and eq. RelPDGap of a GPU state against the
+oracle's. This file is collected last so that a failure here does not hide
+other tests.
 """
 import numpy as np
 import pytest
@@ -41,3 +43,23 @@ def test_hybrid_refinement_matches_oracle(lib):
     assert np.abs(got - want).sum() / want.sum() < PLAN_TOL
     ref_cost = ref.history[-1][3].cost
     assert abs(cost - ref_cost) / ref_cost < COST_TOL
+
+
+def test_relative_pd_gap_of_a_gpu_run(lib):
+    # eq. RelPDGap of the converged 32² state: duals and coupling from the GPU,
+    # gluing and gap on the host, against the oracle's dense evaluation of its
+    # own run; both near zero (Table 1 reports about 1e-4 at Err = 1e-4)
+    mu = syn.gaussian_mixture(32, 3, 50)
+    nu = syn.gaussian_mixture(32, 3, 51)
+    sched = [(0.004, 4, 0)]
+    g = lib.DD(mu, nu, 4, 1, sched, err_tol=1e-7)
+    g.run_schedule()
+    rel, gap, primal = g.relative_pd_gap(mu, nu)
+    g.close()
+    ref = odd.run_schedule(mu, nu, 4, 1, sched, odd.Params(err=1e-10))
+    a_hat, _ = odd.glue_duals(ref.prob, ref.alpha["A"], ref.alpha["B"], ref.eps)
+    b_hat = odd.best_y_dual(ref.prob, a_hat, ref.eps)
+    P = odd.partition_plan(ref.prob, ref.last_part, ref.rows, ref.alpha[ref.last_part], ref.eps)
+    rel_w, _, primal_w = odd.relative_pd_gap(ref.prob, P, a_hat, b_hat, ref.eps)
+    assert primal == pytest.approx(primal_w, rel=1e-5)
+    assert abs(rel) < 1e-4 and abs(rel - rel_w) < 1e-5
