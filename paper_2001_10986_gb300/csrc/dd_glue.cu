@@ -12,6 +12,7 @@
 // by the vertex degrees) converge; the solution is then shifted to mean zero
 // on every connected component, which is the minimum-norm least-squares
 // solution and, on a connected graph, the gauge Σ V = 0.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <numeric>
