@@ -77,3 +77,17 @@ def test_options_default(lib):
     assert o.dual_refine == 0
     with pytest.raises(TypeError):
         lib.dd_options_default(no_such_option=1)
+
+
+def test_header_is_plain_c(tmp_path):
+    # the boundary is a C ABI: include/dd.h compiles as C99 without warnings
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "dd.h"\nint main(void) { dd_options o; dd_options_default(&o); return o.mode; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
