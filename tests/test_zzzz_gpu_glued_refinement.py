@@ -46,17 +46,19 @@ def test_hybrid_refinement_matches_oracle(lib):
 
 
 def test_relative_pd_gap_of_a_gpu_run(lib):
-    # eq. RelPDGap of the converged 32² state: duals and coupling from the GPU,
-    # gluing and gap on the host, against the oracle's dense evaluation of its
-    # own run; both near zero (Table 1 reports about 1e-4 at Err = 1e-4)
-    mu = syn.gaussian_mixture(32, 3, 50)
-    nu = syn.gaussian_mixture(32, 3, 51)
-    sched = [(0.004, 4, 0)]
-    g = lib.DD(mu, nu, 4, 1, sched, err_tol=1e-7)
+    # eq. RelPDGap after the multi-scale schedule (16² → 32², 6 final sweeps):
+    # duals and coupling from the GPU, gluing and gap on the host, against the
+    # oracle's dense evaluation of its own run of the same schedule (1.5e-7
+    # there; a few sweeps at one ε from the product coupling leave a gap of
+    # several percent, so the schedule matters)
+    mu = syn.gaussian_mixture(32, 4, 30)
+    nu = syn.gaussian_mixture(32, 4, 31)
+    sched = syn.paper_schedule(32, 2, 6)
+    g = lib.DD(mu, nu, 4, 2, sched, err_tol=1e-6)
     g.run_schedule()
     rel, gap, primal = g.relative_pd_gap(mu, nu)
     g.close()
-    ref = odd.run_schedule(mu, nu, 4, 1, sched, odd.Params(err=1e-10))
+    ref = odd.run_schedule(mu, nu, 4, 2, sched, odd.Params(err=1e-9))
     a_hat, _ = odd.glue_duals(ref.prob, ref.alpha["A"], ref.alpha["B"], ref.eps)
     b_hat = odd.best_y_dual(ref.prob, a_hat, ref.eps)
     P = odd.partition_plan(ref.prob, ref.last_part, ref.rows, ref.alpha[ref.last_part], ref.eps)
