@@ -300,6 +300,15 @@ dd_status dd_relative_pd_gap_host(int32_t n, const double* mu, const double* nu,
                                   const int64_t* row_ptr, const int32_t* col, const double* val,
                                   const double* alpha_hat, double* rel, double* gap, double* primal);
 
+/* Colour image of a coupling (§7.2): rgb[3·y + k] = Σ_i colours[3·i + k] ·
+ * ν_i(y) / ν(y) with ν(y) = Σ_i ν_i(y), for basic Y-marginals given as the
+ * CSR of dd_get_basic_marginals (row_ptr[n_basic+1], col < n², val ≥ 0);
+ * pixels that no ν_i reaches are black. colours: n_basic × 3 floats (e.g. a
+ * checkerboard); rgb: n² × 3 floats, written. Host code; no GPU, no context.
+ * DD_ERR_ARG for bad sizes, indices or values. */
+dd_status dd_coupling_image_host(int32_t n, int32_t n_basic, const int64_t* row_ptr, const int32_t* col,
+                                 const double* val, const float* colours, float* rgb);
+
 /* α = ε·log u_{C,J} of `partition` on every pixel of the current level, up to
  * one additive constant per composite cell (the gauge of Prop. 2.3 (ii)). */
 dd_status dd_get_duals(dd_ctx* ctx, int32_t partition, double* alpha);

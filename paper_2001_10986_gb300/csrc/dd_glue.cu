@@ -323,3 +323,34 @@ extern "C" dd_status dd_relative_pd_gap_host(int32_t n, const double* mu, const 
     return DD_ERR_OOM;
   }
 }
+
+// Visualisation of a coupling through its basic Y-marginals (§7.2): every
+// basic cell i has a colour col_i, and pixel y of the Y image gets
+// Σ_i col_i · ν_i(y) / ν(y), ν(y) = Σ_i ν_i(y). A deterministic coupling
+// (a Monge map T) paints T(X_i) in col_i; overlapping ν_i mix their colours
+// in proportion to their masses.
+extern "C" dd_status dd_coupling_image_host(int32_t n, int32_t n_basic, const int64_t* row_ptr, const int32_t* col,
+                                           const double* val, const float* colours, float* rgb) {
+  if (n < 1 || n_basic < 1 || !row_ptr || !colours || !rgb || row_ptr[0] != 0) return DD_ERR_ARG;
+  const size_t n2 = (size_t)n * n;
+  for (int32_t i = 0; i < n_basic; ++i)
+    if (row_ptr[i + 1] < row_ptr[i]) return DD_ERR_ARG;
+  const int64_t nnz = row_ptr[n_basic];
+  if (nnz > 0 && (!col || !val)) return DD_ERR_ARG;
+  for (int64_t e = 0; e < nnz; ++e)
+    if (col[e] < 0 || (size_t)col[e] >= n2 || !std::isfinite(val[e]) || val[e] < 0.0) return DD_ERR_ARG;
+  try {
+    std::vector<double> acc(3 * n2, 0.0), mass(n2, 0.0);
+    for (int32_t i = 0; i < n_basic; ++i)
+      for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+        const size_t y = (size_t)col[e];
+        for (int k = 0; k < 3; ++k) acc[3 * y + k] += (double)colours[3 * (size_t)i + k] * val[e];
+        mass[y] += val[e];
+      }
+    for (size_t y = 0; y < n2; ++y)
+      for (int k = 0; k < 3; ++k) rgb[3 * y + k] = mass[y] > 0.0 ? (float)(acc[3 * y + k] / mass[y]) : 0.f;
+    return DD_OK;
+  } catch (...) {
+    return DD_ERR_OOM;
+  }
+}

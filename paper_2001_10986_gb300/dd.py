@@ -81,6 +81,7 @@ _lib.dd_glue_duals_host.argtypes = [C.c_int32, C.c_int32, _P, _P, _P, C.c_double
 _lib.dd_interpolate_dual_host.argtypes = [C.c_int32, _P, _P]
 _lib.dd_relative_pd_gap_host.argtypes = [C.c_int32, _P, _P, C.c_double, _P, _P, _P, _P,
                                          C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+_lib.dd_coupling_image_host.argtypes = [C.c_int32, C.c_int32, _P, _P, _P, _P, _P]
 _lib.dd_objective.argtypes = [_P, C.c_int32, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
                               C.POINTER(C.c_double)]
 _lib.dd_get_info.argtypes = [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -113,7 +114,7 @@ for _f in ("dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep", "dd_run_sch
            "dd_reset_profile", "dd_get_cell_stats", "dd_mlp_create", "dd_mlp_get_params", "dd_mlp_set_params",
            "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step", "dd_attach_mlp", "dd_cell_training_pairs",
            "dd_autotune", "dd_objective", "dd_glue_potential", "dd_glue_duals_host",
-           "dd_interpolate_dual_host", "dd_relative_pd_gap_host"):
+           "dd_interpolate_dual_host", "dd_relative_pd_gap_host", "dd_coupling_image_host"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep",
@@ -122,7 +123,8 @@ EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", 
             "dd_last_error", "dd_solve_cell_noalloc", "dd_mlp_num_params", "dd_mlp_create", "dd_mlp_destroy",
             "dd_mlp_get_params", "dd_mlp_set_params", "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step",
             "dd_attach_mlp", "dd_cell_training_pairs", "dd_autotune", "dd_objective", "dd_glue_potential",
-            "dd_glue_duals_host", "dd_interpolate_dual_host", "dd_relative_pd_gap_host")
+            "dd_glue_duals_host", "dd_interpolate_dual_host", "dd_relative_pd_gap_host",
+            "dd_coupling_image_host")
 
 
 def _check(ctx, st):
@@ -310,6 +312,37 @@ def dd_relative_pd_gap_host(mu, nu, eps, plan, alpha_hat):
     return r.value, g.value, p.value
 
 
+def checkerboard_colours(n_basic_side, a=(0.95, 0.55, 0.1), b=(0.1, 0.35, 0.9)):
+    """Colours of the basic cells in a checkerboard of two colours (§7.2)."""
+    i, j = np.divmod(np.arange(n_basic_side * n_basic_side), n_basic_side)
+    return np.where(((i + j) % 2 == 0)[:, None], np.array(a, np.float32), np.array(b, np.float32))
+
+
+def dd_coupling_image_host(n, basic_marginals, colours):
+    """n×n×3 float image Σ_i col_i·ν_i/ν of basic marginals (row_ptr, col, val)."""
+    rp = np.ascontiguousarray(basic_marginals[0], dtype=np.int64)
+    cl = np.ascontiguousarray(basic_marginals[1], dtype=np.int32)
+    vl = np.ascontiguousarray(basic_marginals[2], dtype=np.float64)
+    cs = np.ascontiguousarray(colours, dtype=np.float32)
+    nb = rp.size - 1
+    if cs.shape != (nb, 3) or cl.size != vl.size or cl.size < rp[-1]:
+        raise DDError(DD_ERR_ARG, "inconsistent sizes")
+    out = np.zeros((int(n), int(n), 3), dtype=np.float32)
+    st = _lib.dd_coupling_image_host(int(n), nb, rp.ctypes.data, cl.ctypes.data if cl.size else None,
+                                     vl.ctypes.data if vl.size else None, cs.ctypes.data, out.ctypes.data)
+    if st != DD_OK:
+        raise DDError(st, _STATUS.get(st, "unknown status"))
+    return out
+
+
+def write_ppm(path, rgb):
+    """Write an n×m×3 image with values in [0, 1] as a binary PPM file."""
+    img = (np.clip(np.asarray(rgb, dtype=np.float64), 0.0, 1.0) * 255.0 + 0.5).astype(np.uint8)
+    with open(path, "wb") as f:
+        f.write(b"P6\n%d %d\n255\n" % (img.shape[1], img.shape[0]))
+        f.write(img.tobytes())
+
+
 def dd_get_duals(ctx, partition):
     _, nl, _, _, _ = dd_get_info(ctx)
     out = np.zeros(nl * nl, dtype=np.float64)
@@ -463,6 +496,14 @@ class DD:
 
     def objective(self, partition=-1, eps=0.0):
         return dd_objective(self.ctx, partition, eps)
+
+    def coupling_image(self, colours=None):
+        """§7.2 colour image (n_l×n_l×3) of the current basic marginals; the
+        default colours are a checkerboard over the basic cells."""
+        _, nl, nbasic, _, _ = dd_get_info(self.ctx)
+        if colours is None:
+            colours = checkerboard_colours(int(round(nbasic ** 0.5)))
+        return dd_coupling_image_host(nl, self.basic_marginals(), colours)
 
     def relative_pd_gap(self, mu, nu):
         """eq. RelPDGap of the current state (§6.3): the duals of both

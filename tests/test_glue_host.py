@@ -154,3 +154,36 @@ def test_relative_pd_gap_matches_the_oracle(lib, sweeps, err, max_iter):
         assert abs(rel) < 1e-8
     else:
         assert rel > 1e-6
+
+
+def _rows_csr(rows):
+    rp = np.zeros(len(rows) + 1, dtype=np.int64)
+    for i, (c, _) in enumerate(rows):
+        rp[i + 1] = rp[i] + c.size
+    return rp, np.concatenate([c for c, _ in rows]).astype(np.int32), np.concatenate([v for _, v in rows])
+
+
+def test_coupling_image(lib, tmp_path):
+    # §7.2: the product coupling paints every pixel with the μ-weighted mean
+    # colour; the identity coupling (ν_i = μ on X_i) paints the checkerboard
+    # of the basic cells itself; overlapping ν_i mix in proportion to mass
+    n, b = 16, 4
+    mu = syn.gaussian_mixture(n, 2, 60)
+    prob = odd.GridProblem(mu, mu, b, 1.0 / n)
+    colours = lib.checkerboard_colours(n // b)
+    img = lib.dd_coupling_image_host(n, _rows_csr(odd.product_state(prob)), colours)
+    mean = (prob.basic_mass[:, None] * colours).sum(axis=0) / prob.basic_mass.sum()
+    assert np.abs(img - mean[None, None, :]).max() < 1e-6
+    ident = [(np.sort(X), mu.ravel()[np.sort(X)]) for X in prob.basic]
+    img = lib.dd_coupling_image_host(n, _rows_csr(ident), colours)
+    cell = (np.arange(n)[:, None] // b) * (n // b) + np.arange(n)[None, :] // b
+    assert np.abs(img - colours[cell]).max() < 1e-7
+    rows = [(np.array([5]), np.array([1.0])), (np.array([5, 6]), np.array([3.0, 2.0]))]
+    two = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, 1.0]], np.float32)
+    img = lib.dd_coupling_image_host(4, _rows_csr(rows), two)
+    assert np.allclose(img[1, 1], [0.25, 0.0, 0.75]) and np.allclose(img[1, 2], [0.0, 0.0, 1.0])
+    assert np.all(img[0, 0] == 0.0)                   # no mass: black
+    path = tmp_path / "c.ppm"
+    lib.write_ppm(path, img)
+    data = path.read_bytes()
+    assert data.startswith(b"P6\n4 4\n255\n") and len(data) == len(b"P6\n4 4\n255\n") + 48
