@@ -615,3 +615,37 @@ def test_helmholtz_potential_of_an_exact_gradient():
     phi = np.array([0.3, -1.2, 2.5, 0.1])
     V = dd.helmholtz_potential(4, j1, j2, phi[j2] - phi[j1])
     assert np.allclose(V, phi - phi.mean(), atol=1e-12)
+
+
+def test_stop_rule_after_truncation_loss():
+    # ν_cell lighter than μ_J by δ (mass that Truncate removed): no coupling
+    # of the cell meets μ_J, and the rescaled stop rule still ends the solve;
+    # at its end P_X π = μ·‖ν‖/‖μ‖ up to the tolerance, so the reported
+    # (unscaled) X-error is δ in closed form
+    rng = np.random.default_rng(7)
+    C = rng.uniform(0, 1, (6, 9))
+    mu = rng.uniform(0.5, 1, 6); mu /= mu.sum()
+    nu = rng.uniform(0.5, 1, 9); nu /= nu.sum()
+    delta = 1e-6
+    nu_cell = nu * (1.0 - delta)
+    f, g, P, it, ex = dd.sinkhorn_cell(C, mu, nu_cell, np.zeros(6), 0.2, 1e-12, 100000)
+    assert it < 100000
+    assert ex == pytest.approx(delta, rel=1e-4)
+    np.testing.assert_allclose(P.sum(axis=1), mu * (1.0 - delta), rtol=1e-10)
+
+
+def test_truncate_keeps_exactly_the_entries_above_the_threshold():
+    # Truncate (§6.1, §7.1): after a half-sweep every stored entry of the
+    # basic marginals is above the threshold, and the mass reported as
+    # truncated is what the Y-marginal lost
+    prob = _grid(16, 4, 3, 26)
+    eps = 0.004
+    rows = dd.product_state(prob)
+    alpha = np.zeros(prob.mu.size)
+    trunc = 1e-9
+    new_rows, info = dd.half_sweep(prob, "A", rows, alpha, eps, dd.Params(err=1e-8, trunc=trunc))
+    vals = np.concatenate([v for _, v in new_rows])
+    assert vals.min() > trunc
+    assert info.truncated_mass > 0
+    s = dd.rows_to_dense(new_rows, prob.nu.size).sum(axis=0)
+    assert prob.nu.sum() - s.sum() == pytest.approx(info.truncated_mass, rel=1e-6, abs=1e-15)
