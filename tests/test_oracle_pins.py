@@ -649,3 +649,27 @@ def test_truncate_keeps_exactly_the_entries_above_the_threshold():
     assert info.truncated_mass > 0
     s = dd.rows_to_dense(new_rows, prob.nu.size).sum(axis=0)
     assert prob.nu.sum() - s.sum() == pytest.approx(info.truncated_mass, rel=1e-6, abs=1e-15)
+
+
+def test_balance_measures_closed_form():
+    # reading R3 by hand: ν_0 = (2, 1) carries 1 too much (target 2), so a
+    # third of each entry moves; the deficits 0.25 and 0.75 take a quarter
+    # and three quarters of what moved, entry by entry
+    parts = [np.array([2.0, 1.0]), np.array([0.5, 0.0]), np.array([0.0, 1.5])]
+    out = dd.balance_measures([p.copy() for p in parts], [2.0, 0.75, 2.25])
+    moved = np.array([2.0, 1.0]) / 3.0
+    np.testing.assert_allclose(out[0], np.array([2.0, 1.0]) - moved, rtol=1e-15)
+    np.testing.assert_allclose(out[1], np.array([0.5, 0.0]) + 0.25 * moved, rtol=1e-15)
+    np.testing.assert_allclose(out[2], np.array([0.0, 1.5]) + 0.75 * moved, rtol=1e-15)
+
+
+def test_gather_is_the_sum_on_the_union_of_supports():
+    # Algorithm 2: ν_cell = Σ_{i∈J} ν_i, here on hand-made rows
+    rows = [(np.array([1, 4, 7]), np.array([0.1, 0.2, 0.3])),
+            (np.array([4, 5]), np.array([0.4, 0.5])),
+            (np.array([0, 7]), np.array([0.6, 0.7]))]
+    cols, nu_cell = dd.gather(rows, [0, 1, 2])
+    np.testing.assert_array_equal(cols, [0, 1, 4, 5, 7])
+    np.testing.assert_allclose(nu_cell, [0.6, 0.1, 0.6, 0.5, 1.0], rtol=1e-15)
+    cols, nu_cell = dd.gather(rows, [1])
+    np.testing.assert_array_equal(cols, [4, 5])
