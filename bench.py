@@ -59,7 +59,6 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-ttc", action="store_true", help="skip the time-to-converged runs")
     p.add_argument("--no-learned", action="store_true", help="skip the learned warm-start arm")
-    p.add_argument("--cpu-cells", type=int, default=160)
     p.add_argument("--err", type=float, default=1e-6)
     p.add_argument("--tpc", type=int, default=0, help="threads per cell solve (0: library choice)")
     p.add_argument("--clusters", type=int, default=-1, help="max cells solved by 8-CTA clusters (-1: library choice)")
@@ -134,46 +133,155 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-class OracleSample:
-    """The FP64 oracle on a bounded sample of the same workload: one half-sweep
-    over a set of A-cells of the finest level, started from a feasible
-    synthetic state with zero duals; the time per cell is extrapolated to whole
-    sweeps."""
+class OracleBlock:
+    """The FP64 oracle on a bounded sample of the same workload, in the same
+    warm steady state the GPU arm sweeps: a block of 16×16 basic cells
+    (64×64 pixels, 64 A cells and the 49 B cells inside it) of the 1024²
+    problem at the final ε = 2h², with ν and the basic marginals of a
+    feasible synthetic state (`synthetic.feasible_state`). `warm_sweeps`
+    untimed oracle sweeps of the block (A then B, from zero duals) bring its
+    cells to warm starts; every timed step is one more sweep of the block.
+    px·sweeps/s of the block needs no extrapolation (the unit is intensive).
+    The cells of a half-sweep are independent (§6.1) and are split over a
+    pool of `workers` processes (started with spawn), each running the
+    oracle's own half_sweep on its cells; workers = 1 runs in-process."""
 
-    def __init__(self, workload):
+    MARGIN = 16          # pixels of Y around the block (the rows reach ≤ 13)
+
+    def __init__(self, workload, workers=1, block=16, warm_sweeps=6, err=1e-6):
         import numpy as np
         from oracle import dd as odd
         from paper_2001_10986_gb300 import synthetic as syn
         self.np, self.odd = np, odd
         w = syn.WORKLOADS[workload]
-        self.n, self.b = w.n, w.b
+        self.n, self.b, self.err = w.n, w.b, err
         mu, _ = syn.image_pair(w, 0)
-        nu, rp, col, val = syn.feasible_state(mu, self.b, seed=7)
-        self.prob = odd.GridProblem(mu, nu, self.b, 1.0 / self.n)
-        self.rows = odd.rows_from_csr(rp, col, val)
+        # the feasible state of a window around the block only (its rows are
+        # those of the full image: each depends on its own basic cell alone)
+        b0 = (self.n // self.b) // 2 - block // 2          # first basic cell of the block
+        m = self.MARGIN
+        self.p0 = b0 * self.b - m                           # window origin (pixels)
+        side = block * self.b + 2 * m
+        nu_full, rp, col, val = syn.feasible_state(mu, self.b, seed=7)
+        win_mu = mu[self.p0:self.p0 + side, self.p0:self.p0 + side]
+        win_nu = nu_full[self.p0:self.p0 + side, self.p0:self.p0 + side]
+        self.prob = odd.GridProblem(win_mu, win_nu, self.b, 1.0 / self.n)
+        nbw, nbf = side // self.b, self.n // self.b
+        rows = []
+        for R in range(nbw):
+            for S in range(nbw):
+                i = (self.p0 // self.b + R) * nbf + (self.p0 // self.b + S)
+                c = col[rp[i]:rp[i + 1]].astype(np.int64)
+                r_, c_ = np.divmod(c, self.n)
+                r_, c_ = r_ - self.p0, c_ - self.p0
+                ok = (r_ >= 0) & (r_ < side) & (c_ >= 0) & (c_ < side)
+                rows.append(((r_[ok] * side + c_[ok]), val[rp[i]:rp[i + 1]][ok].astype(np.float64)))
+        self.rows = rows
+        blk = set(range(m // self.b, m // self.b + block))
+        def inside(J):
+            return all((i // nbw) in blk and (i % nbw) in blk for i in J)
+        self.cells = {p: [k for k, J in enumerate(self.prob.parts[p]) if inside(J)] for p in "AB"}
         self.eps = 2.0 / self.n ** 2
-        self.rng = np.random.default_rng(0)
-        self.cells_per_sweep = len(self.prob.parts["A"]) + len(self.prob.parts["B"])
+        self.alpha = {"A": np.zeros(side * side), "B": np.zeros(side * side)}
+        self.px = (block * self.b) ** 2
+        self.workers = max(1, int(workers))
+        self.pool = None
+        if self.workers > 1:
+            import multiprocessing as mp
+            self.pool = mp.get_context("spawn").Pool(
+                self.workers, initializer=_oracle_block_init, initargs=(win_mu, win_nu, self.b, 1.0 / self.n))
+        self.iters = []
+        for _ in range(warm_sweeps):
+            self.sweep()
 
-    def run(self, n_cells):
-        cells = self.rng.choice(len(self.prob.parts["A"]), n_cells, replace=False).tolist()
-        alpha = self.np.zeros(self.n * self.n)
+    def _half(self, part):
+        odd = self.odd
+        cells = self.cells[part]
+        if self.pool is None:
+            self.rows, info = odd.half_sweep(self.prob, part, self.rows, self.alpha[part], self.eps,
+                                             odd.Params(err=self.err), cells=cells)
+            return list(info.iters)
+        k = self.workers
+        chunks = [cells[s::k] for s in range(k) if cells[s::k]]
+        tasks = []
+        for ch in chunks:
+            need = {i for jn in ch for i in self.prob.parts[part][jn]}
+            tasks.append((part, {i: self.rows[i] for i in need}, self.alpha[part], self.eps, self.err, ch))
+        its = []
+        for rows_sub, alpha_sub, it in self.pool.map(_oracle_block_task, tasks):
+            for i, r in rows_sub.items():
+                self.rows[i] = r
+            for X, a in alpha_sub:
+                self.alpha[part][X] = a
+            its += it
+        return its
+
+    def sweep(self):
         t = time.perf_counter()
-        _, info = self.odd.half_sweep(self.prob, "A", self.rows, alpha, self.eps,
-                                      self.odd.Params(err=1e-6), cells=cells)
-        dt = time.perf_counter() - t
-        per_cell = dt / n_cells
-        return self.n * self.n / (per_cell * self.cells_per_sweep), per_cell, dt, float(self.np.mean(info.iters))
+        its = self._half("A") + self._half("B")
+        self.iters = its
+        return time.perf_counter() - t
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
 
 
-def cpu_baseline(workload, n_cells):
-    s = OracleSample(workload)
-    v, per_cell, dt, iters = s.run(n_cells)
-    sample = (f"oracle (numpy FP64, 1 thread) on {n_cells} random A-cells of one half-sweep at "
-              f"{s.n}², eps=2h², from a feasible synthetic state with zero duals "
-              f"(mean {iters:.0f} Sinkhorn iterations per cell); {per_cell*1e3:.1f} ms per "
-              f"cell, extrapolated to {s.cells_per_sweep} cells per sweep; {dt:.1f} s of CPU work")
-    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+_BLOCK = {}
+
+
+def _oracle_block_init(mu, nu, b, spacing):
+    from oracle import dd as odd
+    _BLOCK["prob"] = odd.GridProblem(mu, nu, b, spacing)
+
+
+def _oracle_block_task(task):
+    # one worker's share of a block half-sweep: the oracle's half_sweep on a
+    # subset of the cells; returns their new rows and α
+    from oracle import dd as odd
+    prob = _BLOCK["prob"]
+    part, rows_sub, alpha, eps, err, cells = task
+    rows = [None] * len(prob.basic)
+    for i, r in rows_sub.items():
+        rows[i] = r
+    alpha = alpha.copy()
+    new_rows, info = odd.half_sweep(prob, part, rows, alpha, eps, odd.Params(err=err), cells=cells)
+    out_rows, out_alpha = {}, []
+    for jn in cells:
+        J = prob.parts[part][jn]
+        for i in J:
+            out_rows[i] = new_rows[i]
+        X = prob.cell_points(J)
+        out_alpha.append((X, alpha[X]))
+    return out_rows, out_alpha, list(info.iters)
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0))
+
+
+def cpu_baseline(workload, steps=2):
+    """The oracle, as it stands, on the block sample (see OracleBlock), on all
+    host cores and on one; px·sweeps/s of the timed block sweeps."""
+    import numpy as np
+    out = {}
+    for workers in (host_cores(), 1):
+        blk = OracleBlock(workload, workers=workers)
+        ts = [blk.sweep() for _ in range(steps)]
+        out[workers] = (blk.px * steps / sum(ts), float(np.mean(blk.iters)), sum(ts), blk)
+        blk.close()
+    cores = host_cores()
+    v, it, dt, blk = out[cores]
+    v1, _, dt1, _ = out[1]
+    sample = (f"FP64 oracle, {steps} timed sweeps (A+B) of a 64×64-pixel block (16×16 basic cells: "
+              f"{len(blk.cells['A'])} A + {len(blk.cells['B'])} B cells) of the {blk.n}² problem at eps=2h², "
+              f"warm: 6 untimed oracle sweeps of the block from a feasible synthetic state first; "
+              f"mean {it:.1f} Sinkhorn iterations per cell solve (plain iteration, Err 1e-6); "
+              f"{dt:.1f} s on {cores} processes; 1 process: {v1:.4g} px·sweeps/s ({dt1:.1f} s)")
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "value_1_core": v1, "mean_iters_per_cell": it}
 
 
 def replica_timing(ms_local, pg, device):
@@ -197,62 +305,116 @@ def run_reference(args):
         return
     from paper_2001_10986_gb300 import synthetic as syn
     w = syn.WORKLOADS[args.workload]
-    s = OracleSample(args.workload)
-    vals = []
-    cells = 16
-    for k in range(args.warmup + args.steps):
-        v, _, _, _ = s.run(cells)
-        if k >= args.warmup:
-            vals.append(v)
-    v = statistics.median(vals)
-    ms = w.n * w.n / v * 1e3
-    cb = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-          "sample": f"each step: the FP64 oracle on {cells} random A-cells of a {w.n}² half-sweep "
-                    f"(feasible synthetic state, zero duals), extrapolated to a whole sweep"}
+    cores = host_cores()
+    blk = OracleBlock(args.workload, workers=cores)
+    for _ in range(args.warmup):
+        blk.sweep()
+    ts = [blk.sweep() for _ in range(args.steps)]
+    its = blk.iters
+    blk.close()
+    import numpy as np
+    ms = 1e3 * sum(ts) / max(len(ts), 1)
+    v = blk.px / (ms * 1e-3)
+    cb = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+          "sample": f"each step: one sweep (A+B) of a 64×64-pixel block of the {w.n}² problem at eps=2h² "
+                    f"(16×16 basic cells, warm after 6 untimed sweeps from a feasible synthetic state), "
+                    f"FP64 oracle on {cores} processes; mean {float(np.mean(its)):.1f} iterations per cell; "
+                    f"ms_per_step is the measured time of one block sweep"}
     out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "n": w.n, "b": w.b, "levels": w.levels,
-                      "eps_final": "2h^2"},
+                      "eps_final": "2h^2", "sample": "64x64-pixel block"},
            "impl": "reference", "cpu_baseline": cb,
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
-def time_to_converged(dd, syn, mu, nu, w, args, stream, max_final_sweeps=400, mlp=None, **opts):
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def load_golden(workload):
+    """The converged FP64 oracle state of a workload, if stored (written by
+    tests/golden/oracle_converged.py): (json dict, npz of sampled rows)."""
+    import numpy as np
+    base = os.path.join(GOLDEN, f"converged_{workload}")
+    if not os.path.exists(base + ".json"):
+        return None
+    with open(base + ".json") as f:
+        return json.load(f), dict(np.load(base + ".npz"))
+
+
+def sampled_rows_rel_l1(rp, col, val, npz):
+    """Relative L1 distance of basic marginals (ν_i) to the stored rows."""
+    import numpy as np
+    ids, grp, gcol, gval = (npz[k] for k in ("row_ids", "row_ptr", "col", "val"))
+    num = den = 0.0
+    for k, i in enumerate(ids):
+        ce, ve = gcol[grp[k]:grp[k + 1]], gval[grp[k]:grp[k + 1]]
+        cg, vg = col[rp[i]:rp[i + 1]], val[rp[i]:rp[i + 1]]
+        u = np.union1d(ce, cg)
+        a_ = np.zeros(u.size)
+        a_[np.searchsorted(u, cg)] = vg
+        e = np.zeros(u.size)
+        e[np.searchsorted(u, ce)] = ve
+        num += np.abs(a_ - e).sum()
+        den += e.sum()
+    return float(num / den)
+
+
+def time_to_converged(dd, syn, mu, nu, w, args, stream, max_final_sweeps=400, mlp=None, gold=None, **opts):
     """Wall time from host images to a converged plan: dd_create, the whole
-    coarse-to-fine schedule, then sweeps at the final ε until one sweep
-    changes the FP64 transport cost by at most 1e-7 relative (the cell solves
-    hold the X-marginal error at ≤ Err·‖μ‖, the Y-marginal is exact). Each
-    check is a dd_cost call, i.e. one device→host read per sweep."""
+    coarse-to-fine schedule (one sweep at the final ε), then sweeps at the
+    final ε until the convergence criterion holds. With a stored converged
+    oracle state (gold): X- and Y-marginal L1 errors ≤ 1e-6 and the
+    transport cost within 1e-6 relative of the oracle's; afterwards (outside
+    the clock) the basic marginals are compared with the oracle's sampled
+    rows. Without one: both errors ≤ 1e-6 and one sweep changing the cost by
+    at most 1e-7 relative. Each check is one dd_cost call (a device→host read
+    per sweep)."""
     import torch
     n, b, L = w.n, w.b, w.levels
     torch.cuda.synchronize()
     t = time.perf_counter()
     h = dd.DD(mu, nu, b, L, syn.paper_schedule(n, L, 1), err_tol=args.err, stream=stream,
-              threads_per_cell=args.tpc, max_cluster_cells=args.clusters, mode=args.mode, **opts)
+              threads_per_cell=args.tpc if w.n == 1024 else 0,
+              max_cluster_cells=args.clusters if w.n == 1024 else -1, mode=args.mode, **opts)
     if mlp is not None:
         h.attach_mlp(mlp)
     h.run_schedule()
-    prev, _, _ = h.cost(with_y=False)
-    k, rel = 1, None
-    while k < max_final_sweeps:
+    k, rel, prev = 1, None, None
+    while True:
+        cost, ex, ey = h.cost()
+        if gold is not None:
+            rel = abs(cost - gold[0]["cost"]) / gold[0]["cost"]
+            done = ex <= 1e-6 and ey <= 1e-6 and rel <= 1e-6
+        else:
+            rel = abs(cost - prev) / abs(cost) if prev is not None else None
+            done = ex <= 1e-6 and ey <= 1e-6 and rel is not None and rel <= 1e-7
+        prev = cost
+        if done or k >= max_final_sweeps:
+            break
         h.sweep(1)
         k += 1
-        cur, _, _ = h.cost(with_y=False)
-        rel = abs(cur - prev) / abs(cur)
-        prev = cur
-        if rel <= 1e-7:
-            break
-    cost, ex, ey = h.cost()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t
     p = h.profile()
+    out = {"seconds": dt, "final_sweeps": k, "converged": bool(done), "cost": cost, "err_x": ex, "err_y": ey,
+           "sinkhorn_iters": p.sinkhorn_iters, "newton_steps": p.newton_steps,
+           "learned_cells": p.learned_cells, "compared_cells": p.compared_cells,
+           "rescued_cells": p.rescued_cells}
+    if gold is not None:
+        rp, col, val = h.basic_marginals()
+        out.update(oracle_cost_rel=rel, plan_rel_l1=sampled_rows_rel_l1(rp, col, val, gold[1]),
+                   plan_rows_compared=int(gold[1]["row_ids"].size),
+                   criterion="err_x, err_y <= 1e-6 and |cost - oracle|/oracle <= 1e-6 (converged FP64 oracle, "
+                             "tests/golden); plan: sampled basic marginals vs the oracle's")
+    else:
+        out.update(last_rel_change=rel,
+                   criterion="err_x, err_y <= 1e-6 and relative cost change over one final-eps sweep <= 1e-7 "
+                             "(no converged oracle state stored for this size)")
     h.close()
-    return {"seconds": dt, "final_sweeps": k, "last_rel_change": rel, "cost": cost, "err_x": ex, "err_y": ey,
-            "sinkhorn_iters": p.sinkhorn_iters, "newton_steps": p.newton_steps,
-            "learned_cells": p.learned_cells, "compared_cells": p.compared_cells,
-            "criterion": "relative cost change over one final-ε sweep <= 1e-7"}
+    return out
 
 
 def run_cuda(args):
@@ -370,8 +532,14 @@ def run_cuda(args):
                "seconds": dt}
 
     ttc = None
+    ttc256 = None
     if not args.no_ttc:
         ttc = {"plain": time_to_converged(dd, syn, mu, nu, w, args, stream)}
+        gold256 = load_golden("gm256_b4_l3")
+        w256 = syn.WORKLOADS["gm256_b4_l3"]
+        m256, n256 = syn.image_pair(w256, 0)
+        if gold256 is not None:
+            ttc256 = {"plain": time_to_converged(dd, syn, m256, n256, w256, args, stream, gold=gold256)}
         if not args.no_learned:
             # learned warm start: network trained on pairs logged from plain
             # runs on 256² images (5 blobs, 3 levels), compared cell by cell
@@ -395,6 +563,9 @@ def run_cuda(args):
                 res["training_pairs"] = int(sum(x.shape[0] for x in fs))
                 res["warm"] = mode
                 ttc["learned" if mode == 1 else "learned_every_eps"] = res
+            if ttc256 is not None:
+                ttc256["learned"] = time_to_converged(dd, syn, m256, n256, w256, args, stream, warm=1, mlp=net,
+                                                      gold=gold256)
             # the evaluation case of the learned warm start: 512², 6 blobs, the
             # whole schedule with the previous duals and with the prediction
             ev = {}
@@ -425,7 +596,7 @@ def run_cuda(args):
         return
     cpu = None
     if not args.no_cpu and world == 1:
-        cpu = cpu_baseline(args.workload, args.cpu_cells)
+        cpu = cpu_baseline(args.workload)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -436,6 +607,7 @@ def run_cuda(args):
                       "autotuned": None if tuned is None else {"threads_per_cell": tuned[0],
                                                                 "max_cluster_cells": tuned[1]}},
            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "time_to_converged": ttc,
+           "time_to_converged_gm256_b4_l3": ttc256,
            "gpu_launches": int(prof.launches), "clocks": clk.summary(),
            "quality": {"cost": cost, "err_x": ex, "err_y": ey, "max_iters_last": st.max_iters,
                        "mean_iters_last": st.mean_iters, "cells_not_converged_last": st.cells_not_converged}}

@@ -44,7 +44,9 @@ typedef enum {
   DD_ERR_CAPACITY = 4,     /* a caller buffer is too small (see *nnz)          */
   DD_ERR_NUMERIC = 5,      /* a cell solve produced a non-finite value         */
   DD_ERR_STATE = 6,        /* context unusable or call out of order            */
-  DD_ERR_NOT_CONVERGED = 7 /* an iterative host solve missed its tolerance     */
+  DD_ERR_NOT_CONVERGED = 7 /* an iterative solve missed its tolerance: a host
+                              solve, or cell solves still at max_iter after the
+                              safeguard (the call completed; state feasible)  */
 } dd_status;
 
 /* Image size and number of multi-scale levels (§6.4, §7.1 "Multi-scale"). */
@@ -109,7 +111,28 @@ typedef struct {
                             the context.                                       */
   uint64_t debug_flags;  /* bit 0: synchronise and check after every kernel;
                             bit 1: time the gather and cell-solve kernels with
-                            CUDA events (see dd_get_profile)                   */
+                            CUDA events (see dd_get_profile).
+                            Fault injection on the host (for tests; no GPU
+                            fault is involved):
+                            bit 2: graph-replayed sweeps (mode 1) get an
+                            output buffer of half the current entries, so the
+                            sweep overflows and is run again with per-kernel
+                            launches (dd_profile.graph_reruns counts it);
+                            bit 3: the main solve of every cell stops after
+                            one iteration, so the safeguard re-solves it;
+                            bit 4: the first growth of the half-sweep
+                            workspace fails as a failed cudaMalloc would
+                            (DD_ERR_OOM, state untouched; one shot).
+                            Bits 0 and 1 turn the graph replay of mode 1
+                            off.                                               */
+  int32_t safeguard;     /* 1: a cell whose solve stops at max_iter is solved
+                            again, warm-started from where it stopped, first
+                            at 4·ε and then at ε (the local safeguard of §7.3,
+                            "temporarily increasing ε"); cells still at
+                            max_iter afterwards make the call return
+                            DD_ERR_NOT_CONVERGED after completing it. 0: off
+                            (the half-sweep keeps the cut-off solves). Default
+                            1.                                                 */
 } dd_options;
 
 /* Counters of the work done by a context since creation or the last
@@ -135,6 +158,9 @@ typedef struct {
                                 duals (warm ≠ 0)                                 */
   int64_t compared_cells;    /* cell solves whose prediction was compared with
                                 the previous duals                               */
+  int64_t rescued_cells;     /* cells re-solved by the safeguard                 */
+  int64_t graph_reruns;      /* graph-replayed sweeps whose output did not fit
+                                and that ran again with per-kernel launches      */
 } dd_profile;
 
 /* Statistics of the last sweep run by dd_sweep / dd_run_schedule. */
@@ -145,8 +171,10 @@ typedef struct {
   int64_t nnz;            /* entries stored in (ν_i) after it                 */
   int32_t max_iters;      /* largest Sinkhorn iteration count over its cells  */
   double mean_iters;      /* mean Sinkhorn iteration count over its cells     */
-  int32_t cells_not_converged; /* cells that stopped at max_iter               */
+  int32_t cells_not_converged; /* cells still at max_iter after the safeguard   */
   int64_t sweeps_done;    /* total sweeps since dd_create                     */
+  int32_t cells_rescued;  /* cells of the last half-sweep that the safeguard
+                             solved again                                     */
 } dd_sweep_stats;
 
 /* Fill *opt with the defaults listed above. */
@@ -183,6 +211,12 @@ dd_status dd_set_state(dd_ctx* ctx, const int64_t* row_ptr, const int32_t* col,
  * from u_{C,J} (stop rule of §6.2), extract ν_i = P_Y(π_cell|X_i×Y),
  * BalanceMeasures, Truncate. Does not advance the schedule. */
 dd_status dd_half_sweep(dd_ctx* ctx, int32_t partition, double eps);
+
+/* Move the state one level finer (§6.4) without sweeping: the basic
+ * marginals by eq. FineBasicMarginals, the duals as dd_options.dual_refine
+ * says. dd_sweep then continues the schedule; its steps on coarser levels run
+ * on the current level. DD_ERR_STATE at the finest level. */
+dd_status dd_refine(dd_ctx* ctx);
 
 /* Run n_sweeps sweeps (A then B) following the schedule, refining when the
  * schedule enters a new level. After the last step of the schedule the
@@ -335,14 +369,15 @@ dd_status dd_reset_profile(dd_ctx* ctx);
 
 /* Solve one composite cell without allocating any memory (no counterpart in
  * the paper: this is a library facility). Some callers cannot call
- * cudaMalloc when they need a solve: code that is capturing a stream into a
- * CUDA graph (an allocation is not a capturable operation and synchronises
- * the device), latency-critical loops that must not wait on the allocator,
- * and hosts whose device memory belongs to another runtime. This entry point
- * runs the same cell solve as a half-sweep (Sinkhorn with the §6.2 stop rule,
- * extraction, BalanceMeasures, Truncate) with all scratch memory in one
- * fixed-size array that the library holds on every device that loads it,
- * from load until process exit (about 1.9 MB).
+ * cudaMalloc when they need a solve: hosts whose device memory belongs to
+ * another runtime or memory pool that forbids allocations behind its back
+ * (for example a plug-in that only receives pre-allocated buffers), and
+ * latency-critical loops that must not stall on the allocator (cudaMalloc can
+ * synchronise the device). This entry point runs the same cell solve as a
+ * half-sweep (Sinkhorn with the §6.2 stop rule, extraction, BalanceMeasures,
+ * Truncate) with all scratch memory in one fixed-size array that the library
+ * holds on every device that loads it, from load until process exit (about
+ * 1.9 MB).
  *
  * The cell is a 2b×2b block of 4 basic cells of b×b pixels with pixel
  * spacing `spacing` ([0,1]² units). All array arguments are DEVICE pointers
@@ -352,7 +387,9 @@ dd_status dd_reset_profile(dd_ctx* ctx);
  *             cell's top-left pixel, distinct, sorted row-major, each in
  *             (−2048, 2048);
  *   nu        n_y FP64 masses ν_cell(y) > 0 (all masses are fractions of a
- *             total mass 1, as in dd_create);
+ *             total mass 1, as in dd_create). BalanceMeasures needs the cell's
+ *             two masses to agree: |Σ nu − Σ mu| ≤ 1e-9·Σ mu + 4·n_y·trunc
+ *             (the second term allows for mass that Truncate removed);
  *   alpha     (2b)² FP64, in: warm-start α = ε·log u (any constant offset),
  *             out: the cell's new α (up to a constant);
  *   nu_basic  4·n_y FP64 output, row k = basic cell k (row-major in the 2×2
@@ -364,13 +401,19 @@ dd_status dd_reset_profile(dd_ctx* ctx);
  *
  * Limits: b ∈ {2,4,8}; 1 ≤ n_y ≤ 16384; larger inputs are rejected with
  * DD_ERR_ARG before any work is queued, and dd_last_error(NULL) says why.
- * The first call on a device resolves the address of the scratch array with
- * cudaGetSymbolAddress and raises the cell-solve kernel's shared-memory limit
- * with cudaFuncSetAttribute; make that first call before any stream capture
- * begins. Every call reuses the same array and leaves its own data in it;
- * calls that overlap on the GPU (other streams or host threads) race on it
- * and must be serialised by the caller. Errors: DD_ERR_ARG (sizes, NULL,
- * unsorted or out-of-range support), DD_ERR_NUMERIC, DD_ERR_CUDA. */
+ * The first call on a device does a one-time set-up with that device
+ * current: it resolves the device address of the scratch array
+ * (cudaGetSymbolAddress) and raises the cell-solve kernel's shared-memory
+ * limit (cudaFuncSetAttribute); make that first call before any stream
+ * capture begins. Every call reuses the same array and leaves its own data in
+ * it; calls that overlap on the GPU (other streams or host threads) race on
+ * it and must be serialised by the caller.
+ * Errors: DD_ERR_ARG (sizes, NULL, unsorted or out-of-range support, masses
+ * of μ and ν that disagree; for the last two the solve is skipped and alpha
+ * and nu_basic are left as they were), DD_ERR_NOT_CONVERGED (the solve
+ * stopped at max_iter before its X-error reached ‖μ_J‖·err_tol; alpha and
+ * nu_basic hold its result, which is feasible: Σ_k nu_basic[k] = nu),
+ * DD_ERR_NUMERIC, DD_ERR_CUDA. */
 dd_status dd_solve_cell_noalloc(const double* mu, int32_t b, double spacing, int32_t n_y,
                                 const int32_t* y_row, const int32_t* y_col, const double* nu,
                                 double eps, double err_tol, int32_t max_iter, double trunc,
@@ -430,6 +473,24 @@ dd_status dd_attach_mlp(dd_ctx* ctx, dd_mlp* m);
  * 8×8 pixels (the others are not written). cap: rows the buffers hold. */
 dd_status dd_cell_training_pairs(dd_ctx* ctx, float* features, float* targets, int32_t* ok, int64_t cap,
                                  int64_t* n_cells);
+
+/* Checkpoint and resume (no counterpart in the paper). dd_save writes the
+ * context's state to the file `path`: the images (finest level, fixed point),
+ * the schedule and its position, the options (without stream), the basic
+ * marginals (ν_i) and the duals of both partitions at the current level, and
+ * the iteration counts of the last solves (which order the next launch). An
+ * attached network is not saved. The file is in host byte order.
+ * dd_load creates a new context (*out) on the current device from such a
+ * file; opt = NULL takes the saved options (stream NULL), otherwise *opt.
+ * Sweeps after dd_load give the state that the saved context would have
+ * reached with the same sweeps, bit for bit.
+ * Errors: DD_ERR_ARG for a path that cannot be opened, a failed write, or a
+ * file that is not a checkpoint of this library or is truncated or
+ * inconsistent (checked before any device memory is allocated); DD_ERR_CUDA /
+ * DD_ERR_OOM from the device; dd_last_error(NULL) describes a dd_load
+ * failure. */
+dd_status dd_save(dd_ctx* ctx, const char* path);
+dd_status dd_load(const char* path, const dd_options* opt, dd_ctx** out);
 
 /* Free the context and all device memory it owns. NULL is allowed. */
 void dd_destroy(dd_ctx* ctx);

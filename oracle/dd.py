@@ -607,6 +607,29 @@ def relative_pd_gap(prob, P, alpha_hat, beta_hat, eps):
     return gap / primal, gap, primal
 
 
+def fill_massless_affine(prob, alpha):
+    """A copy of α in which every pixel without mass takes the value of the
+    least-squares affine fit a + s_r·i + s_c·j of α over the pixels with mass
+    of its A cell (i, j: pixel row and column). A pixel without mass has no
+    dual (the problem lives on the support of μ, §2); §6.4 interpolates the
+    glued dual between pixel centres, and this gives those pixels values that
+    continue the cell's dual instead of an arbitrary constant. Each basic
+    cell has positive mass (Def. 3.1), so an A cell has pixels with mass in
+    all four of its basic cells, which no straight line meets, and the fit is
+    unique."""
+    out = np.asarray(alpha, dtype=np.float64).copy()
+    for J in prob.parts["A"]:
+        X = prob.cell_points(J)
+        live = prob.mu[X] > 0
+        if live.all():
+            continue
+        i, j = np.divmod(X, prob.n)
+        D = np.stack([np.ones(X.size), i, j], axis=1).astype(np.float64)
+        coef = np.linalg.lstsq(D[live], out[X[live]], rcond=None)[0]
+        out[X[~live]] = D[~live] @ coef
+    return out
+
+
 def refine_duals_glued(coarse, fine, alpha_hat_c):
     """Dual initialisation at the next level as §6.4 describes it: the glued
     coarse X-dual, interpolated linearly in log space (on α̂ = ε·log û)
@@ -678,7 +701,7 @@ def run_schedule(mu_img, nu_img, b, levels, schedule, params, *, on_half_sweep=N
             rows = refine_basic_marginals(prob, fine, rows)
             if dual_refinement in ("glued", "hybrid") and eps is not None:
                 a_hat, _ = glue_duals(prob, alpha["A"], alpha["B"], eps)
-                a0 = refine_duals_glued(prob, fine, a_hat)
+                a0 = refine_duals_glued(prob, fine, fill_massless_affine(prob, a_hat))
                 a0[fine.mu == 0] = 0.0
                 a_cell = refine_duals(prob, fine, alpha[last], last) if dual_refinement == "hybrid" else a0
                 alpha = {"A": a_cell.copy(), "B": a0.copy()}

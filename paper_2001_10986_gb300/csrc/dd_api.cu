@@ -130,6 +130,12 @@ struct dd_ctx {
   cudaEvent_t ev_c0 = nullptr, ev_c1 = nullptr;   // cluster kernel timing
   int* nbig = nullptr;
   int* work_next = nullptr;           // persistent per-CTA solves: next cell position
+  // safeguard (§7.3): cells whose solve stopped at max_iter, re-solved at a
+  // larger ε and then at ε
+  int32_t* retry = nullptr;
+  int* retry_count = nullptr;
+  int64_t unconverged_in_call = 0;    // cells left at max_iter by the current API call
+  bool fail_next_ws_alloc = false;    // fault injection (debug_flags bit 4), one shot
   // graph-captured sweeps (options.mode = 1): the instantiated graph of one
   // A+B sweep and what it was captured with
   cudaGraphExec_t graph_exec = nullptr;
@@ -257,6 +263,7 @@ void alloc_level_buffers(dd_ctx* c, int l, float*& alpha0, float*& alpha1, int2*
   dev_alloc(c->cell_newton, ncell);
   dev_alloc(c->cell_status, ncell);
   dev_alloc(c->order, ncell);
+  dev_alloc(c->retry, ncell);
   if (std::getenv("DD_TRACE_TIMES")) dev_alloc(c->cell_times, 2 * ncell);
   c->serial_solve = std::getenv("DD_SERIAL_SOLVE") != nullptr;
   for (int k = 0; k < 2; ++k) {
@@ -288,8 +295,17 @@ void ensure_state(dd_ctx* c);
 void drop_graph(dd_ctx* c);
 
 void ensure_sweep_capacity(dd_ctx* c, int64_t nnz_in) {
+  if (nnz_in > c->ws_cap || 4 * c->ws_cap > c->tmp_cap) {
+    if (c->fail_next_ws_alloc) {
+      // fault injection (debug_flags bit 4): this growth fails as a failed
+      // cudaMalloc would, before any buffer or the state is touched
+      c->fail_next_ws_alloc = false;
+      throw DdError{DD_ERR_OOM, "cudaMalloc of the half-sweep workspace failed (injected)"};
+    }
+  }
   if (nnz_in > c->ws_cap) {
     int64_t need = nnz_in + nnz_in / 2 + 1024;
+    c->ws_cap = 0;   // a failure below leaves every buffer to be allocated again
     dev_alloc(c->ws_ytmp, need);
     dev_alloc(c->ws_vtmp, need);
     dev_alloc(c->ws_eta, need);
@@ -300,6 +316,7 @@ void ensure_sweep_capacity(dd_ctx* c, int64_t nnz_in) {
   }
   if (4 * c->ws_cap > c->tmp_cap) {
     const int64_t need = 4 * c->ws_cap;
+    c->tmp_cap = 0;
     dev_alloc(c->tmp_col, need);
     dev_alloc(c->tmp_val, need);
     c->tmp_cap = need;
@@ -313,7 +330,9 @@ SweepArgs sweep_args(dd_ctx* c, int part, double eps) {
   a.ncells = num_cells(part, a.L.nb);
   a.eps = (float)eps;
   a.err_tol = (float)c->opt.err_tol;
-  a.max_iter = c->opt.max_iter;
+  // fault injection (debug_flags bit 3): the main solve of every cell stops
+  // after one iteration, so that the safeguard has to re-solve it
+  a.max_iter = (c->opt.debug_flags & 8) ? 1 : c->opt.max_iter;
   const double tq = c->opt.trunc * kFixOne;
   a.trunc_q = tq <= 0 ? 0ull : (tq >= 1.8e19 ? ~0ull : (uint64_t)tq);
   a.rp = c->rp[c->cur];
@@ -392,6 +411,34 @@ void launch_cta_solves(dd_ctx* c, SweepArgs a) {
   }
 }
 
+// The safeguard of §7.3 for cells whose solve stopped at max_iter: the
+// failed cells are collected on the device and re-solved, warm-started from
+// the duals their solve ended with, first at a temporarily larger ε
+// (kSafeguardFactor·ε, where the cell problem is smoother and Sinkhorn
+// contracts faster) and then at ε from the result. Each re-solve is a full
+// cell solve with extraction, BalanceMeasures and Truncate, so the cell's
+// basic marginals end up those of the solve at ε. Two persistent launches
+// that exit at once when no cell failed; no host synchronisation.
+constexpr double kSafeguardFactor = 4.0;
+
+void enqueue_safeguard(dd_ctx* c, const SweepArgs& a, double eps) {
+  if (!c->opt.safeguard) return;
+  DD_CUDA(launch_collect_failed(a, c->retry, c->retry_count, c->stream));
+  SweepArgs r = a;
+  r.order = c->retry;
+  r.ncells_dev = c->retry_count;
+  r.nbig = nullptr;
+  r.cell_learned = nullptr;
+  r.max_iter = c->opt.max_iter;
+  for (const double f : {kSafeguardFactor, 1.0}) {
+    r.eps = (float)(eps * f);
+    DD_CUDA(cudaMemsetAsync(c->work_next, 0, sizeof(int), c->stream));
+    r.work_next = c->work_next;
+    DD_CUDA(launch_sinkhorn(r, threads_per_cell(c), c->stream, true));
+  }
+  c->prof.launches += 3;
+}
+
 int threads_per_cell(dd_ctx* c) {
   const int t = c->opt.threads_per_cell;
   return (t == 32 || t == 64 || t == 128 || t == 256) ? t : 128;
@@ -455,6 +502,9 @@ void half_sweep(dd_ctx* c, int part, double eps) {
     DD_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   }
   check_debug(c, "sinkhorn");
+  enqueue_safeguard(c, a, eps);
+  a.rescued_dev = c->opt.safeguard ? c->retry_count : nullptr;
+  check_debug(c, "safeguard");
   if (timing) DD_CUDA(cudaEventRecord(c->ev[2], c->stream));
   DD_CUDA(launch_row_scan(c->row_cnt, c->rp[other], c->tile, nrows, c->stream, c->err_flag));
   DD_CUDA(launch_reduce_cells(a, c->totals, c->stream));
@@ -494,6 +544,8 @@ void half_sweep(dd_ctx* c, int part, double eps) {
     c->prof.compared_cells += c->last_tot.compared;
   }
   c->prof.cells += a.ncells;
+  c->prof.rescued_cells += c->last_tot.rescued;
+  c->unconverged_in_call += c->last_tot.not_converged;
   if (c->cell_times && std::getenv("DD_TRACE_TIMES_FILE")) {
     const int nc = a.ncells;
     std::vector<unsigned long long> t(2 * nc);
@@ -556,31 +608,85 @@ std::vector<double> host_duals(dd_ctx* c, int part) {
   return out;
 }
 
+// Least-squares affine fit a0 + sr·i + sc·j (i, j: row and column inside the
+// H×W block at (r0, c0) of an n-wide level) of al over the block's pixels
+// with mass. A pixel without mass has no dual (§2: the problem lives on the
+// support of μ), so its value must not steer the fit. The normal equations
+// get a ridge of 1e-12 of their trace on the slopes, so that a block whose
+// pixels with mass lie on one line (possible for a B corner cell) gets a
+// slope along that line and none across it.
+void affine_fit(const double* al, const uint64_t* mu_q, int n, int r0, int c0, int H, int W, double& a0,
+                double& sr, double& sc) {
+  const double ci = 0.5 * (H - 1), cj = 0.5 * (W - 1);   // centred coordinates
+  double s1 = 0, si = 0, sj = 0, sii = 0, sij = 0, sjj = 0, sa = 0, sia = 0, sja = 0;
+  for (int i = 0; i < H; ++i)
+    for (int j = 0; j < W; ++j) {
+      const size_t p = (size_t)(r0 + i) * n + c0 + j;
+      if (mu_q[p] == 0) continue;
+      const double x = i - ci, y = j - cj, v = al[p];
+      s1 += 1; si += x; sj += y; sii += x * x; sij += x * y; sjj += y * y;
+      sa += v; sia += x * v; sja += y * v;
+    }
+  a0 = 0.0;
+  sr = sc = 0.0;
+  if (s1 == 0) return;
+  const double rg = 1e-12 * (s1 + sii + sjj);
+  // 3×3 system [[s1 si sj][si sii+rg sij][sj sij sjj+rg]]·(m, sr, sc) = (sa, sia, sja), Cramer
+  const double A[3][3] = {{s1, si, sj}, {si, sii + rg, sij}, {sj, sij, sjj + rg}};
+  const double bvec[3] = {sa, sia, sja};
+  auto det3 = [](const double M[3][3]) {
+    return M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+           M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+  };
+  const double d = det3(A);
+  double sol[3];
+  for (int k = 0; k < 3; ++k) {
+    double M[3][3];
+    for (int r = 0; r < 3; ++r)
+      for (int q = 0; q < 3; ++q) M[r][q] = q == k ? bvec[r] : A[r][q];
+    sol[k] = d != 0.0 ? det3(M) / d : (k == 0 ? sa / s1 : 0.0);
+  }
+  sr = sol[1];
+  sc = sol[2];
+  a0 = sol[0] - sr * ci - sc * cj;   // value of the fit at (0, 0)
+}
+
 // α (absolute frame, FP64, one value per pixel of level `lev`) into the cell
-// frames of partition `part` (the reduction of dd_set_state: per cell an
-// anchor from the mean slope, the cell's first value removed), written to the
-// device arrays alpha and anchor
+// frames of partition `part`: per cell the anchor from the slope of the
+// affine fit over the pixels with mass and the fit's value at the corner
+// removed (α is defined up to a constant per cell), written to the device
+// arrays alpha and anchor; 0 on pixels without mass
+void cell_frames(const LevelHost& h, int b, int part, const double* al, std::vector<float>& at,
+                 std::vector<int2>& an) {
+  const int nc = num_cells(part, h.nb);
+  const double d2 = h.spacing * h.spacing;
+  at.assign((size_t)h.n * h.n, 0.f);
+  an.resize((size_t)nc);
+  for (int J = 0; J < nc; ++J) {
+    const CellGeom g = cell_geom(part, J, h.nb, b);
+    int Dr = 0, Dc = 0;
+    if (al) {
+      double a00, sr, sc;
+      affine_fit(al, h.mu_q.data(), h.n, g.r0, g.c0, g.H, g.W, a00, sr, sc);
+      Dr = (int)std::lround(sr / (2 * d2));
+      Dc = (int)std::lround(sc / (2 * d2));
+      for (int i = 0; i < g.H; ++i)
+        for (int j = 0; j < g.W; ++j) {
+          const size_t p = (size_t)(g.r0 + i) * h.n + g.c0 + j;
+          at[p] = h.mu_q[p] ? (float)(al[p] - a00 - 2 * d2 * ((double)Dr * i + (double)Dc * j)) : 0.f;
+        }
+    }
+    an[J] = make_int2(g.r0 - Dr, g.c0 - Dc);
+  }
+}
+
 void upload_duals(dd_ctx* c, int lev, int part, const double* al, float* alpha, int2* anchor) {
   const LevelHost& h = c->lh[lev];
   const int n2 = h.n * h.n;
   const int nc = num_cells(part, h.nb);
-  const double d2 = h.spacing * h.spacing;
-  std::vector<float> at((size_t)n2, 0.f);
-  std::vector<int2> an((size_t)nc);
-  for (int J = 0; J < nc; ++J) {
-    const CellGeom g = cell_geom(part, J, h.nb, c->b);
-    const double a00 = al[(size_t)g.r0 * h.n + g.c0];
-    const double sr = (al[(size_t)(g.r0 + g.H - 1) * h.n + g.c0] - a00) / (g.H - 1);
-    const double sc = (al[(size_t)g.r0 * h.n + g.c0 + g.W - 1] - a00) / (g.W - 1);
-    const int Dr = (int)std::lround(sr / (2 * d2));
-    const int Dc = (int)std::lround(sc / (2 * d2));
-    for (int i = 0; i < g.H; ++i)
-      for (int j = 0; j < g.W; ++j) {
-        const size_t p = (size_t)(g.r0 + i) * h.n + g.c0 + j;
-        at[p] = (float)(al[p] - a00 - 2 * d2 * ((double)Dr * i + (double)Dc * j));
-      }
-    an[J] = make_int2(g.r0 - Dr, g.c0 - Dc);
-  }
+  std::vector<float> at;
+  std::vector<int2> an;
+  cell_frames(h, c->b, part, al, at, an);
   DD_CUDA(cudaMemcpyAsync(alpha, at.data(), 4 * (size_t)n2, cudaMemcpyHostToDevice, c->stream));
   DD_CUDA(cudaMemcpyAsync(anchor, an.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, c->stream));
   DD_CUDA(cudaStreamSynchronize(c->stream));
@@ -601,6 +707,22 @@ void refine(dd_ctx* c) {
     const dd_status st =
         dd_glue_duals_host(h0.n, c->b, mu.data(), aA.data(), aB.data(), c->eps_cur, glued.data(), nullptr);
     if (st != DD_OK) throw DdError{st, "dual gluing at the refinement failed"};
+    // pixels without mass have no glued dual (0 from the gluing); before the
+    // interpolation they take the affine fit of their A cell's dual, so that
+    // neighbouring fine pixels with mass are not pulled towards 0. Every
+    // basic cell has mass (Def. 3.1): an A cell's pixels with mass never lie
+    // on one line and the fit is unique.
+    const int na = h0.nb / 2;
+    for (int J = 0; J < na * na; ++J) {
+      const CellGeom g = cell_geom(0, J, h0.nb, c->b);
+      double a00, sr, sc;
+      affine_fit(glued.data(), h0.mu_q.data(), h0.n, g.r0, g.c0, g.H, g.W, a00, sr, sc);
+      for (int i = 0; i < g.H; ++i)
+        for (int j = 0; j < g.W; ++j) {
+          const size_t p = (size_t)(g.r0 + i) * h0.n + g.c0 + j;
+          if (h0.mu_q[p] == 0) glued[p] = a00 + sr * i + sc * j;
+        }
+    }
   }
   const LevelHost& hc = c->lh[lc];
   const LevelHost& hf = c->lh[lf];
@@ -676,8 +798,6 @@ void refine(dd_ctx* c) {
     std::vector<double> af((size_t)hf.n * hf.n);
     const dd_status st = dd_interpolate_dual_host(hc.n, glued.data(), af.data());
     if (st != DD_OK) throw DdError{st, "dual interpolation at the refinement failed"};
-    for (size_t p = 0; p < af.size(); ++p)
-      if (hf.mu_q[p] == 0) af[p] = 0.0;
     upload_duals(c, lf, 1, af.data(), a1, n1);
   }
   dev_free(rp_c);
@@ -745,32 +865,16 @@ void ensure_state(dd_ctx* c) {
   c->need_init = false;
 }
 
-void build_levels(dd_ctx* c, const double* mu, const double* nu) {
+// the level pyramid from the finest level's fixed-point images: coarse
+// levels are push-forwards (2×2 sums, §6.4), plus per level μ as float,
+// log2 μ and the basic-cell masses
+void build_pyramid(dd_ctx* c, std::vector<uint64_t> mu_q, std::vector<uint64_t> nu_q) {
   const int n = c->n, L = c->levels;
-  const size_t n2 = (size_t)n * n;
-  double smu = 0, snu = 0;
-  for (size_t i = 0; i < n2; ++i) {
-    smu += mu[i];
-    snu += nu[i];
-  }
-  auto quantise = [&](const double* a, double s) {
-    std::vector<uint64_t> q(n2);
-    long double tot = 0;
-    size_t imax = 0;
-    for (size_t i = 0; i < n2; ++i) {
-      q[i] = (uint64_t)std::llround(a[i] / s * kFixOne);
-      tot += (long double)q[i];
-      if (a[i] > a[imax]) imax = i;
-    }
-    const long double diff = (long double)kFixOne - tot;
-    q[imax] = (uint64_t)((long double)q[imax] + diff);
-    return q;
-  };
   c->lh.assign(L, LevelHost{});
   LevelHost& fin = c->lh[L - 1];
   fin.n = n;
-  fin.mu_q = quantise(mu, smu);
-  fin.nu_q = quantise(nu, snu);
+  fin.mu_q = std::move(mu_q);
+  fin.nu_q = std::move(nu_q);
   for (int l = L - 2; l >= 0; --l) {
     const LevelHost& f = c->lh[l + 1];
     LevelHost& h = c->lh[l];
@@ -803,6 +907,30 @@ void build_levels(dd_ctx* c, const double* mu, const double* nu) {
   }
 }
 
+void build_levels(dd_ctx* c, const double* mu, const double* nu) {
+  const int n = c->n;
+  const size_t n2 = (size_t)n * n;
+  double smu = 0, snu = 0;
+  for (size_t i = 0; i < n2; ++i) {
+    smu += mu[i];
+    snu += nu[i];
+  }
+  auto quantise = [&](const double* a, double s) {
+    std::vector<uint64_t> q(n2);
+    long double tot = 0;
+    size_t imax = 0;
+    for (size_t i = 0; i < n2; ++i) {
+      q[i] = (uint64_t)std::llround(a[i] / s * kFixOne);
+      tot += (long double)q[i];
+      if (a[i] > a[imax]) imax = i;
+    }
+    const long double diff = (long double)kFixOne - tot;
+    q[imax] = (uint64_t)((long double)q[imax] + diff);
+    return q;
+  };
+  build_pyramid(c, quantise(mu, smu), quantise(nu, snu));
+}
+
 void release(dd_ctx* c) {
   for (int k = 0; k < 2; ++k) {
     dev_free(c->rp[k]);
@@ -816,7 +944,7 @@ void release(dd_ctx* c) {
                   c->row_cnt, c->row_src, c->tile, c->cell_off, c->cell_ny, c->anchor_new, c->cell_cost,
                   c->cell_errx, c->cell_iters, c->cell_newton, c->cell_status, c->ydense, c->ws_counter, c->err_flag,
                   c->totals, c->yerr, c->order, c->iters_hist[0], c->iters_hist[1], c->trace_buf, c->nbig, c->cell_times,
-                  c->feat, c->pred, c->fanc, c->fok, c->cell_learned};
+                  c->feat, c->pred, c->fanc, c->fok, c->cell_learned, c->retry, c->retry_count};
   for (void* p : bufs) dev_free(p);
   drop_graph(c);
   if (c->h_tot_g) cudaFreeHost(c->h_tot_g);
@@ -859,6 +987,21 @@ dd_status guarded(dd_ctx* c, F&& f) {
     c->err = "unexpected internal error";
     return DD_ERR_STATE;
   }
+}
+
+// guarded() for the calls that run half-sweeps: when a cell is still at
+// max_iter after the safeguard, the call finishes its sweeps (the state stays
+// feasible) and then returns DD_ERR_NOT_CONVERGED
+template <typename F>
+dd_status guarded_sweeps(dd_ctx* c, F&& f) {
+  if (c) c->unconverged_in_call = 0;
+  const dd_status st = guarded(c, std::forward<F>(f));
+  if (st == DD_OK && c->unconverged_in_call > 0) {
+    c->err = std::to_string(c->unconverged_in_call) +
+             " cell solves stopped at max_iter, also after the safeguard; the sweeps were completed";
+    return DD_ERR_NOT_CONVERGED;
+  }
+  return st;
 }
 
 // ---- graph-captured sweeps (options.mode = 1) ----
@@ -913,6 +1056,8 @@ void enqueue_half_sweep(dd_ctx* c, int part, double eps, int in, int out, int sl
   DD_CUDA(cudaEventRecord(c->ev_join, c->stream2));
   launch_cta_solves(c, a);
   DD_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  enqueue_safeguard(c, a, eps);
+  a.rescued_dev = c->opt.safeguard ? c->retry_count : nullptr;
   DD_CUDA(launch_row_scan(c->row_cnt, c->rp[out], c->tile, nrows, c->stream, c->err_flag));
   DD_CUDA(launch_reduce_cells(a, c->totals, c->stream));
   DD_CUDA(launch_compact(c->row_cnt, c->row_src, c->tile, c->rp[out], c->tmp_col, c->tmp_val, c->col[out],
@@ -932,6 +1077,8 @@ void account_half_sweep(dd_ctx* c, const SweepTotals& t, int ncells) {
   c->prof.newton_steps += t.newton_steps;
   c->prof.hessian_fma += t.hessian_fma;
   c->prof.cells += ncells;
+  c->prof.rescued_cells += t.rescued;
+  c->unconverged_in_call += t.not_converged;
 }
 
 // One A+B sweep replayed from a CUDA graph. Both state buffers get a fixed
@@ -944,9 +1091,26 @@ void graph_sweep(dd_ctx* c, double eps) {
   const int nrows = h.nb * h.nb;
   const int64_t want = std::max<int64_t>(2 * c->nnz, 1 << 16);
   const int cur = c->cur, other = 1 - c->cur;
-  if (c->cap[cur] < want || c->cap[other] < want) drop_graph(c);
-  state_grow_keep(c, cur, want, c->nnz);
-  state_grow_keep(c, other, want, 0);
+  if (c->opt.debug_flags & 4) {
+    // fault injection (debug_flags bit 2): the output buffer of the A
+    // half-sweep gets half the current entries, so the captured sweep
+    // overflows and is run again with per-kernel launches
+    const int64_t small = std::max<int64_t>(c->nnz / 2, 1);
+    drop_graph(c);
+    state_grow_keep(c, cur, c->nnz, c->nnz);
+    if (c->cap[other] > small) {
+      dev_free(c->col[other]);
+      dev_free(c->val[other]);
+      c->col[other] = nullptr;
+      c->val[other] = nullptr;
+      c->cap[other] = 0;
+    }
+    state_grow_keep(c, other, small, 0);
+  } else {
+    if (c->cap[cur] < want || c->cap[other] < want) drop_graph(c);
+    state_grow_keep(c, cur, want, c->nnz);
+    state_grow_keep(c, other, want, 0);
+  }
   ensure_sweep_capacity(c, std::max(c->cap[0], c->cap[1]));
   double e = eps;
   uint64_t eb = 0;
@@ -989,6 +1153,7 @@ void graph_sweep(dd_ctx* c, double eps) {
   if (err & 2) throw DdError{DD_ERR_NUMERIC, "a cell solve produced a non-finite value"};
   if (err & (4 | 8)) {
     drop_graph(c);
+    c->prof.graph_reruns += 1;
     if (c->h_nnz_g[0] > c->cap[other]) {
       // A did not fit: its input is untouched
       half_sweep(c, 0, eps);
@@ -1028,7 +1193,7 @@ void one_sweep(dd_ctx* c) {
   // learned warm start or debugging step has to run in between
   const bool same = !c->need_init && c->last_part == 1 && c->part_lev[0] == c->lev && c->part_lev[1] == c->lev &&
                     c->part_eps[0] == s.eps && c->part_eps[1] == s.eps;
-  if (c->opt.mode == 1 && same && c->opt.debug_flags == 0 && c->opt.warm != 3 && !c->trace_buf &&
+  if (c->opt.mode == 1 && same && (c->opt.debug_flags & 3) == 0 && c->opt.warm != 3 && !c->trace_buf &&
       !c->cell_times) {
     graph_sweep(c, s.eps);
   } else {
@@ -1055,8 +1220,53 @@ void fill_stats(dd_ctx* c, dd_sweep_stats* st) {
   st->mean_iters = nc > 0 ? (double)c->last_tot.iters_sum / nc : 0.0;
   st->cells_not_converged = c->last_tot.not_converged;
   st->sweeps_done = c->sweeps_done;
+  st->cells_rescued = c->last_tot.rescued;
 }
 
+}  // namespace
+
+namespace {
+// streams, events, and the small device and pinned buffers of a new context
+void init_device(dd_ctx* c) {
+  if (c->opt.stream) {
+    c->stream = (cudaStream_t)c->opt.stream;
+  } else {
+    DD_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    c->own_stream = true;
+  }
+  dev_alloc(c->ws_counter, 1);
+  dev_alloc(c->err_flag, 1);
+  dev_alloc(c->totals, 1);
+  dev_alloc(c->yerr, 1);
+  DD_CUDA(cudaMallocHost((void**)&c->h_tot, sizeof(SweepTotals)));
+  DD_CUDA(cudaMallocHost((void**)&c->h_nnz, sizeof(int64_t)));
+  DD_CUDA(cudaMallocHost((void**)&c->h_err, sizeof(int)));
+  DD_CUDA(cudaMallocHost((void**)&c->h_yerr, sizeof(double)));
+  for (int k = 0; k < 3; ++k) DD_CUDA(cudaEventCreate(&c->ev[k]));
+  // cluster solves take the highest stream priority: when per-CTA solves
+  // retire, their SMs go to the waiting clusters first
+  int prio_least = 0, prio_greatest = 0;
+  DD_CUDA(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+  DD_CUDA(cudaStreamCreateWithPriority(&c->stream2, cudaStreamNonBlocking, prio_greatest));
+  DD_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  DD_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  DD_CUDA(cudaEventCreate(&c->ev_c0));
+  DD_CUDA(cudaEventCreate(&c->ev_c1));
+  dev_alloc(c->nbig, 1);
+  dev_alloc(c->work_next, 1);
+  dev_alloc(c->retry_count, 1);
+  DD_CUDA(cudaMemsetAsync(c->retry_count, 0, sizeof(int), c->stream));
+  c->fail_next_ws_alloc = (c->opt.debug_flags & 16) != 0;
+  DD_CUDA(cudaMallocHost((void**)&c->h_tot_g, 2 * sizeof(SweepTotals)));
+  DD_CUDA(cudaMallocHost((void**)&c->h_nnz_g, 2 * sizeof(int64_t)));
+  DD_CUDA(cudaMallocHost((void**)&c->h_err_g, sizeof(int)));
+  if (const char* tr = std::getenv("DD_TRACE_CELL")) {
+    if (std::sscanf(tr, "%d,%d", &c->trace_part, &c->trace_cell) == 2) {
+      dev_alloc(c->trace_buf, 1024);
+      DD_CUDA(cudaMemset(c->trace_buf, 0, 4096));
+    }
+  }
+}
 }  // namespace
 
 void dd_set_noalloc_error(const char* msg) { g_create_error = msg ? msg : ""; }
@@ -1076,6 +1286,7 @@ void dd_options_default(dd_options* opt) {
   opt->mode = 0;
   opt->stream = nullptr;
   opt->debug_flags = 0;
+  opt->safeguard = 1;
 }
 
 dd_status dd_create(const double* mu, const double* nu, const dd_grid* grid, int32_t b,
@@ -1130,41 +1341,7 @@ dd_status dd_create(const double* mu, const double* nu, const dd_grid* grid, int
   c->b = b;
   c->sched.assign(schedule, schedule + n_steps);
   dd_status st = guarded(c, [&] {
-    if (c->opt.stream) {
-      c->stream = (cudaStream_t)c->opt.stream;
-    } else {
-      DD_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
-      c->own_stream = true;
-    }
-    dev_alloc(c->ws_counter, 1);
-    dev_alloc(c->err_flag, 1);
-    dev_alloc(c->totals, 1);
-    dev_alloc(c->yerr, 1);
-    DD_CUDA(cudaMallocHost((void**)&c->h_tot, sizeof(SweepTotals)));
-    DD_CUDA(cudaMallocHost((void**)&c->h_nnz, sizeof(int64_t)));
-    DD_CUDA(cudaMallocHost((void**)&c->h_err, sizeof(int)));
-    DD_CUDA(cudaMallocHost((void**)&c->h_yerr, sizeof(double)));
-    for (int k = 0; k < 3; ++k) DD_CUDA(cudaEventCreate(&c->ev[k]));
-    // cluster solves take the highest stream priority: when per-CTA solves
-    // retire, their SMs go to the waiting clusters first
-    int prio_least = 0, prio_greatest = 0;
-    DD_CUDA(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
-    DD_CUDA(cudaStreamCreateWithPriority(&c->stream2, cudaStreamNonBlocking, prio_greatest));
-    DD_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
-    DD_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
-    DD_CUDA(cudaEventCreate(&c->ev_c0));
-    DD_CUDA(cudaEventCreate(&c->ev_c1));
-    dev_alloc(c->nbig, 1);
-    dev_alloc(c->work_next, 1);
-    DD_CUDA(cudaMallocHost((void**)&c->h_tot_g, 2 * sizeof(SweepTotals)));
-    DD_CUDA(cudaMallocHost((void**)&c->h_nnz_g, 2 * sizeof(int64_t)));
-    DD_CUDA(cudaMallocHost((void**)&c->h_err_g, sizeof(int)));
-    if (const char* tr = std::getenv("DD_TRACE_CELL")) {
-      if (std::sscanf(tr, "%d,%d", &c->trace_part, &c->trace_cell) == 2) {
-        dev_alloc(c->trace_buf, 1024);
-        DD_CUDA(cudaMemset(c->trace_buf, 0, 4096));
-      }
-    }
+    init_device(c);
     build_levels(c, mu, nu);
     enter_level0(c);
     c->eps_cur = c->sched[0].eps;
@@ -1178,6 +1355,7 @@ dd_status dd_create(const double* mu, const double* nu, const dd_grid* grid, int
   *out = c;
   return DD_OK;
 }
+
 
 dd_status dd_set_state(dd_ctx* c, const int64_t* row_ptr, const int32_t* col, const double* val,
                        const double* alpha_A, const double* alpha_B) {
@@ -1210,30 +1388,13 @@ dd_status dd_set_state(dd_ctx* c, const int64_t* row_ptr, const int32_t* col, co
     DD_CUDA(cudaMemcpyAsync(c->rp[c->cur], rp.data(), 8 * (nrows + 1), cudaMemcpyHostToDevice, c->stream));
     DD_CUDA(cudaMemcpyAsync(c->col[c->cur], cs.data(), 4 * nnz, cudaMemcpyHostToDevice, c->stream));
     DD_CUDA(cudaMemcpyAsync(c->val[c->cur], vs.data(), 8 * nnz, cudaMemcpyHostToDevice, c->stream));
-    // duals: reduce α to the cell frame with an anchor from its mean slope
-    const double d2 = h.spacing * h.spacing;
+    // duals: reduce α to the cell frames (affine fit over the pixels with mass)
     for (int part = 0; part < 2; ++part) {
       const double* al = part == 0 ? alpha_A : alpha_B;
       const int nc = num_cells(part, h.nb);
-      std::vector<float> at((size_t)n2, 0.f);
-      std::vector<int2> an(nc);
-      for (int J = 0; J < nc; ++J) {
-        CellGeom g = cell_geom(part, J, h.nb, c->b);
-        int Dr = 0, Dc = 0;
-        if (al) {
-          const double a00 = al[(size_t)g.r0 * h.n + g.c0];
-          const double sr = (al[(size_t)(g.r0 + g.H - 1) * h.n + g.c0] - a00) / (g.H - 1);
-          const double sc = (al[(size_t)g.r0 * h.n + g.c0 + g.W - 1] - a00) / (g.W - 1);
-          Dr = (int)std::lround(sr / (2 * d2));
-          Dc = (int)std::lround(sc / (2 * d2));
-          for (int i = 0; i < g.H; ++i)
-            for (int j = 0; j < g.W; ++j) {
-              const size_t p = (size_t)(g.r0 + i) * h.n + g.c0 + j;
-              at[p] = (float)(al[p] - a00 - 2 * d2 * ((double)Dr * i + (double)Dc * j));
-            }
-        }
-        an[J] = make_int2(g.r0 - Dr, g.c0 - Dc);
-      }
+      std::vector<float> at;
+      std::vector<int2> an;
+      cell_frames(h, c->b, part, al, at, an);
       DD_CUDA(cudaMemcpyAsync(c->alpha[part], at.data(), 4 * (size_t)n2, cudaMemcpyHostToDevice, c->stream));
       DD_CUDA(cudaMemcpyAsync(c->anchor[part], an.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, c->stream));
       DD_CUDA(cudaStreamSynchronize(c->stream));
@@ -1244,8 +1405,15 @@ dd_status dd_set_state(dd_ctx* c, const int64_t* row_ptr, const int32_t* col, co
   });
 }
 
-dd_status dd_half_sweep(dd_ctx* c, int32_t partition, double eps) {
+dd_status dd_refine(dd_ctx* c) {
   return guarded(c, [&] {
+    if (c->lev + 1 >= c->levels) throw DdError{DD_ERR_STATE, "the context is at the finest level"};
+    refine(c);
+  });
+}
+
+dd_status dd_half_sweep(dd_ctx* c, int32_t partition, double eps) {
+  return guarded_sweeps(c, [&] {
     if (partition != 0 && partition != 1) throw DdError{DD_ERR_ARG, "partition must be 0 (A) or 1 (B)"};
     if (!(eps > 0) || !std::isfinite(eps)) throw DdError{DD_ERR_ARG, "eps must be positive"};
     half_sweep(c, partition, eps);
@@ -1253,7 +1421,7 @@ dd_status dd_half_sweep(dd_ctx* c, int32_t partition, double eps) {
 }
 
 dd_status dd_sweep(dd_ctx* c, int32_t n_sweeps, dd_sweep_stats* stats) {
-  return guarded(c, [&] {
+  return guarded_sweeps(c, [&] {
     if (n_sweeps < 0) throw DdError{DD_ERR_ARG, "n_sweeps must be >= 0"};
     for (int k = 0; k < n_sweeps; ++k) one_sweep(c);
     fill_stats(c, stats);
@@ -1261,7 +1429,7 @@ dd_status dd_sweep(dd_ctx* c, int32_t n_sweeps, dd_sweep_stats* stats) {
 }
 
 dd_status dd_run_schedule(dd_ctx* c, dd_sweep_stats* stats) {
-  return guarded(c, [&] {
+  return guarded_sweeps(c, [&] {
     int64_t remaining = 0;
     if (c->step < c->sched.size()) {
       remaining = c->sched[c->step].sweeps - c->step_done;
@@ -1477,6 +1645,244 @@ dd_status dd_get_profile(dd_ctx* c, dd_profile* out) {
 
 dd_status dd_reset_profile(dd_ctx* c) {
   return guarded(c, [&] { c->prof = dd_profile{}; });
+}
+
+}  // extern "C"
+
+// ---- checkpoint / resume ----
+// File layout (host byte order): magic "DDCKPT01", then the header fields in
+// the order written below, the finest level's fixed-point images, the state
+// (basic marginals as CSR in fixed point) and per partition α̃, anchors and
+// the iteration counts of the last solves (which set the launch order).
+namespace {
+constexpr char kCkptMagic[8] = {'D', 'D', 'C', 'K', 'P', 'T', '0', '1'};
+
+struct FileW {
+  FILE* f;
+  template <typename T>
+  void put(const T& v) { put_n(&v, 1); }
+  template <typename T>
+  void put_n(const T* p, size_t n) {
+    if (n && std::fwrite(p, sizeof(T), n, f) != n) throw DdError{DD_ERR_ARG, "checkpoint write failed"};
+  }
+};
+struct FileR {
+  FILE* f;
+  template <typename T>
+  T get() {
+    T v{};
+    get_n(&v, 1);
+    return v;
+  }
+  template <typename T>
+  void get_n(T* p, size_t n) {
+    if (n && std::fread(p, sizeof(T), n, f) != n) throw DdError{DD_ERR_ARG, "checkpoint file is truncated"};
+  }
+};
+struct FileCloser {
+  FILE* f;
+  ~FileCloser() {
+    if (f) std::fclose(f);
+  }
+};
+
+template <typename T>
+std::vector<T> to_host(dd_ctx* c, const T* d, size_t n) {
+  std::vector<T> h(n);
+  if (n) DD_CUDA(cudaMemcpyAsync(h.data(), d, sizeof(T) * n, cudaMemcpyDeviceToHost, c->stream));
+  return h;
+}
+template <typename T>
+void to_dev(dd_ctx* c, T* d, const std::vector<T>& h) {
+  if (!h.empty()) DD_CUDA(cudaMemcpyAsync(d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, c->stream));
+}
+
+void write_options(FileW& w, const dd_options& o) {
+  w.put(o.err_tol); w.put(o.trunc); w.put(o.max_iter); w.put(o.threads_per_cell); w.put(o.max_cluster_cells);
+  w.put(o.x_newton); w.put(o.warm); w.put(o.dual_refine); w.put(o.mode); w.put(o.safeguard); w.put(o.debug_flags);
+}
+dd_options read_options(FileR& r) {
+  dd_options o;
+  dd_options_default(&o);
+  o.err_tol = r.get<double>(); o.trunc = r.get<double>(); o.max_iter = r.get<int32_t>();
+  o.threads_per_cell = r.get<int32_t>(); o.max_cluster_cells = r.get<int32_t>(); o.x_newton = r.get<int32_t>();
+  o.warm = r.get<int32_t>(); o.dual_refine = r.get<int32_t>(); o.mode = r.get<int32_t>();
+  o.safeguard = r.get<int32_t>(); o.debug_flags = r.get<uint64_t>();
+  return o;
+}
+}  // namespace
+
+extern "C" {
+
+dd_status dd_save(dd_ctx* c, const char* path) {
+  return guarded(c, [&] {
+    if (!path) throw DdError{DD_ERR_ARG, "path is NULL"};
+    const LevelHost& h = c->lh[c->lev];
+    const size_t n2 = (size_t)h.n * h.n, nbasic = (size_t)h.nb * h.nb, ncell = (size_t)num_cells(1, h.nb);
+    // device state first (nothing is written if a copy fails)
+    std::vector<int64_t> rp;
+    std::vector<int32_t> col;
+    std::vector<uint64_t> val;
+    if (!c->need_init) {
+      rp = to_host(c, c->rp[c->cur], nbasic + 1);
+      col = to_host(c, c->col[c->cur], (size_t)c->nnz);
+      val = to_host(c, c->val[c->cur], (size_t)c->nnz);
+    }
+    std::vector<float> al[2];
+    std::vector<int2> an[2];
+    std::vector<int32_t> ih[2];
+    for (int k = 0; k < 2; ++k) {
+      al[k] = to_host(c, c->alpha[k], n2);
+      an[k] = to_host(c, c->anchor[k], ncell);
+      ih[k] = to_host(c, c->iters_hist[k], ncell);
+    }
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) throw DdError{DD_ERR_ARG, std::string("cannot open ") + path + " for writing"};
+    FileCloser fc{f};
+    FileW w{f};
+    w.put_n(kCkptMagic, 8);
+    w.put((int32_t)c->n); w.put((int32_t)c->levels); w.put((int32_t)c->b);
+    w.put((int32_t)c->sched.size());
+    for (const dd_eps_step& e : c->sched) { w.put(e.eps); w.put(e.sweeps); w.put(e.level); }
+    write_options(w, c->opt);
+    w.put((int64_t)c->step); w.put((int32_t)c->step_done); w.put((int32_t)c->lev); w.put((int32_t)c->last_part);
+    w.put(c->eps_cur); w.put(c->part_eps[0]); w.put(c->part_eps[1]); w.put((int32_t)c->part_lev[0]);
+    w.put((int32_t)c->part_lev[1]); w.put((int64_t)c->sweeps_done); w.put((int32_t)(c->need_init ? 1 : 0));
+    const LevelHost& fin = c->lh[c->levels - 1];
+    w.put_n(fin.mu_q.data(), fin.mu_q.size());
+    w.put_n(fin.nu_q.data(), fin.nu_q.size());
+    w.put((int64_t)(c->need_init ? 0 : c->nnz));
+    w.put_n(rp.data(), rp.size());
+    w.put_n(col.data(), col.size());
+    w.put_n(val.data(), val.size());
+    for (int k = 0; k < 2; ++k) {
+      w.put_n(al[k].data(), al[k].size());
+      w.put_n(an[k].data(), an[k].size());
+      w.put_n(ih[k].data(), ih[k].size());
+    }
+    if (std::fflush(f) != 0) throw DdError{DD_ERR_ARG, "checkpoint write failed"};
+  });
+}
+
+dd_status dd_load(const char* path, const dd_options* opt, dd_ctx** out) {
+  g_create_error.clear();
+  if (!out) {
+    g_create_error = "out is NULL";
+    return DD_ERR_ARG;
+  }
+  *out = nullptr;
+  dd_ctx* c = new (std::nothrow) dd_ctx();
+  if (!c) return DD_ERR_OOM;
+  bool device = false;
+  dd_status st = guarded(c, [&] {
+    if (!path) throw DdError{DD_ERR_ARG, "path is NULL"};
+    FILE* f = std::fopen(path, "rb");
+    if (!f) throw DdError{DD_ERR_ARG, std::string("cannot open ") + path};
+    FileCloser fc{f};
+    FileR r{f};
+    char magic[8];
+    r.get_n(magic, 8);
+    if (std::memcmp(magic, kCkptMagic, 8) != 0) throw DdError{DD_ERR_ARG, "not a checkpoint of this library"};
+    c->n = r.get<int32_t>();
+    c->levels = r.get<int32_t>();
+    c->b = r.get<int32_t>();
+    const int32_t ns = r.get<int32_t>();
+    if ((c->b != 2 && c->b != 4 && c->b != 8) || c->levels < 1 || c->levels > 12 || c->n < 2 * c->b ||
+        c->n > 16384 || (c->n % (1 << (c->levels - 1))) || ns < 1 || ns > (1 << 20))
+      throw DdError{DD_ERR_ARG, "checkpoint header is invalid"};
+    c->sched.resize(ns);
+    for (dd_eps_step& e : c->sched) {
+      e.eps = r.get<double>();
+      e.sweeps = r.get<int32_t>();
+      e.level = r.get<int32_t>();
+      if (!(e.eps > 0) || e.level < 0 || e.level >= c->levels) throw DdError{DD_ERR_ARG, "bad schedule"};
+    }
+    const dd_options saved = read_options(r);
+    c->opt = opt ? *opt : saved;
+    if (c->opt.max_iter <= 0) c->opt.max_iter = 2000;
+    c->step = (size_t)r.get<int64_t>();
+    c->step_done = r.get<int32_t>();
+    const int lev = r.get<int32_t>();
+    c->last_part = r.get<int32_t>();
+    c->eps_cur = r.get<double>();
+    c->part_eps[0] = r.get<double>();
+    c->part_eps[1] = r.get<double>();
+    c->part_lev[0] = r.get<int32_t>();
+    c->part_lev[1] = r.get<int32_t>();
+    c->sweeps_done = r.get<int64_t>();
+    const bool need_init = r.get<int32_t>() != 0;
+    if (lev < 0 || lev >= c->levels || c->step > c->sched.size() || c->last_part < -1 || c->last_part > 1)
+      throw DdError{DD_ERR_ARG, "checkpoint position is invalid"};
+    const size_t n2f = (size_t)c->n * c->n;
+    std::vector<uint64_t> mu_q(n2f), nu_q(n2f);
+    r.get_n(mu_q.data(), n2f);
+    r.get_n(nu_q.data(), n2f);
+    build_pyramid(c, std::move(mu_q), std::move(nu_q));
+    const LevelHost& h = c->lh[lev];
+    const size_t n2 = (size_t)h.n * h.n, nbasic = (size_t)h.nb * h.nb, ncell = (size_t)num_cells(1, h.nb);
+    const int64_t nnz = r.get<int64_t>();
+    if (nnz < 0 || (need_init && nnz != 0) || nnz > ((int64_t)1 << 40)) throw DdError{DD_ERR_ARG, "bad state size"};
+    std::vector<int64_t> rp(need_init ? 0 : nbasic + 1);
+    std::vector<int32_t> col((size_t)nnz);
+    std::vector<uint64_t> val((size_t)nnz);
+    r.get_n(rp.data(), rp.size());
+    r.get_n(col.data(), col.size());
+    r.get_n(val.data(), val.size());
+    if (!need_init) {
+      if (rp[0] != 0 || rp[nbasic] != nnz) throw DdError{DD_ERR_ARG, "bad state rows"};
+      for (size_t i = 0; i < nbasic; ++i)
+        if (rp[i + 1] < rp[i]) throw DdError{DD_ERR_ARG, "bad state rows"};
+      for (int32_t y : col)
+        if (y < 0 || (size_t)y >= n2) throw DdError{DD_ERR_ARG, "bad state columns"};
+    }
+    std::vector<float> al[2];
+    std::vector<int2> an[2];
+    std::vector<int32_t> ih[2];
+    for (int k = 0; k < 2; ++k) {
+      al[k].resize(n2);
+      an[k].resize(ncell);
+      ih[k].resize(ncell);
+      r.get_n(al[k].data(), n2);
+      r.get_n(an[k].data(), ncell);
+      r.get_n(ih[k].data(), ncell);
+    }
+    // the context on the device, at the saved level
+    device = true;
+    init_device(c);
+    c->lev = lev;
+    c->ld = upload_level(c, lev);
+    float *a0 = nullptr, *a1 = nullptr;
+    int2 *n0 = nullptr, *n1 = nullptr;
+    alloc_level_buffers(c, lev, a0, a1, n0, n1);
+    c->alpha[0] = a0;
+    c->alpha[1] = a1;
+    c->anchor[0] = n0;
+    c->anchor[1] = n1;
+    for (int k = 0; k < 2; ++k) {
+      to_dev(c, c->alpha[k], al[k]);
+      to_dev(c, c->anchor[k], an[k]);
+      to_dev(c, c->iters_hist[k], ih[k]);
+    }
+    c->cur = 0;
+    c->need_init = need_init;
+    c->nnz = nnz;
+    if (!need_init) {
+      state_reserve(c, 0, nnz);
+      to_dev(c, c->rp[0], rp);
+      to_dev(c, c->col[0], col);
+      to_dev(c, c->val[0], val);
+    }
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+  });
+  if (st != DD_OK) {
+    g_create_error = c->err;
+    if (device) release(c);
+    delete c;
+    return st;
+  }
+  *out = c;
+  return DD_OK;
 }
 
 void dd_destroy(dd_ctx* c) {

@@ -128,6 +128,9 @@ struct SweepArgs {
   const int* nbig;          // the first *nbig cells of `order` are solved by clusters (NULL: none)
   int* work_next;           // persistent per-CTA solves: next position of `order` to take
                             // (NULL: one CTA per cell)
+  const int* ncells_dev;    // persistent per-CTA solves: number of cells in `order`, read on the
+                            // device (NULL: ncells); the safeguard's re-solves use it
+  const int* rescued_dev;   // cells re-solved by the safeguard in this half-sweep (NULL: none)
   int max_big;              // upper limit for *nbig (≤ 256)
   int32_t* iters_hist;      // iterations of each cell's last solve in this partition
   int trace_cell;           // debug: cell whose per-iteration error is recorded (-1: none)
@@ -164,8 +167,12 @@ struct SweepTotals {
   int iters_max, not_converged, nonfinite, overflow;
   int learned;               // cells started from the learned duals
   int compared;              // cells whose prediction was compared
+  int rescued;               // cells re-solved by the safeguard
 };
 cudaError_t launch_reduce_cells(const SweepArgs& a, SweepTotals* out_dev, cudaStream_t s);
+// the cells of the half-sweep in `a` whose solve stopped at max_iter (status
+// bit 0) into list[0..*count), for the safeguard's re-solves
+cudaError_t launch_collect_failed(const SweepArgs& a, int32_t* list, int* count, cudaStream_t s);
 cudaError_t launch_y_error(LevelView L, const int64_t* rp, const int32_t* col, const uint64_t* val,
                            int nrows, unsigned long long* scratch, double* out_dev, cudaStream_t s);
 

@@ -717,19 +717,75 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
         bv[tid] = 0.f;
       }
       __syncthreads();
-      // LDLᵀ in place: afterwards M(k,k) = D(k), M(i,k) = L(i,k)·D(k) for i > k
+      // LDLᵀ, right-looking: afterwards M(k,k) = D(k), M(i,k) = L(i,k)·D(k)
+      // for i > k. The lower triangle is held in registers as 4×4 blocks
+      // (136 of them; thread t owns blocks t and t + NT). At step k the owners
+      // of column k (final after step k − 1) write it to shared memory; after
+      // one barrier every thread applies the rank-1 update M(i,j) −=
+      // M(i,k)·M(j,k)/D(k) to its elements with j > k. One barrier per column.
+      constexpr int kNBlk = (kNewtonN / 4) * (kNewtonN / 4 + 1) / 2;
+      float R[2][16];
+      int qbi[2], qbj[2];
+      bool has[2];
+#pragma unroll
+      for (int sb = 0; sb < 2; ++sb) {
+        const int q = tid + sb * NT;
+        has[sb] = q < kNBlk;
+        int bi = 0;
+        if (has[sb])
+          while ((bi + 1) * (bi + 2) / 2 <= q) ++bi;
+        qbi[sb] = bi;
+        qbj[sb] = has[sb] ? q - bi * (bi + 1) / 2 : 0;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) R[sb][r] = 0.f;
+        if (has[sb]) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) R[sb][4 * r + c] = M[(4 * qbi[sb] + r) * kNewtonLd + 4 * qbj[sb] + c];
+        }
+      }
       bool ok = true;
+#pragma unroll 1
       for (int k = 0; k < kNewtonN; ++k) {
-        const float d = M[k * kNewtonLd + k];
-        ok = ok && d > 0.f;
-        const int i = tid & (kNewtonN - 1);
-        if (ok && i > k) {
-          const float lik = M[i * kNewtonLd + k] / d;
-          const int jstep = NT >> 6;   // thread groups of 64, one per column residue
-          for (int j = k + 1 + (tid >> 6); j <= i; j += jstep) M[i * kNewtonLd + j] -= lik * M[j * kNewtonLd + k];
+#pragma unroll
+        for (int sb = 0; sb < 2; ++sb) {
+          if (has[sb] && qbj[sb] == (k >> 2)) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              const int i = 4 * qbi[sb] + r;
+              float v = R[sb][4 * r];
+#pragma unroll
+              for (int c = 1; c < 4; ++c) v = (k & 3) == c ? R[sb][4 * r + c] : v;
+              if (i >= k) M[i * kNewtonLd + k] = v;
+            }
+          }
         }
         __syncthreads();
+        const float d = M[k * kNewtonLd + k];
+        ok = d > 0.f;   // the same d in every thread: a uniform exit
+        if (!ok) break;
+        const float dinv = 1.0f / d;
+#pragma unroll
+        for (int sb = 0; sb < 2; ++sb) {
+          if (has[sb] && 4 * qbj[sb] + 3 > k) {
+            float ci[4], cj[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              ci[r] = M[(4 * qbi[sb] + r) * kNewtonLd + k] * dinv;
+              cj[r] = M[(4 * qbj[sb] + r) * kNewtonLd + k];
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                const int i = 4 * qbi[sb] + r, j = 4 * qbj[sb] + c;
+                if (j > k && j <= i) R[sb][4 * r + c] -= ci[r] * cj[c];
+              }
+          }
+        }
       }
+      __syncthreads();
       if (ok && warp == 0) {
         for (int k = 0; k < kNewtonN; ++k) {
           const float zk = bv[k] / M[k * kNewtonLd + k];
@@ -1424,6 +1480,7 @@ __global__ void __maxnreg__(168) k_sinkhorn(SweepArgs a) {
   __shared__ int s_pos, s_stop;
   extern __shared__ float4 ys_small[];
   const int nbig = a.nbig ? *a.nbig : 0;
+  const int ncells = a.ncells_dev ? *a.ncells_dev : a.ncells;
   // one cell per CTA, or (persistent) cells taken in launch order from a
   // counter until none are left. The capacity bits of err_flag (4: workspace,
   // set by the gather; 8: output, set by an earlier compaction) do not change
@@ -1444,7 +1501,7 @@ __global__ void __maxnreg__(168) k_sinkhorn(SweepArgs a) {
       pos = nbig + blockIdx.x;
       stop = *a.err_flag & (4 | 8);
     }
-    if (pos >= a.ncells || stop) break;
+    if (pos >= ncells || stop) break;
     const int J = a.order ? a.order[pos] : pos;
     if (a.cell_times && threadIdx.x == 0) a.cell_times[2 * J] = globaltimer();
     // dynamic shared memory: the staged support points, then the Newton buffer
@@ -1710,7 +1767,22 @@ __global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals*
     out->overflow = ov;
     out->learned = nl;
     out->compared = nj;
+    out->rescued = a.rescued_dev ? *a.rescued_dev : 0;
   }
+}
+
+__global__ void __launch_bounds__(1024) k_collect_failed(SweepArgs a, int32_t* list, int* count) {
+  __shared__ int s_n;
+  if (*a.err_flag) {   // an earlier step failed: the statuses are not this half-sweep's
+    if (threadIdx.x == 0) *count = 0;
+    return;
+  }
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  for (int J = threadIdx.x; J < a.ncells; J += blockDim.x)
+    if ((a.cell_status[J] & 7) == 1) list[atomicAdd(&s_n, 1)] = J;   // stopped at max_iter, finite
+  __syncthreads();
+  if (threadIdx.x == 0) *count = s_n;
 }
 
 __global__ void k_scatter_rows(const int64_t* rp, int nrows, const int32_t* col, const uint64_t* val,
@@ -2179,6 +2251,11 @@ cudaError_t launch_init_product(LevelView L, int64_t* rp, int32_t* col, uint64_t
                                 cudaStream_t s) {
   const int n2 = L.n * L.n;
   k_init_product<<<(n2 + 255) / 256, 256, 0, s>>>(L, rp, col, val, imax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_collect_failed(const SweepArgs& a, int32_t* list, int* count, cudaStream_t s) {
+  k_collect_failed<<<1, 1024, 0, s>>>(a, list, count);
   return cudaGetLastError();
 }
 

@@ -1,20 +1,22 @@
 // dd_solve_cell_noalloc: one composite-cell solve that allocates no memory.
 //
 // Some callers cannot allocate device memory at the moment they need a
-// solve: code running while a CUDA stream is being captured into a graph
-// (cudaMalloc is not a capturable operation and it also synchronises the
-// device), programs that must not stall on the allocator inside a
-// latency-critical loop, and hosts whose device memory is owned by another
-// runtime that forbids allocations behind its back. For them this entry point
-// runs the library's cell solve (the same k_sinkhorn kernel as a half-sweep)
-// with all of its scratch memory in one file-scope __device__ array of fixed
-// size. The caller passes device pointers for every input and output.
+// solve: hosts whose device memory belongs to another runtime or pool that
+// forbids allocations behind its back (a plug-in inside a framework that
+// hands out only pre-allocated buffers), and latency-critical loops that must
+// not stall on cudaMalloc, which can synchronise the device and take locks.
+// For them this entry point runs the library's cell solve (the same
+// k_sinkhorn kernel as a half-sweep) with all of its scratch memory in one
+// file-scope __device__ array of fixed size. The caller passes device
+// pointers for every input and output.
 //
 // The scratch array is a single buffer per device, held from library load to
-// process exit. Every call uses it and leaves its own data in it; the kernels
-// below rewrite what they read before reading it. Calls that overlap on the
-// GPU (from different streams or host threads) race on it; callers serialise
-// them.
+// process exit. Its device address is resolved once per device, by the first
+// call on that device (cudaGetSymbolAddress with that device current); that
+// first call should come before any stream capture begins. Every call uses
+// the array and leaves its own data in it; the kernels below rewrite what
+// they read before reading it. Calls that overlap on the GPU (from different
+// streams or host threads) race on it; callers serialise them.
 #include "dd.h"
 #include "dd_internal.cuh"
 
@@ -55,7 +57,8 @@ struct Scratch {
   int64_t cell_off;
   double cell_cost, cell_errx;
   int2 anchor, anchor_new;
-  int32_t cell_ny, cell_iters, cell_status, order, err_flag;
+  int2 flags;               // {err_flag, cell_status}: read back together
+  int32_t cell_ny, cell_iters, order;
   unsigned long long ws_counter;
 };
 
@@ -89,17 +92,21 @@ __device__ double block_sum_d(double v, double* ws) {
   return t;
 }
 
-// inputs → scratch: masses in fixed point, anchor, frame of the duals
+// inputs → scratch: masses in fixed point, anchor, frame of the duals. A
+// rejected input (err_flag 16: support; 32: masses of μ and ν disagree) sets
+// cell_off = −1, so the solve kernel returns at once and k_noalloc_finish
+// leaves the caller's buffers untouched.
 __global__ void k_noalloc_prep(Scratch* S, int b, double spacing, const double* mu, int n_y,
                                const int32_t* y_row, const int32_t* y_col, const double* nu,
-                               const double* alpha) {
+                               const double* alpha, double trunc) {
   __shared__ double ws[32];
   __shared__ int s_anchor[2];
+  __shared__ unsigned long long s_mq[4];
   const Geometry q = geometry(b);
   const int H = 2 * b;
   const int tid = threadIdx.x;
   if (tid == 0) {
-    S->err_flag = 0;
+    S->flags = make_int2(0, 0);
     S->cell_off = 0;
     S->cell_ny = n_y;
     S->order = q.J;
@@ -120,9 +127,10 @@ __global__ void k_noalloc_prep(Scratch* S, int b, double spacing, const double* 
       for (int c = 0; c < b; ++c) s += __double2ull_rn(mu[(kr * b + r) * H + kc * b + c] * kFixOne);
     const int slot = kr * q.nb + kc;
     S->M_q[slot] = s;
+    s_mq[i] = s;
   }
   // support: fixed-point ν, validity, centroid
-  double sw = 0.0, sr = 0.0, sc = 0.0;
+  double sw = 0.0, sr = 0.0, sc = 0.0, sq = 0.0;
   int bad = 0;
   for (int k = tid; k < n_y; k += blockDim.x) {
     const int yr = y_row[k], yc = y_col[k];
@@ -130,15 +138,22 @@ __global__ void k_noalloc_prep(Scratch* S, int b, double spacing, const double* 
     if (yr <= -kCorner || yr >= kCorner || yc <= -kCorner || yc >= kCorner || !(v > 0.0)) bad = 1;
     if (k > 0 && (y_row[k - 1] > yr || (y_row[k - 1] == yr && y_col[k - 1] >= yc))) bad = 1;
     S->ws_nu[k] = __double2ull_rn(v * kFixOne);
+    sq += (double)S->ws_nu[k];
     sw += v;
     sr += v * yr;
     sc += v * yc;
   }
-  if (bad) atomicOr(&S->err_flag, 16);
+  if (bad) atomicOr(&S->flags.x, 16);
   sw = block_sum_d(sw, ws);
   sr = block_sum_d(sr, ws);
   sc = block_sum_d(sc, ws);
+  sq = block_sum_d(sq, ws);
   if (tid == 0) {
+    // BalanceMeasures needs ‖ν_cell‖ = ‖μ_J‖; Truncate may have removed up to
+    // trunc per entry of the four basic marginals from a previous solve
+    const double mq = (double)s_mq[0] + (double)s_mq[1] + (double)s_mq[2] + (double)s_mq[3];
+    if (!(fabs(sq - mq) <= 1e-9 * mq + 4.0 * n_y * trunc * kFixOne)) atomicOr(&S->flags.x, 32);
+    if (S->flags.x & (16 | 32)) S->cell_off = -1;
     const double cr = sw > 0 ? sr / sw : 0.0, cc = sw > 0 ? sc / sw : 0.0;
     s_anchor[0] = kCorner + (int)lrint(cr - 0.5 * (H - 1));
     s_anchor[1] = kCorner + (int)lrint(cc - 0.5 * (H - 1));
@@ -166,6 +181,7 @@ __global__ void k_noalloc_finish(Scratch* S, int b, double spacing, int n_y, con
                                  const int32_t* y_col, double* alpha, double* nu_basic) {
   const Geometry q = geometry(b);
   const int H = 2 * b;
+  if (S->flags.x & (16 | 32)) return;   // rejected input: outputs untouched
   for (int e = threadIdx.x; e < 4 * n_y; e += blockDim.x) nu_basic[e] = 0.0;
   __syncthreads();
   for (int i = 0; i < 4; ++i) {
@@ -226,7 +242,7 @@ extern "C" dd_status dd_solve_cell_noalloc(const double* mu, int32_t b, double s
   cudaStream_t st = (cudaStream_t)stream;
   const Geometry q = geometry(b);
 
-  k_noalloc_prep<<<1, 256, 0, st>>>(S, b, spacing, mu, n_y, y_row, y_col, nu, alpha);
+  k_noalloc_prep<<<1, 256, 0, st>>>(S, b, spacing, mu, n_y, y_row, y_col, nu, alpha, trunc);
 
   // views: shift each array so that the cell's level indices land in S
   SweepArgs a{};
@@ -264,8 +280,8 @@ extern "C" dd_status dd_solve_cell_noalloc(const double* mu, int32_t b, double s
   a.cell_errx = &S->cell_errx - q.J;
   a.cell_iters = &S->cell_iters - q.J;
   a.newton = 1;
-  a.cell_status = &S->cell_status - q.J;
-  a.err_flag = &S->err_flag;
+  a.cell_status = &S->flags.y - q.J;
+  a.err_flag = &S->flags.x;
   a.order = &S->order;
   a.nbig = nullptr;
   a.max_big = 0;
@@ -276,12 +292,14 @@ extern "C" dd_status dd_solve_cell_noalloc(const double* mu, int32_t b, double s
   cudaError_t e = launch_sinkhorn(a, 128, st);
   if (e != cudaSuccess) return fail(std::string("launch: ") + cudaGetErrorString(e), DD_ERR_CUDA);
   k_noalloc_finish<<<1, 256, 0, st>>>(S, b, spacing, n_y, y_row, y_col, alpha, nu_basic);
-  int flag = 0;
-  e = cudaMemcpyAsync(&flag, &S->err_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  int2 flags = make_int2(0, 0);   // {err_flag, cell_status}
+  e = cudaMemcpyAsync(&flags, &S->flags, sizeof(int2), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(std::string("CUDA: ") + cudaGetErrorString(e), DD_ERR_CUDA);
-  if (flag & 16) return fail("support points must be distinct, row-major sorted, within 2047 pixels of the corner, with nu > 0");
-  if (flag & 2) return fail("the cell solve produced a non-finite value", DD_ERR_NUMERIC);
+  if (flags.x & 16) return fail("support points must be distinct, row-major sorted, within 2047 pixels of the corner, with nu > 0");
+  if (flags.x & 32) return fail("the masses of mu and nu over the cell must agree (1e-9 relative + 4 n_y trunc)");
+  if (flags.x & 2) return fail("the cell solve produced a non-finite value", DD_ERR_NUMERIC);
+  if (flags.y & 1) return fail("the cell solve stopped at max_iter before reaching err_tol", DD_ERR_NOT_CONVERGED);
   dd_set_noalloc_error("");
   return DD_OK;
 }

@@ -31,13 +31,13 @@ class dd_options(C.Structure):
     _fields_ = [("err_tol", C.c_double), ("trunc", C.c_double), ("max_iter", C.c_int32),
                 ("threads_per_cell", C.c_int32), ("max_cluster_cells", C.c_int32), ("x_newton", C.c_int32),
                 ("warm", C.c_int32), ("dual_refine", C.c_int32), ("mode", C.c_int32), ("stream", C.c_void_p),
-                ("debug_flags", C.c_uint64)]
+                ("debug_flags", C.c_uint64), ("safeguard", C.c_int32)]
 
 
 class dd_sweep_stats(C.Structure):
     _fields_ = [("level", C.c_int32), ("partition", C.c_int32), ("eps", C.c_double), ("nnz", C.c_int64),
                 ("max_iters", C.c_int32), ("mean_iters", C.c_double), ("cells_not_converged", C.c_int32),
-                ("sweeps_done", C.c_int64)]
+                ("sweeps_done", C.c_int64), ("cells_rescued", C.c_int32)]
 
 
 class dd_profile(C.Structure):
@@ -45,13 +45,23 @@ class dd_profile(C.Structure):
                 ("solve_ms", C.c_double), ("gather_launches", C.c_int64), ("gather_ms", C.c_double),
                 ("cluster_ms", C.c_double), ("kernel_evals", C.c_double), ("sinkhorn_iters", C.c_double), ("cells", C.c_int64),
                 ("newton_steps", C.c_int64), ("hessian_fma", C.c_double), ("learned_cells", C.c_int64),
-                ("compared_cells", C.c_int64)]
+                ("compared_cells", C.c_int64), ("rescued_cells", C.c_int64), ("graph_reruns", C.c_int64)]
 
 
 class DDError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+class DDNotConverged(DDError):
+    """Cell solves stayed at max_iter after the safeguard. The call completed
+    its sweeps and the state is feasible; `stats` holds the call's statistics
+    (None for dd_half_sweep)."""
+
+    def __init__(self, msg, stats=None):
+        super().__init__(DD_ERR_NOT_CONVERGED, msg)
+        self.stats = stats
 
 
 if not os.path.exists(LIB):
@@ -69,6 +79,9 @@ _lib.dd_create.argtypes = [_pd, _pd, C.POINTER(dd_grid), C.c_int32, C.POINTER(dd
                            C.POINTER(dd_options), C.POINTER(_P)]
 _lib.dd_set_state.argtypes = [_P, _pi64, _pi32, _pd, _P, _P]
 _lib.dd_half_sweep.argtypes = [_P, C.c_int32, C.c_double]
+_lib.dd_refine.argtypes = [_P]
+_lib.dd_save.argtypes = [_P, C.c_char_p]
+_lib.dd_load.argtypes = [C.c_char_p, C.POINTER(dd_options), C.POINTER(_P)]
 _lib.dd_sweep.argtypes = [_P, C.c_int32, C.POINTER(dd_sweep_stats)]
 _lib.dd_run_schedule.argtypes = [_P, C.POINTER(dd_sweep_stats)]
 _lib.dd_cost.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -109,7 +122,7 @@ _lib.dd_mlp_train_step.argtypes = [_P, _P, _P, C.c_int64, C.c_float, C.POINTER(C
 _lib.dd_attach_mlp.argtypes = [_P, _P]
 _lib.dd_autotune.argtypes = [_P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
 _lib.dd_cell_training_pairs.argtypes = [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_int64)]
-for _f in ("dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep", "dd_run_schedule", "dd_cost",
+for _f in ("dd_create", "dd_set_state", "dd_half_sweep", "dd_refine", "dd_save", "dd_load", "dd_sweep", "dd_run_schedule", "dd_cost",
            "dd_get_basic_marginals", "dd_get_plan", "dd_get_duals", "dd_get_info", "dd_get_profile",
            "dd_reset_profile", "dd_get_cell_stats", "dd_mlp_create", "dd_mlp_get_params", "dd_mlp_set_params",
            "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step", "dd_attach_mlp", "dd_cell_training_pairs",
@@ -117,7 +130,7 @@ for _f in ("dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep", "dd_run_sch
            "dd_interpolate_dual_host", "dd_relative_pd_gap_host", "dd_coupling_image_host"):
     getattr(_lib, _f).restype = C.c_int
 
-EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", "dd_sweep",
+EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", "dd_refine", "dd_save", "dd_load", "dd_sweep",
             "dd_run_schedule", "dd_cost", "dd_get_basic_marginals", "dd_get_plan", "dd_get_duals",
             "dd_get_info", "dd_get_cell_stats", "dd_get_profile", "dd_reset_profile", "dd_destroy",
             "dd_last_error", "dd_solve_cell_noalloc", "dd_mlp_num_params", "dd_mlp_create", "dd_mlp_destroy",
@@ -127,9 +140,17 @@ EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", 
             "dd_coupling_image_host")
 
 
-def _check(ctx, st):
+def _check(ctx, st, stats=None):
+    if st == DD_ERR_NOT_CONVERGED and ctx is not None:
+        raise DDNotConverged((_lib.dd_last_error(ctx) or b"").decode(), stats)
     if st != DD_OK:
         raise DDError(st, (_lib.dd_last_error(ctx) or b"").decode())
+
+
+class DDConvergenceWarning(UserWarning):
+    """Issued by DD.sweep / run_schedule / half_sweep when cell solves stayed
+    at max_iter after the safeguard (the C call returned DD_ERR_NOT_CONVERGED
+    after completing its sweeps)."""
 
 
 def _stream_ptr(stream):
@@ -181,15 +202,29 @@ def dd_half_sweep(ctx, partition, eps):
     _check(ctx, _lib.dd_half_sweep(ctx, int(partition), float(eps)))
 
 
+def dd_refine(ctx):
+    _check(ctx, _lib.dd_refine(ctx))
+
+
+def dd_save(ctx, path):
+    _check(ctx, _lib.dd_save(ctx, os.fsencode(path)))
+
+
+def dd_load(path, opt: dd_options | None = None):
+    h = _P()
+    _check(None, _lib.dd_load(os.fsencode(path), C.byref(opt) if opt is not None else None, C.byref(h)))
+    return h
+
+
 def dd_sweep(ctx, n_sweeps=1) -> dd_sweep_stats:
     st = dd_sweep_stats()
-    _check(ctx, _lib.dd_sweep(ctx, int(n_sweeps), C.byref(st)))
+    _check(ctx, _lib.dd_sweep(ctx, int(n_sweeps), C.byref(st)), st)
     return st
 
 
 def dd_run_schedule(ctx) -> dd_sweep_stats:
     st = dd_sweep_stats()
-    _check(ctx, _lib.dd_run_schedule(ctx, C.byref(st)))
+    _check(ctx, _lib.dd_run_schedule(ctx, C.byref(st)), st)
     return st
 
 
@@ -470,14 +505,45 @@ class DD:
     def set_state(self, row_ptr, col, val, alpha_A=None, alpha_B=None):
         dd_set_state(self.ctx, row_ptr, col, val, alpha_A, alpha_B)
 
-    def half_sweep(self, partition, eps):
-        dd_half_sweep(self.ctx, partition, eps)
+    def _sweeps(self, fn, *args, strict=False):
+        # a DD_ERR_NOT_CONVERGED call has completed its sweeps: by default it
+        # is reported as a warning and its statistics are returned
+        try:
+            return fn(self.ctx, *args)
+        except DDNotConverged as e:
+            if strict:
+                raise
+            import warnings
+            warnings.warn(str(e), DDConvergenceWarning, stacklevel=3)
+            return e.stats
 
-    def sweep(self, n=1):
-        return dd_sweep(self.ctx, n)
+    def half_sweep(self, partition, eps, strict=False):
+        self._sweeps(dd_half_sweep, partition, eps, strict=strict)
 
-    def run_schedule(self):
-        return dd_run_schedule(self.ctx)
+    def refine(self):
+        dd_refine(self.ctx)
+
+    def save(self, path):
+        dd_save(self.ctx, path)
+
+    @classmethod
+    def load(cls, path, b=None, **opts):
+        """A context resumed from a dd_save file; with keyword options the
+        saved options are replaced by dd_options_default(**opts)."""
+        self = cls.__new__(cls)
+        self.opt = dd_options_default(**opts) if opts else None
+        self.ctx = dd_load(path, self.opt)
+        _, nl, nbasic, _, _ = dd_get_info(self.ctx)
+        self.b = b if b is not None else nl // int(round(nbasic ** 0.5))
+        self.n = None
+        self.levels = None
+        return self
+
+    def sweep(self, n=1, strict=False):
+        return self._sweeps(dd_sweep, n, strict=strict)
+
+    def run_schedule(self, strict=False):
+        return self._sweeps(dd_run_schedule, strict=strict)
 
     def cost(self, with_y=True):
         return dd_cost(self.ctx, with_y)

@@ -91,3 +91,57 @@ def test_header_is_plain_c(tmp_path):
     r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
                         "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_struct_layouts_match_the_binding(tmp_path, lib):
+    # the ctypes mirrors of dd_options, dd_profile and dd_sweep_stats have the
+    # C layout (sizes and every field offset)
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"dd_options": lib.dd_options, "dd_profile": lib.dd_profile, "dd_sweep_stats": lib.dd_sweep_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dd.h"', "int main(void) {"]
+    for sname, cls in structs.items():
+        lines.append(f'  printf("{sname} size %zu\\n", sizeof({sname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{sname} {fname} %zu\\n", offsetof({sname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln.strip():
+            parts = ln.split()
+            got[tuple(parts[:-1])] = int(parts[-1])
+    for sname, cls in structs.items():
+        assert got[(sname, "size")] == ctypes.sizeof(cls), sname
+        for fname, _ in cls._fields_:
+            assert got[(sname, fname)] == getattr(cls, fname).offset, (sname, fname)
+
+
+def test_load_rejects_files_that_are_not_checkpoints(tmp_path, lib):
+    # dd_load checks the file before it touches the device
+    bad = tmp_path / "not_a_checkpoint.bin"
+    bad.write_bytes(b"hello, this is not a checkpoint" * 4)
+    with pytest.raises(lib.DDError) as e:
+        lib.dd_load(str(bad))
+    assert e.value.status == lib.DD_ERR_ARG and "checkpoint" in str(e.value)
+    short = tmp_path / "truncated.bin"
+    short.write_bytes(b"DDCKPT01" + b"\x00" * 6)
+    with pytest.raises(lib.DDError) as e:
+        lib.dd_load(str(short))
+    assert e.value.status == lib.DD_ERR_ARG
+    with pytest.raises(lib.DDError) as e:
+        lib.dd_load(str(tmp_path / "missing.bin"))
+    assert e.value.status == lib.DD_ERR_ARG
+
+
+def test_safeguard_is_on_by_default(lib):
+    assert lib.dd_options_default().safeguard == 1

@@ -673,3 +673,64 @@ def test_gather_is_the_sum_on_the_union_of_supports():
     np.testing.assert_allclose(nu_cell, [0.6, 0.1, 0.6, 0.5, 1.0], rtol=1e-15)
     cols, nu_cell = dd.gather(rows, [1])
     np.testing.assert_array_equal(cols, [4, 5])
+
+
+def test_refined_marginals_hand_computed():
+    # eq. FineBasicMarginals on a case worked out by hand (coarse 4×4 pixels,
+    # fine 8×8, b = 2 at both levels, so coarse basic cell (0,0) is the
+    # parent of fine basic cells (0,0), (0,1), (1,0), (1,1)):
+    #  * fine ν = 1/64 except the children of coarse pixel 1 (fine 2, 3, 10,
+    #    11: 1, 2, 3, 2 /64, so ν̂ = 8/64) and of coarse pixel 10 (fine 36,
+    #    37, 44, 45: 0.5, 1.5, 1, 1 /64, ν̂ = 4/64);
+    #  * fine μ = 1/64 except 3/64 on fine basic cell (0,1), so the parent has
+    #    μ̂ = 24/64, fine cell (0,0) 4/64 (share 1/6) and (0,1) 12/64 (1/2);
+    #  * coarse row 0 holds 0.06 at coarse pixel 1 and 0.02 at pixel 10.
+    # Fine cell (0,0): at the children of pixel 1, ν(y)·(0.06/(8/64))·(1/6) =
+    # ν(y)·0.08; at those of pixel 10, ν(y)·(0.02/(4/64))·(1/6) = ν(y)·0.32/6.
+    # Fine cell (0,1) gets three times these values; fine cell (1,0) (index 4)
+    # the values of (0,0). Coarse row 3 holds 0.05 at coarse pixel 5 (fine
+    # children 18, 19, 26, 27 with ν = 1/64, ν̂ = 4/64); its child fine cell
+    # (2,2) (index 10) has a quarter of its parent's μ: 0.05/16 each.
+    nu_f = np.full((8, 8), 1 / 64)
+    nu_f.flat[[2, 3, 10, 11]] = np.array([1, 2, 3, 2]) / 64
+    nu_f.flat[[36, 37, 44, 45]] = np.array([0.5, 1.5, 1, 1]) / 64
+    mu_f = np.full((8, 8), 1 / 64)
+    mu_f[0:2, 2:4] = 3 / 64
+    coarse = dd.GridProblem(dd.pyramid(mu_f, 2)[0], dd.pyramid(nu_f, 2)[0], 2, 1 / 4)
+    fine = dd.GridProblem(mu_f, nu_f, 2, 1 / 8)
+    rows_c = [(np.array([1, 10]), np.array([0.06, 0.02])), (np.array([0]), np.array([0.01])),
+              (np.array([15]), np.array([0.01])), (np.array([5]), np.array([0.05]))]
+    rows_f = dd.refine_basic_marginals(coarse, fine, rows_c)
+    y0 = [2, 3, 10, 11, 36, 37, 44, 45]
+    v0 = [0.00125, 0.0025, 0.00375, 0.0025, 0.0004166666666666667, 0.00125, 0.0008333333333333334,
+          0.0008333333333333334]
+    v1 = [0.00375, 0.0075, 0.01125, 0.0075, 0.00125, 0.00375, 0.0025, 0.0025]
+    for i, v in ((0, v0), (1, v1), (4, v0)):
+        np.testing.assert_array_equal(rows_f[i][0], y0)
+        np.testing.assert_allclose(rows_f[i][1], v, rtol=1e-13)
+    np.testing.assert_array_equal(rows_f[10][0], [18, 19, 26, 27])
+    np.testing.assert_allclose(rows_f[10][1], [0.003125] * 4, rtol=1e-13)
+
+
+def test_fill_massless_affine_reproduces_an_affine_dual():
+    # pixels without mass take the affine fit of their A cell's dual: on an
+    # affine α (a different plane per A cell) they get exactly its values,
+    # and pixels with mass keep theirs
+    n, b = 16, 4
+    mu = syn.gaussian_mixture(n, 2, 12)
+    dead = [(0, 0), (7, 7), (3, 4), (8, 15), (12, 9)]
+    for r, c in dead:
+        mu[r, c] = 0.0
+    prob = dd.GridProblem(mu, syn.gaussian_mixture(n, 2, 13), b, 1 / n)
+    i, j = np.divmod(np.arange(n * n), n)
+    cell = (i // (2 * b)) * (n // (2 * b)) + j // (2 * b)
+    rng = np.random.default_rng(5)
+    a, sr, sc = rng.normal(size=(3, cell.max() + 1))
+    alpha = a[cell] + sr[cell] * i + sc[cell] * j
+    scrambled = alpha.copy()
+    for r, c in dead:
+        scrambled[r * n + c] = 1e3 * rng.normal()
+    out = dd.fill_massless_affine(prob, scrambled)
+    np.testing.assert_allclose(out, alpha, rtol=0, atol=1e-11)
+    live = prob.mu > 0
+    np.testing.assert_array_equal(out[live], scrambled[live])

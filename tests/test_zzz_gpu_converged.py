@@ -1,0 +1,77 @@
+"""The full coarse-to-fine GPU run of the 256² workload (5 blobs, 4×4 basic
+cells, 64² → 128² → 256², final ε = 2h²) against the converged FP64 oracle
+state stored in tests/golden/converged_gm256_b4_l3.{json,npz} (written by
+tests/golden/oracle_converged.py, which calls only the oracle).
+
+Criterion of convergence (the method's GPU form): X- and Y-marginal errors
+≤ 1e-6 in L1 and the transport cost within 1e-6 relative of the converged
+oracle cost; then the basic marginals (ν_i) within 1e-5 relative L1 of the
+oracle's on the stored sample of basic cells.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2001_10986_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLD = os.path.join(HERE, "golden", "converged_gm256_b4_l3")
+PLAN_TOL = 1e-5
+COST_TOL = 1e-6
+MARG_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2001_10986_gb300 import build
+    build.build()
+    from paper_2001_10986_gb300 import dd
+    return dd
+
+
+def sampled_rows_rel_l1(rp, col, val, gold_npz):
+    """Relative L1 distance of the basic marginals (ν_i) on the stored rows."""
+    ids, grp, gcol, gval = (gold_npz[k] for k in ("row_ids", "row_ptr", "col", "val"))
+    num = den = 0.0
+    for k, i in enumerate(ids):
+        ce, ve = gcol[grp[k]:grp[k + 1]], gval[grp[k]:grp[k + 1]]
+        cg, vg = col[rp[i]:rp[i + 1]], val[rp[i]:rp[i + 1]]
+        u = np.union1d(ce, cg)
+        a = np.zeros(u.size)
+        a[np.searchsorted(u, cg)] = vg
+        e = np.zeros(u.size)
+        e[np.searchsorted(u, ce)] = ve
+        num += np.abs(a - e).sum()
+        den += e.sum()
+    return num / den
+
+
+@pytest.mark.skipif(not os.path.exists(GOLD + ".json"), reason="converged oracle state not stored")
+@pytest.mark.parametrize("mode", [1, 0])
+def test_gm256_full_schedule_reaches_the_converged_oracle(lib, mode):
+    gold = json.load(open(GOLD + ".json"))
+    npz = np.load(GOLD + ".npz")
+    w = syn.WORKLOADS["gm256_b4_l3"]
+    mu, nu = syn.image_pair(w, 0)
+    g = lib.DD(mu, nu, w.b, w.levels, syn.paper_schedule(w.n, w.levels, 1), err_tol=1e-6, mode=mode)
+    g.run_schedule(strict=True)
+    met = False
+    for k in range(80):
+        cost, ex, ey = g.cost()
+        rel_cost = abs(cost - gold["cost"]) / gold["cost"]
+        if ex <= MARG_TOL and ey <= MARG_TOL and rel_cost <= COST_TOL:
+            met = True
+            break
+        g.sweep(1, strict=True)
+    rp, col, val = g.basic_marginals()
+    _, nl, _, eps, _ = g.info()
+    g.close()
+    assert nl == w.n and eps == pytest.approx(gold["eps"], rel=1e-12)
+    assert met, (k, cost, ex, ey, rel_cost)
+    assert sampled_rows_rel_l1(rp, col, val, npz) < PLAN_TOL

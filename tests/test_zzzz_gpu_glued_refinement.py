@@ -65,3 +65,47 @@ def test_relative_pd_gap_of_a_gpu_run(lib):
     rel_w, _, primal_w = odd.relative_pd_gap(ref.prob, P, a_hat, b_hat, ref.eps)
     assert primal == pytest.approx(primal_w, rel=1e-5)
     assert abs(rel) < 1e-4 and abs(rel - rel_w) < 1e-5
+
+
+def test_hybrid_refinement_duals_with_massless_corners(lib):
+    # pixels without mass at corners of coarse A and B cells: the glued coarse
+    # dual is continued there by the affine fit of its A cell before the §6.4
+    # interpolation, so the B duals of the fine level match the oracle's on
+    # every pixel with mass (up to one constant per cell), and the run still
+    # converges to the oracle's state
+    n, b = 32, 4
+    mu = syn.gaussian_mixture(n, 4, 32)
+    nu = syn.gaussian_mixture(n, 4, 33)
+    for (r, c) in ((0, 0), (7, 7), (4, 4), (8, 4)):      # coarse pixels (16² level)
+        mu[2 * r:2 * r + 2, 2 * c:2 * c + 2] = 0.0
+    mu /= mu.sum()
+    sched = syn.paper_schedule(n, 2, 6)
+    coarse = [s for s in sched if s[2] == 0]
+    n0 = sum(s[1] for s in coarse)
+    g = lib.DD(mu, nu, b, 2, sched, err_tol=1e-7, dual_refine=1)
+    g.sweep(n0)
+    g.refine()
+    aB = g.duals(1)
+    with np.errstate(divide="ignore"):
+        ref_c = odd.run_schedule(mu, nu, b, 2, coarse, odd.Params(err=1e-10))
+    fine = odd.GridProblem(mu, nu, b, 1.0 / n)
+    a_hat, _ = odd.glue_duals(ref_c.prob, ref_c.alpha["A"], ref_c.alpha["B"], ref_c.eps)
+    a_ref = odd.refine_duals_glued(ref_c.prob, fine, odd.fill_massless_affine(ref_c.prob, a_hat))
+    eps_f = sched[len(coarse)][0]
+    worst = 0.0
+    for J in fine.parts["B"]:
+        X = fine.cell_points(J)
+        X = X[fine.mu[X] > 0]
+        worst = max(worst, np.ptp(aB[X] - a_ref[X]) / eps_f)
+    assert worst < 1e-3, worst
+    g.sweep(sum(s[1] for s in sched) - n0)
+    rp, col, val = g.basic_marginals()
+    cost, _, _ = g.cost(with_y=False)
+    g.close()
+    with np.errstate(divide="ignore"):
+        ref = odd.run_schedule(mu, nu, b, 2, sched, odd.Params(err=1e-9), dual_refinement="hybrid")
+    got = odd.rows_to_dense(odd.rows_from_csr(rp, col, val), n * n)
+    want = odd.rows_to_dense(ref.rows, n * n)
+    assert np.abs(got - want).sum() / want.sum() < PLAN_TOL
+    ref_cost = ref.history[-1][3].cost
+    assert abs(cost - ref_cost) / ref_cost < COST_TOL
