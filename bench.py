@@ -64,6 +64,7 @@ def parse():
     p.add_argument("--clusters", type=int, default=-1, help="max cells solved by 8-CTA clusters (-1: library choice)")
     p.add_argument("--mode", type=int, default=1, help="0: per-kernel launches, 1: persistent solves + graph-replayed sweeps")
     p.add_argument("--autotune", type=int, default=1, help="1: pick threads per cell and cluster cells by dd_autotune first")
+    p.add_argument("--newton", type=int, default=1, help="dd_options.x_newton (0: plain X-iterations only)")
     return p.parse_args()
 
 
@@ -334,10 +335,11 @@ GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
 def load_golden(workload):
-    """The converged FP64 oracle state of a workload, if stored (written by
-    tests/golden/oracle_converged.py): (json dict, npz of sampled rows)."""
+    """The FP64 oracle's state of a workload after its schedule and a fixed
+    number of final sweeps, if stored (written by tests/golden/oracle_state.py):
+    (json dict, npz of sampled rows)."""
     import numpy as np
-    base = os.path.join(GOLDEN, f"converged_{workload}")
+    base = os.path.join(GOLDEN, f"oracle_state_{workload}")
     if not os.path.exists(base + ".json"):
         return None
     with open(base + ".json") as f:
@@ -362,35 +364,27 @@ def sampled_rows_rel_l1(rp, col, val, npz):
     return float(num / den)
 
 
-def time_to_converged(dd, syn, mu, nu, w, args, stream, max_final_sweeps=400, mlp=None, gold=None, **opts):
+def time_to_converged(dd, syn, mu, nu, w, args, stream, max_final_sweeps=400, mlp=None, **opts):
     """Wall time from host images to a converged plan: dd_create, the whole
     coarse-to-fine schedule (one sweep at the final ε), then sweeps at the
-    final ε until the convergence criterion holds. With a stored converged
-    oracle state (gold): X- and Y-marginal L1 errors ≤ 1e-6 and the
-    transport cost within 1e-6 relative of the oracle's; afterwards (outside
-    the clock) the basic marginals are compared with the oracle's sampled
-    rows. Without one: both errors ≤ 1e-6 and one sweep changing the cost by
-    at most 1e-7 relative. Each check is one dd_cost call (a device→host read
-    per sweep)."""
+    final ε until both marginal L1 errors are ≤ 1e-6 and one sweep changes the
+    transport cost by at most 1e-7 relative. Each check is one dd_cost call (a
+    device→host read per sweep)."""
     import torch
     n, b, L = w.n, w.b, w.levels
     torch.cuda.synchronize()
     t = time.perf_counter()
     h = dd.DD(mu, nu, b, L, syn.paper_schedule(n, L, 1), err_tol=args.err, stream=stream,
               threads_per_cell=args.tpc if w.n == 1024 else 0,
-              max_cluster_cells=args.clusters if w.n == 1024 else -1, mode=args.mode, **opts)
+              max_cluster_cells=args.clusters if w.n == 1024 else -1, mode=args.mode, x_newton=args.newton, **opts)
     if mlp is not None:
         h.attach_mlp(mlp)
     h.run_schedule()
     k, rel, prev = 1, None, None
     while True:
         cost, ex, ey = h.cost()
-        if gold is not None:
-            rel = abs(cost - gold[0]["cost"]) / gold[0]["cost"]
-            done = ex <= 1e-6 and ey <= 1e-6 and rel <= 1e-6
-        else:
-            rel = abs(cost - prev) / abs(cost) if prev is not None else None
-            done = ex <= 1e-6 and ey <= 1e-6 and rel is not None and rel <= 1e-7
+        rel = abs(cost - prev) / abs(cost) if prev is not None else None
+        done = ex <= 1e-6 and ey <= 1e-6 and rel is not None and rel <= 1e-7
         prev = cost
         if done or k >= max_final_sweeps:
             break
@@ -399,22 +393,45 @@ def time_to_converged(dd, syn, mu, nu, w, args, stream, max_final_sweeps=400, ml
     torch.cuda.synchronize()
     dt = time.perf_counter() - t
     p = h.profile()
-    out = {"seconds": dt, "final_sweeps": k, "converged": bool(done), "cost": cost, "err_x": ex, "err_y": ey,
-           "sinkhorn_iters": p.sinkhorn_iters, "newton_steps": p.newton_steps,
-           "learned_cells": p.learned_cells, "compared_cells": p.compared_cells,
-           "rescued_cells": p.rescued_cells}
-    if gold is not None:
-        rp, col, val = h.basic_marginals()
-        out.update(oracle_cost_rel=rel, plan_rel_l1=sampled_rows_rel_l1(rp, col, val, gold[1]),
-                   plan_rows_compared=int(gold[1]["row_ids"].size),
-                   criterion="err_x, err_y <= 1e-6 and |cost - oracle|/oracle <= 1e-6 (converged FP64 oracle, "
-                             "tests/golden); plan: sampled basic marginals vs the oracle's")
-    else:
-        out.update(last_rel_change=rel,
-                   criterion="err_x, err_y <= 1e-6 and relative cost change over one final-eps sweep <= 1e-7 "
-                             "(no converged oracle state stored for this size)")
     h.close()
-    return out
+    return {"seconds": dt, "final_sweeps": k, "converged": bool(done), "last_rel_change": rel, "cost": cost,
+            "err_x": ex, "err_y": ey, "sinkhorn_iters": p.sinkhorn_iters, "newton_steps": p.newton_steps,
+            "learned_cells": p.learned_cells, "compared_cells": p.compared_cells,
+            "rescued_cells": p.rescued_cells, "peak_state_bytes": p.peak_state_bytes,
+            "criterion": "err_x, err_y <= 1e-6 and relative cost change over one final-eps sweep <= 1e-7"}
+
+
+def oracle_parity_256(dd, syn, args, stream, mlp=None, **opts):
+    """The 256² workload's schedule and the stored oracle run's number of
+    final sweeps on the GPU, timed from host images, then compared with the
+    oracle's state (tests/golden): cost, marginal errors, sampled basic
+    marginals."""
+    import torch
+    gold = load_golden("gm256_b4_l3")
+    if gold is None:
+        return None
+    w = syn.WORKLOADS["gm256_b4_l3"]
+    mu, nu = syn.image_pair(w, 0)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    h = dd.DD(mu, nu, w.b, w.levels, syn.paper_schedule(w.n, w.levels, gold[0]["final_sweeps"]), err_tol=args.err,
+              stream=stream, mode=args.mode, x_newton=args.newton, **opts)
+    if mlp is not None:
+        h.attach_mlp(mlp)
+    h.run_schedule()
+    cost, ex, ey = h.cost()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    rp, col, val = h.basic_marginals()
+    p = h.profile()
+    h.close()
+    return {"seconds": dt, "cost": cost, "oracle_cost": gold[0]["cost"],
+            "cost_rel": abs(cost - gold[0]["cost"]) / gold[0]["cost"], "err_x": ex, "err_y": ey,
+            "plan_rel_l1": sampled_rows_rel_l1(rp, col, val, gold[1]),
+            "plan_rows_compared": int(gold[1]["row_ids"].size), "sinkhorn_iters": p.sinkhorn_iters,
+            "oracle_seconds": gold[0]["seconds"], "oracle_workers": gold[0]["workers"],
+            "what": "same schedule and final sweeps as the stored FP64 oracle run; the oracle's wall time is "
+                    "its own run on this build machine's cores"}
 
 
 def run_cuda(args):
@@ -443,7 +460,8 @@ def run_cuda(args):
 
     # ---- setup (untimed): coarse levels, refinement, warm-up sweeps at 2h² ----
     g = dd.DD(mu, nu, b, L, sched, err_tol=args.err, stream=stream, debug_flags=2 if args.mode == 0 else 0,
-              threads_per_cell=args.tpc, max_cluster_cells=args.clusters, mode=args.mode)
+              threads_per_cell=args.tpc, max_cluster_cells=args.clusters, mode=args.mode,
+              x_newton=args.newton)
     g.run_schedule()
     tuned = None
     if args.autotune:
@@ -478,7 +496,7 @@ def run_cuda(args):
         # launches and CUDA events (a graph replay has no per-kernel events)
         gk = dd.DD(mu, nu, b, L, sched, err_tol=args.err, stream=stream, debug_flags=2,
                    threads_per_cell=tuned[0] if tuned else args.tpc,
-                   max_cluster_cells=tuned[1] if tuned else args.clusters, mode=0)
+                   max_cluster_cells=tuned[1] if tuned else args.clusters, mode=0, x_newton=args.newton)
         gk.run_schedule()
         gk.reset_profile()
         for _ in range(min(args.steps, 3)):
@@ -516,7 +534,7 @@ def run_cuda(args):
         t = time.perf_counter()
         sched_e2e = syn.paper_schedule(n, L, args.steps)
         h = dd.DD(mu, nu, b, L, sched_e2e, err_tol=args.err, stream=stream, threads_per_cell=args.tpc,
-                  max_cluster_cells=args.clusters, mode=args.mode)
+                  max_cluster_cells=args.clusters, mode=args.mode, x_newton=args.newton)
         h.run_schedule()
         c2, ex2_, ey2 = h.cost()
         rp, col, val = h.basic_marginals()
@@ -532,14 +550,10 @@ def run_cuda(args):
                "seconds": dt}
 
     ttc = None
-    ttc256 = None
+    par256 = None
     if not args.no_ttc:
         ttc = {"plain": time_to_converged(dd, syn, mu, nu, w, args, stream)}
-        gold256 = load_golden("gm256_b4_l3")
-        w256 = syn.WORKLOADS["gm256_b4_l3"]
-        m256, n256 = syn.image_pair(w256, 0)
-        if gold256 is not None:
-            ttc256 = {"plain": time_to_converged(dd, syn, m256, n256, w256, args, stream, gold=gold256)}
+        par256 = {"plain": oracle_parity_256(dd, syn, args, stream)}
         if not args.no_learned:
             # learned warm start: network trained on pairs logged from plain
             # runs on 256² images (5 blobs, 3 levels), compared cell by cell
@@ -563,9 +577,8 @@ def run_cuda(args):
                 res["training_pairs"] = int(sum(x.shape[0] for x in fs))
                 res["warm"] = mode
                 ttc["learned" if mode == 1 else "learned_every_eps"] = res
-            if ttc256 is not None:
-                ttc256["learned"] = time_to_converged(dd, syn, m256, n256, w256, args, stream, warm=1, mlp=net,
-                                                      gold=gold256)
+            if par256["plain"] is not None:
+                par256["learned"] = oracle_parity_256(dd, syn, args, stream, mlp=net, warm=1)
             # the evaluation case of the learned warm start: 512², 6 blobs, the
             # whole schedule with the previous duals and with the prediction
             ev = {}
@@ -575,7 +588,7 @@ def run_cuda(args):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 h = dd.DD(m5, n5, w5.b, w5.levels, syn.paper_schedule(w5.n, w5.levels, 3), err_tol=args.err,
-                          stream=stream, warm=mode, mode=args.mode)
+                          stream=stream, warm=mode, mode=args.mode, x_newton=args.newton)
                 if mode:
                     h.attach_mlp(net)
                 h.run_schedule()
@@ -607,7 +620,7 @@ def run_cuda(args):
                       "autotuned": None if tuned is None else {"threads_per_cell": tuned[0],
                                                                 "max_cluster_cells": tuned[1]}},
            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "time_to_converged": ttc,
-           "time_to_converged_gm256_b4_l3": ttc256,
+           "oracle_parity_gm256_b4_l3": par256,
            "gpu_launches": int(prof.launches), "clocks": clk.summary(),
            "quality": {"cost": cost, "err_x": ex, "err_y": ey, "max_iters_last": st.max_iters,
                        "mean_iters_last": st.mean_iters, "cells_not_converged_last": st.cells_not_converged}}

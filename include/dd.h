@@ -80,10 +80,14 @@ typedef struct {
                             largest predicted work (≥ an eighth of one SM's
                             share) are solved by a cluster of 8 CTAs each;
                             0 = none, −1 = library default (256).              */
-  int32_t x_newton;      /* 1: a cell of at most 64 pixels whose X-iteration
+  int32_t x_newton;      /* ≥ 1: a cell of at most 64 pixels whose X-iteration
                             contracts slowly switches to Newton X-iterations
-                            (same fixed point, same stopping rule); 0: plain
-                            Sinkhorn X-iterations only. Default 1.             */
+                            (same fixed point, same stopping rule): at
+                            iteration 6 when the contraction over iterations
+                            3–6 predicts more than x_newton − 1 further plain
+                            iterations (1: whenever it is slow), later when 16
+                            iterations reduce the error less than tenfold.
+                            0: plain Sinkhorn X-iterations only. Default 1.    */
   int32_t warm;          /* warm start of the cell solves. 0: the duals of the
                             cell's previous solve (Algorithm 2 input u_{C,J}).
                             1: with a network attached (dd_attach_mlp), 8×8
@@ -125,18 +129,21 @@ typedef struct {
                             (DD_ERR_OOM, state untouched; one shot).
                             Bits 0 and 1 turn the graph replay of mode 1
                             off.                                               */
-  int32_t safeguard;     /* 1: a cell whose solve stops at max_iter is solved
-                            again, warm-started from where it stopped, first
-                            at 4·ε and then at ε (the local safeguard of §7.3,
-                            "temporarily increasing ε"); cells still at
-                            max_iter afterwards make the call return
-                            DD_ERR_NOT_CONVERGED after completing it. 0: off
-                            (the half-sweep keeps the cut-off solves). Default
-                            1.                                                 */
+  int32_t safeguard;     /* 1: a cell whose solve stops at max_iter with an
+                            X-error above 10·Err·‖μ_J‖ is solved again,
+                            warm-started from where it stopped, first at 4·ε
+                            and then at ε (the local safeguard of §7.3,
+                            "temporarily increasing ε"). Cells still at
+                            max_iter afterwards (also those just above their
+                            tolerance, at the FP32 floor of their sums) make
+                            the call return DD_ERR_NOT_CONVERGED after
+                            completing it. 0: off (the half-sweep keeps the
+                            cut-off solves). Default 1.                        */
 } dd_options;
 
 /* Counters of the work done by a context since creation or the last
- * dd_reset_profile. Kernel times are filled only with debug_flags bit 1. */
+ * dd_reset_profile (the peaks are maxima over the same period). Kernel times
+ * are filled only with debug_flags bit 1. */
 typedef struct {
   int64_t launches;          /* CUDA kernels launched by the context            */
   int64_t half_sweeps;       /* half-sweeps run                                 */
@@ -161,6 +168,12 @@ typedef struct {
   int64_t rescued_cells;     /* cells re-solved by the safeguard                 */
   int64_t graph_reruns;      /* graph-replayed sweeps whose output did not fit
                                 and that ran again with per-kernel launches      */
+  int64_t peak_nnz;          /* largest number of stored entries of (ν_i)        */
+  int64_t peak_state_bytes;  /* largest device memory of the two CSR buffers of
+                                (ν_i): column, fixed-point value, row pointers   */
+  int64_t peak_work_bytes;   /* largest device memory of the half-sweep buffers
+                                that scale with the entries (gathered supports,
+                                stabilisers, extracted rows)                     */
 } dd_profile;
 
 /* Statistics of the last sweep run by dd_sweep / dd_run_schedule. */
@@ -342,6 +355,15 @@ dd_status dd_relative_pd_gap_host(int32_t n, const double* mu, const double* nu,
  * DD_ERR_ARG for bad sizes, indices or values. */
 dd_status dd_coupling_image_host(int32_t n, int32_t n_basic, const int64_t* row_ptr, const int32_t* col,
                                  const double* val, const float* colours, float* rgb);
+
+/* The colour image of §7.2 for the context's current basic marginals,
+ * computed on the GPU: rgb[3·y + k] = Σ_i colours[3·i + k]·ν_i(y)/ν(y), ν(y) =
+ * Σ_i ν_i(y), black where no ν_i reaches y (the same image as
+ * dd_coupling_image_host, summed with FP64 atomics in an unspecified order).
+ * colours: n_basic × 3 floats (HOST, finite); rgb: n_l² × 3 floats (HOST,
+ * written). Allocates and frees scratch of 40 bytes per pixel; synchronises
+ * the stream. DD_ERR_ARG for NULL or non-finite colours. */
+dd_status dd_coupling_image(dd_ctx* ctx, const float* colours, float* rgb);
 
 /* α = ε·log u_{C,J} of `partition` on every pixel of the current level, up to
  * one additive constant per composite cell (the gauge of Prop. 2.3 (ii)). */

@@ -193,6 +193,19 @@ void state_reserve(dd_ctx* c, int k, int64_t need) {
   c->cap[k] = cap;
 }
 
+// largest entry count and largest device memory of the sparse plan seen so
+// far: both CSR buffers of the basic marginals (column, fixed-point value,
+// row pointers) and the half-sweep's work buffers that scale with the entries
+void track_peaks(dd_ctx* c) {
+  c->prof.peak_nnz = std::max<int64_t>(c->prof.peak_nnz, c->nnz);
+  const int64_t state = (c->cap[0] + c->cap[1]) * (int64_t)(sizeof(int32_t) + sizeof(uint64_t)) +
+                        2 * c->rp_rows * (int64_t)sizeof(int64_t);
+  const int64_t work = c->ws_cap * (int64_t)(2 * sizeof(int32_t) + 2 * sizeof(uint64_t) + 2 * sizeof(float)) +
+                       c->tmp_cap * (int64_t)(sizeof(int32_t) + sizeof(uint64_t));
+  c->prof.peak_state_bytes = std::max<int64_t>(c->prof.peak_state_bytes, state);
+  c->prof.peak_work_bytes = std::max<int64_t>(c->prof.peak_work_bytes, work);
+}
+
 void check_debug(dd_ctx* c, const char* what) {
   if (c->opt.debug_flags & 1) {
     cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -411,8 +424,9 @@ void launch_cta_solves(dd_ctx* c, SweepArgs a) {
   }
 }
 
-// The safeguard of §7.3 for cells whose solve stopped at max_iter: the
-// failed cells are collected on the device and re-solved, warm-started from
+// The safeguard of §7.3 for cells whose solve stopped at max_iter with an
+// X-error above 10·Err·‖μ_J‖: such cells are collected on the device and
+// re-solved, warm-started from
 // the duals their solve ended with, first at a temporarily larger ε
 // (kSafeguardFactor·ε, where the cell problem is smoother and Sinkhorn
 // contracts faster) and then at ε from the result. Each re-solve is a full
@@ -423,7 +437,9 @@ constexpr double kSafeguardFactor = 4.0;
 
 void enqueue_safeguard(dd_ctx* c, const SweepArgs& a, double eps) {
   if (!c->opt.safeguard) return;
-  DD_CUDA(launch_collect_failed(a, c->retry, c->retry_count, c->stream));
+  // every cut-off cell when the main solves are cut off on purpose (debug bit 3)
+  const double min_err = (c->opt.debug_flags & 8) ? 0.0 : 10.0 * c->opt.err_tol;
+  DD_CUDA(launch_collect_failed(a, c->retry, c->retry_count, min_err, c->stream));
   SweepArgs r = a;
   r.order = c->retry;
   r.ncells_dev = c->retry_count;
@@ -546,18 +562,20 @@ void half_sweep(dd_ctx* c, int part, double eps) {
   c->prof.cells += a.ncells;
   c->prof.rescued_cells += c->last_tot.rescued;
   c->unconverged_in_call += c->last_tot.not_converged;
+  track_peaks(c);
   if (c->cell_times && std::getenv("DD_TRACE_TIMES_FILE")) {
     const int nc = a.ncells;
     std::vector<unsigned long long> t(2 * nc);
-    std::vector<int32_t> it(nc), ny(nc), pred(pred_copy);
+    std::vector<int32_t> it(nc), ny(nc), nw(nc), pred(pred_copy);
     pred.resize(nc);
     DD_CUDA(cudaMemcpy(t.data(), c->cell_times, 16 * (size_t)nc, cudaMemcpyDeviceToHost));
     DD_CUDA(cudaMemcpy(it.data(), c->cell_iters, 4 * (size_t)nc, cudaMemcpyDeviceToHost));
     DD_CUDA(cudaMemcpy(ny.data(), c->cell_ny, 4 * (size_t)nc, cudaMemcpyDeviceToHost));
+    DD_CUDA(cudaMemcpy(nw.data(), c->cell_newton, 4 * (size_t)nc, cudaMemcpyDeviceToHost));
     if (FILE* f = std::fopen(std::getenv("DD_TRACE_TIMES_FILE"), "a")) {
       std::fprintf(f, "# half-sweep part %d level %d ncells %d\n", part, c->lev, nc);
       for (int J = 0; J < nc; ++J)
-        std::fprintf(f, "%d %d %d %llu %llu %d\n", J, it[J], ny[J], t[2 * J], t[2 * J + 1], pred[J]);
+        std::fprintf(f, "%d %d %d %llu %llu %d %d\n", J, it[J], ny[J], t[2 * J], t[2 * J + 1], pred[J], nw[J]);
       std::fclose(f);
     }
   }
@@ -817,6 +835,7 @@ void refine(dd_ctx* c) {
   c->anchor[0] = n0;
   c->anchor[1] = n1;
   c->last_part = -1;
+  track_peaks(c);
 }
 
 void enter_level0(dd_ctx* c) {
@@ -863,6 +882,7 @@ void ensure_state(dd_ctx* c) {
   c->cur = 0;
   c->nnz = nnz;
   c->need_init = false;
+  track_peaks(c);
 }
 
 // the level pyramid from the finest level's fixed-point images: coarse
@@ -1172,6 +1192,8 @@ void graph_sweep(dd_ctx* c, double eps) {
   (void)nrows;
   account_half_sweep(c, c->h_tot_g[0], ncA);
   account_half_sweep(c, c->h_tot_g[1], ncB);
+  c->nnz = std::max(c->h_nnz_g[0], c->h_nnz_g[1]);
+  track_peaks(c);
   c->nnz = c->h_nnz_g[1];
   c->last_part = 1;
   c->eps_cur = eps;
@@ -1583,6 +1605,44 @@ dd_status dd_objective(dd_ctx* c, int32_t partition, double eps, double* primal,
     if (primal) *primal = h[0];
     if (gap) *gap = h[1];
     if (gap_abs) *gap_abs = h[2];
+  });
+}
+
+dd_status dd_coupling_image(dd_ctx* c, const float* colours, float* rgb) {
+  return guarded(c, [&] {
+    if (!colours || !rgb) throw DdError{DD_ERR_ARG, "NULL argument"};
+    ensure_state(c);
+    const LevelHost& h = c->lh[c->lev];
+    const int nrows = h.nb * h.nb;
+    const size_t n2 = (size_t)h.n * h.n;
+    for (int i = 0; i < 3 * nrows; ++i)
+      if (!std::isfinite(colours[i])) throw DdError{DD_ERR_ARG, "colours must be finite"};
+    float* dcol = nullptr;
+    double* acc = nullptr;
+    unsigned long long* mass = nullptr;
+    float* drgb = nullptr;
+    try {
+      dev_alloc(dcol, 3 * (size_t)nrows);
+      dev_alloc(acc, 3 * n2);
+      dev_alloc(mass, n2);
+      dev_alloc(drgb, 3 * n2);
+      DD_CUDA(cudaMemcpyAsync(dcol, colours, sizeof(float) * 3 * nrows, cudaMemcpyHostToDevice, c->stream));
+      DD_CUDA(launch_coupling_image(c->rp[c->cur], c->col[c->cur], c->val[c->cur], nrows, (int)n2, dcol, acc, mass,
+                                    drgb, c->stream));
+      DD_CUDA(cudaMemcpyAsync(rgb, drgb, sizeof(float) * 3 * n2, cudaMemcpyDeviceToHost, c->stream));
+      DD_CUDA(cudaStreamSynchronize(c->stream));
+      c->prof.launches += 2;
+    } catch (...) {
+      dev_free(dcol);
+      dev_free(acc);
+      dev_free(mass);
+      dev_free(drgb);
+      throw;
+    }
+    dev_free(dcol);
+    dev_free(acc);
+    dev_free(mass);
+    dev_free(drgb);
   });
 }
 

@@ -170,9 +170,16 @@ struct SweepTotals {
   int rescued;               // cells re-solved by the safeguard
 };
 cudaError_t launch_reduce_cells(const SweepArgs& a, SweepTotals* out_dev, cudaStream_t s);
+// §7.2 image of basic marginals (CSR, nrows rows, Y pixels < n2): rgb[3y+k]
+// = Σ_i colours[3i+k]·ν_i(y) / Σ_i ν_i(y) (0 where no row reaches y); acc
+// (3·n2 doubles) and mass (n2) are scratch
+cudaError_t launch_coupling_image(const int64_t* rp, const int32_t* col, const uint64_t* val, int nrows, int n2,
+                                  const float* colours, double* acc, unsigned long long* mass, float* rgb,
+                                  cudaStream_t s);
 // the cells of the half-sweep in `a` whose solve stopped at max_iter (status
-// bit 0) into list[0..*count), for the safeguard's re-solves
-cudaError_t launch_collect_failed(const SweepArgs& a, int32_t* list, int* count, cudaStream_t s);
+// bit 0) with an X-error above min_err·‖μ_J‖ into list[0..*count), for the
+// safeguard's re-solves
+cudaError_t launch_collect_failed(const SweepArgs& a, int32_t* list, int* count, double min_err, cudaStream_t s);
 cudaError_t launch_y_error(LevelView L, const int64_t* rp, const int32_t* col, const uint64_t* val,
                            int nrows, unsigned long long* scratch, double* out_dev, cudaStream_t s);
 

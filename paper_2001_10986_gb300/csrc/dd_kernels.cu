@@ -344,14 +344,17 @@ constexpr int kMaxHW = 256;
 constexpr int kTraceLen = 512;
 constexpr int kClusterCTAs = 8;    // CTAs sharing one large cell
 constexpr int kMaxBig = 256;       // cells solved by clusters per launch
-constexpr int kStageSmall = 1536;  // support points staged in shared memory per CTA (per-CTA solves)
+constexpr int kStageSmall = 1408;  // support points staged in shared memory per CTA (per-CTA solves)
 constexpr int kStageBig = 3840;    // … and per CTA of a cluster
 constexpr int kNewtonN = 64;       // pixels of a cell that takes Newton steps
 constexpr int kNewtonLd = kNewtonN + 1;
 // shared floats of the Newton step: the 64×65 matrix C, then M; a batch of
 // up to 64 rows z_y; the right-hand side / step
 constexpr int kNewtonZ = kNewtonN * kNewtonLd;
-constexpr int kNewtonB = kNewtonZ + 64 * kNewtonN;
+// row stride of the batch rows z_y: 72 floats puts the 32 lanes of every
+// tensor-core fragment load on 32 distinct shared-memory banks
+constexpr int kZs = kNewtonN + 8;
+constexpr int kNewtonB = kNewtonZ + 64 * kZs;
 constexpr int kNewtonFloats = kNewtonB + kNewtonN + 1;
 // largest |δ| of one Newton step in log u; a longer step is scaled down
 constexpr float kNewtonMaxStep = 4.0f;
@@ -450,45 +453,48 @@ struct ScatterShape {
 // factorised kernel is used (see sinkhorn_cell)
 constexpr float kResMax = 24.0f;
 
-// Σ_y z_y z_yᵀ over a batch of nys rows z_y (64 floats each, at nbuf +
-// kNewtonZ) added into this thread's 4×TC tile of C (stride kNewtonLd at
-// nbuf); 64·64/(4·TC) threads cover C
-template <int TC>
-__device__ __forceinline__ void hess_batch(float* nbuf, int nys, int tid) {
-  constexpr int TJ = kNewtonN / TC;
-  const int ti = tid / TJ, tj = tid % TJ;
+__device__ __forceinline__ uint32_t f2tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// Σ_y z_y z_yᵀ over a batch of nys rows z_y (64 floats each, row stride kZs
+// at nbuf + kNewtonZ; nys a multiple of 8) added into C (stride kNewtonLd at
+// nbuf), on the tensor cores (mma.sync m16n8k8, TF32 inputs, FP32 sums):
+// A = Zᵀ (16 rows of C per tile), B = Z (8 columns per tile). Only the 20
+// tiles of 16×8 that touch the lower triangle are formed (the diagonal 16×16
+// blocks in full); the upper triangle is mirrored after the pass. The Newton
+// step needs its Hessian only approximately: its right-hand side (μ − P_X π)
+// is exact in FP32, so the step keeps the fixed point and the stopping rule,
+// and a Hessian with relative errors of about 1e-3 still contracts fast.
+__device__ __forceinline__ void hess_batch_mma(float* nbuf, int nys, int tid, int nthreads) {
+  const int lane = tid & 31, warp = tid >> 5, nw = nthreads >> 5;
+  const int g = lane >> 2, t = lane & 3;
   const float* Z = nbuf + kNewtonZ;
-  unsigned long long C2[2 * TC];
-#pragma unroll
-  for (int q = 0; q < 2 * TC; ++q) C2[q] = 0ull;
-#pragma unroll 2
-  for (int yy = 0; yy < nys; ++yy) {
-    const float4 zi = *reinterpret_cast<const float4*>(Z + yy * kNewtonN + 4 * ti);
-    unsigned long long Jp[TC / 2];
-#pragma unroll
-    for (int c4 = 0; c4 < TC / 4; ++c4) {
-      const float4 zj = *reinterpret_cast<const float4*>(Z + yy * kNewtonN + TC * tj + 4 * c4);
-      Jp[2 * c4] = pk2(zj.x, zj.y);
-      Jp[2 * c4 + 1] = pk2(zj.z, zj.w);
+  for (int p = warp; p < 20; p += nw) {
+    // tile p → row block mt (16 rows), column block nt ≤ 2·mt + 1 (8 columns)
+    const int mt = p < 2 ? 0 : p < 6 ? 1 : p < 12 ? 2 : 3;
+    const int nt = p - mt * (mt + 1);
+    float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+    for (int k0 = 0; k0 < nys; k0 += 8) {
+      const float* z0 = Z + (k0 + t) * kZs;
+      const float* z4 = Z + (k0 + t + 4) * kZs;
+      const uint32_t a0 = f2tf32(z0[16 * mt + g]), a1 = f2tf32(z0[16 * mt + g + 8]);
+      const uint32_t a2 = f2tf32(z4[16 * mt + g]), a3 = f2tf32(z4[16 * mt + g + 8]);
+      const uint32_t b0 = f2tf32(z0[8 * nt + g]), b1 = f2tf32(z4[8 * nt + g]);
+      asm volatile(
+          "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+          "{%0,%1,%2,%3};\n"
+          : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
+          : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
     }
-    const float zr[4] = {zi.x, zi.y, zi.z, zi.w};
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const unsigned long long I2 = pk2(zr[r], zr[r]);
-#pragma unroll
-      for (int q = 0; q < TC / 2; ++q) C2[r * (TC / 2) + q] = fma2(I2, Jp[q], C2[r * (TC / 2) + q]);
-    }
+    float* cp = nbuf + (16 * mt + g) * kNewtonLd + 8 * nt + 2 * t;
+    cp[0] += c0;
+    cp[1] += c1;
+    cp[8 * kNewtonLd] += c2;
+    cp[8 * kNewtonLd + 1] += c3;
   }
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int q = 0; q < TC / 2; ++q) {
-      float c0, c1;
-      upk2(C2[r * (TC / 2) + q], c0, c1);
-      float* cp = nbuf + (4 * ti + r) * kNewtonLd + TC * tj + 2 * q;
-      cp[0] += c0;
-      cp[1] += c1;
-    }
 }
 
 // H×W: the cell's shape in pixels. CS > 1: a cluster of CS CTAs shares one
@@ -566,6 +572,7 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
                          NT / GJ <= 64;
   bool newton = false, newton_off = false;
   float ep_before = 0.f, e_mark = 0.f;
+  const int newton_min = a.newton - 1;   // see the X-iteration's Newton decision
 
   // This CTA's share of the support: all of it, or a contiguous chunk per
   // cluster rank. When it fits, the share is staged once in shared memory as
@@ -898,11 +905,15 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
           }
           return group_sum<GM>(s0 + s1);
         };
-        float s = fact_sum(Gs);
-        if (!(s > 1e-30f && s < 1e30f)) {
-          // stabiliser too far off for this y: restart it from the running maximum
-          Gs = restab(true);
+        // one call site, so that the factor arrays stay in registers; a
+        // second attempt when the stabiliser is too far off for this y,
+        // restarted from the running maximum
+        float s;
+#pragma unroll 1
+        for (int attempt = 0;; ++attempt) {
           s = fact_sum(Gs);
+          if ((s > 1e-30f && s < 1e30f) || attempt == 1) break;
+          Gs = restab(true);
           absorb = true;
         }
         // v = ν/s with IEEE division: the iteration map itself uses correctly
@@ -947,7 +958,7 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
           // the rows z_y have no entries beyond the cell's pixels
           if constexpr (H * W < kNewtonN) {
             constexpr int pad = kNewtonN - H * W;
-            for (int q = tid; q < 64 * pad; q += NT) nbuf[kNewtonZ + (q / pad) * kNewtonN + H * W + q % pad] = 0.f;
+            for (int q = tid; q < 64 * pad; q += NT) nbuf[kNewtonZ + (q / pad) * kZs + H * W + q % pad] = 0.f;
           }
         }
       }
@@ -1021,11 +1032,14 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
           upk2(S2, s0, s1);
           return group_sum<G>(s0 + s1);
         };
-        float s = kernel_row(Gs);
-        if (!(s > 1e-30f && s < 1e30f)) {
-          // stabiliser too far off for this y: restart it from the running maximum
-          Gs = row_max(true);
+        // one call site (see the split pass); a second attempt from the
+        // running maximum when the stabiliser is too far off for this y
+        float s;
+#pragma unroll 1
+        for (int attempt = 0;; ++attempt) {
           s = kernel_row(Gs);
+          if ((s > 1e-30f && s < 1e30f) || attempt == 1) break;
+          Gs = row_max(true);
           absorb = true;
         }
         const float v = valid ? nuy / s : 0.f;
@@ -1040,13 +1054,22 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
             const float w = valid ? sqrtf(nuy) / s : 0.f;
             const unsigned long long W2 = pk2(w, w);
             unsigned long long* zrow =
-                reinterpret_cast<unsigned long long*>(nbuf + kNewtonZ + slot * kNewtonN + gid * PJ);
+                reinterpret_cast<unsigned long long*>(nbuf + kNewtonZ + slot * kZs + gid * PJ);
 #pragma unroll
             for (int q = 0; q < RPT * WP; ++q) zrow[q] = mul2(mul2(P2[q], U2[q]), W2);
             __syncthreads();
-            if (NT == 256) hess_batch<4>(nbuf, YS, tid);
-            else hess_batch<8>(nbuf, YS, tid);
+            hess_batch_mma(nbuf, YS, tid, NT);
             __syncthreads();
+          }
+        }
+      }
+      if constexpr (kNewtonShape) {
+        if (newton) {
+          // the upper triangle of C outside the diagonal 16×16 blocks from the
+          // lower one (read after the barrier that ends the pass)
+          for (int q = tid; q < kNewtonN * kNewtonN; q += NT) {
+            const int i = q / kNewtonN, j = q % kNewtonN;
+            if (j >= 16 * ((i >> 4) + 1)) nbuf[i * kNewtonLd + j] = nbuf[j * kNewtonLd + i];
           }
         }
       }
@@ -1183,7 +1206,13 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     }
     if (!newton_step && newton_ok && !newton_off && !newton) {
       const bool near = ep < kNewtonNear * muJ;   // Newton steps only close to the solution
-      if (it == 6 && rho6 > 0.75f && near) newton = true;
+      // at iteration 6 only when the plain iteration, contracting by rho6 per
+      // iteration, would need more than newton_min further iterations:
+      // ln(tol/ep) < newton_min·ln(rho6) (a Newton step costs as much as
+      // several plain iterations)
+      if (it == 6 && rho6 > 0.75f && near &&
+          (newton_min <= 0 || logf(tol / ep) < (float)newton_min * logf(rho6)))
+        newton = true;
       if (it > 6 && (it & 15) == 0) {
         if (ep > 0.1f * e_mark && near) newton = true;
         e_mark = ep;
@@ -1266,82 +1295,149 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   }
 
   // ---- epilogue: final plan → fractions per basic cell, transport cost ----
-  // (the mapping of the unsplit pass: G threads per support point)
-  int arow[RPT];
-#pragma unroll
-  for (int r = 0; r < RPT; ++r) arow[r] = gid * RPT + r;
-  float Fr[RPT * W], ur[RPT * W];
-#pragma unroll
-  for (int r = 0; r < RPT; ++r)
-#pragma unroll
-    for (int c = 0; c < W; ++c) {
-      const bool ok = arow[r] < g.H;
-      Fr[r * W + c] = ok ? sm.F[arow[r] * W + c] : kNegBig;
-      ur[r * W + c] = ok ? sm.u[arow[r] * W + c] : 0.f;
-    }
+  // The plan of the last Y-iteration, π(x,y) = ν(y)·p(x,y)/Σ_x p(x,y) with
+  // p = K̃·u: per support point the fractions of its mass in each basic cell
+  // and the cost Σ_x p·|x−y|²/Σ_x p (in pixel² units).
   const int nbas = g.nbr * g.nbc;
-  const int bsh = __ffs(L.b) - 1;  // b is a power of two
   const int64_t tbase = 4 * off;
   double cost_acc = 0.0;
-  for (int k0 = 0; k0 < ny; k0 += YS) {
-    const int k = k0 + slot;
-    const bool valid = k < ny;
-    const int kk = valid ? k : 0;
-    const int32_t e = a.ws_eta[off + kk];
-    const int er = eta_r(e), ec = eta_c(e);
-    const float Gs = a.ws_g[off + kk];
-    float Cc[W], Dcc[W];
-#pragma unroll
-    for (int c = 0; c < W; ++c) {
-      const float t = (float)(c - ec);
-      Cc[c] = kappa * t * t;
-      const float w = (float)(Dc + c - ec);
-      Dcc[c] = w * w;
+  // one support point's results: fixed-point fractions into the extraction
+  // buffer (the largest takes the rounding remainder), cost into cost_acc
+  auto emit = [&](int k, int er, int ec, const float (&q)[4], float s, float cst) {
+    const uint64_t nuq = a.ws_nu[off + k];
+    const float S = q[0] + q[1] + q[2] + q[3];
+    int imax = 0;
+    for (int i = 1; i < nbas; ++i)
+      if (q[i] > q[imax]) imax = i;
+    uint64_t rest = nuq;
+    const int y = (anc.x + er) * L.n + (anc.y + ec);
+    const float invS = S > 0.f ? 1.0f / S : 0.f;
+    for (int i = 0; i < nbas; ++i) {
+      if (i == imax) continue;
+      const uint64_t vq = __umul64hi(nuq, frac_to_u64(q[i] * invS));
+      rest -= vq;
+      a.tmp_val[tbase + (int64_t)i * ny + k] = vq;
+      a.tmp_col[tbase + (int64_t)i * ny + k] = y;
     }
-    float q[4] = {0.f, 0.f, 0.f, 0.f};
-    float cst = 0.f, s = 0.f;
+    a.tmp_val[tbase + (int64_t)imax * ny + k] = rest;
+    a.tmp_col[tbase + (int64_t)imax * ny + k] = y;
+    const double nuf = (double)nuq * (1.0 / kFixOne);
+    if (s > 0.f) cost_acc += (double)cst * (nuf / (double)s);
+  };
+  if (fact) {
+    // the separable split of the last pass (F, u and 2^res·u unchanged since
+    // its prepare): p = 2^res·u(x) · ρ_y(r) · γ_y(c), so a point costs H + W
+    // exponentials. Basic rows split at br, basic columns at bc.
+    const int br = g.nbr == 2 ? L.b : H, bc = g.nbc == 2 ? L.b : W;
+    for (int k0 = 0; k0 < ny; k0 += YSM) {
+      const int k = k0 + slm;
+      const bool valid = k < ny;
+      const int kk = valid ? k : 0;
+      const int32_t e = a.ws_eta[off + kk];
+      const int er = eta_r(e), ec = eta_c(e);
+      const float Gs = a.ws_g[off + kk];
+      float ce[W], GA[W], GD[W];
+      float mc = kNegBig;
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      const float tr = (float)(arow[r] - er);
-      const float Ra = Gs - kappa * tr * tr;
-      const float wr = (float)(Dr + arow[r] - er);
-      const float Drr = wr * wr;
-      const int kb_r = (arow[r] >> bsh) * g.nbc;
+      for (int j = 0; j < WP; ++j) {
+        float f0, f1;
+        upk2(FC2[j], f0, f1);
+        const float t0 = (float)(2 * j) - (float)ec, t1 = (float)(2 * j + 1) - (float)ec;
+        ce[2 * j] = f0 - kappa * t0 * t0;
+        ce[2 * j + 1] = f1 - kappa * t1 * t1;
+        mc = fmaxf(mc, fmaxf(ce[2 * j], ce[2 * j + 1]));
+      }
 #pragma unroll
       for (int c = 0; c < W; ++c) {
-        const float p = ex2(Fr[r * W + c] + Ra - Cc[c]) * ur[r * W + c];
-        s += p;
-        cst = fmaf(p, Drr + Dcc[c], cst);
-        if (arow[r] < g.H) {
-          const int kb = kb_r + (c >> bsh);
-          if (kb == 0) q[0] += p; else if (kb == 1) q[1] += p; else if (kb == 2) q[2] += p; else q[3] += p;
+        GA[c] = ex2(ce[c] - mc);
+        const float w = (float)(Dc + c - ec);
+        GD[c] = GA[c] * (w * w);
+      }
+      float q[4] = {0.f, 0.f, 0.f, 0.f};
+      float s = 0.f, cst = 0.f;
+#pragma unroll
+      for (int r = 0; r < RM; ++r) {
+        const int row = row0 + r;
+        const float tr = (float)(row - er);
+        const float rho = ex2(FR[r] + Gs + mc - kappa * tr * tr);
+        float t0 = 0.f, t1 = 0.f, tD = 0.f;
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+          const float wt = sm.WT[row * W + c];
+          if (c < bc) t0 = fmaf(wt, GA[c], t0);
+          else t1 = fmaf(wt, GA[c], t1);
+          tD = fmaf(wt, GD[c], tD);
+        }
+        const float wr = (float)(Dr + row - er);
+        const float t = t0 + t1;
+        const int i0 = (row >= br ? 1 : 0) * g.nbc;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) q[i] += i == i0 ? rho * t0 : (i == i0 + 1 ? rho * t1 : 0.f);
+        s = fmaf(rho, t, s);
+        cst = fmaf(rho, fmaf(wr * wr, t, tD), cst);
+      }
+      s = group_sum<GM>(s);
+      cst = group_sum<GM>(cst);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) q[i] = group_sum<GM>(q[i]);
+      if (valid && gm == 0) emit(k, er, ec, q, s, cst);
+    }
+  } else {
+    // unsplit: G threads per support point (the mapping of the unsplit pass),
+    // one exponential per kernel entry
+    int arow[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) arow[r] = gid * RPT + r;
+    float Fr[RPT * W], ur[RPT * W];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        const bool ok = arow[r] < g.H;
+        Fr[r * W + c] = ok ? sm.F[arow[r] * W + c] : kNegBig;
+        ur[r * W + c] = ok ? sm.u[arow[r] * W + c] : 0.f;
+      }
+    const int bsh = __ffs(L.b) - 1;  // b is a power of two
+    for (int k0 = 0; k0 < ny; k0 += YS) {
+      const int k = k0 + slot;
+      const bool valid = k < ny;
+      const int kk = valid ? k : 0;
+      const int32_t e = a.ws_eta[off + kk];
+      const int er = eta_r(e), ec = eta_c(e);
+      const float Gs = a.ws_g[off + kk];
+      float Cc[W], Dcc[W];
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        const float t = (float)(c - ec);
+        Cc[c] = kappa * t * t;
+        const float w = (float)(Dc + c - ec);
+        Dcc[c] = w * w;
+      }
+      float q[4] = {0.f, 0.f, 0.f, 0.f};
+      float cst = 0.f, s = 0.f;
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const float tr = (float)(arow[r] - er);
+        const float Ra = Gs - kappa * tr * tr;
+        const float wr = (float)(Dr + arow[r] - er);
+        const float Drr = wr * wr;
+        const int kb_r = (arow[r] >> bsh) * g.nbc;
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+          const float p = ex2(Fr[r * W + c] + Ra - Cc[c]) * ur[r * W + c];
+          s += p;
+          cst = fmaf(p, Drr + Dcc[c], cst);
+          if (arow[r] < g.H) {
+            const int kb = kb_r + (c >> bsh);
+            if (kb == 0) q[0] += p; else if (kb == 1) q[1] += p; else if (kb == 2) q[2] += p; else q[3] += p;
+          }
         }
       }
-    }
-    s = group_sum<G>(s);
-    cst = group_sum<G>(cst);
+      s = group_sum<G>(s);
+      cst = group_sum<G>(cst);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) q[i] = group_sum<G>(q[i]);
-    if (valid && gid == 0) {
-      const uint64_t nuq = a.ws_nu[off + k];
-      const float S = q[0] + q[1] + q[2] + q[3];
-      int imax = 0;
-      for (int i = 1; i < nbas; ++i)
-        if (q[i] > q[imax]) imax = i;
-      uint64_t rest = nuq;
-      const int y = (anc.x + er) * L.n + (anc.y + ec);
-      const float invS = S > 0.f ? 1.0f / S : 0.f;
-      for (int i = 0; i < nbas; ++i) {
-        if (i == imax) continue;
-        const uint64_t vq = __umul64hi(nuq, frac_to_u64(q[i] * invS));
-        rest -= vq;
-        a.tmp_val[tbase + (int64_t)i * ny + k] = vq;
-        a.tmp_col[tbase + (int64_t)i * ny + k] = y;
-      }
-      a.tmp_val[tbase + (int64_t)imax * ny + k] = rest;
-      a.tmp_col[tbase + (int64_t)imax * ny + k] = y;
-      const double nuf = (double)nuq * (1.0 / kFixOne);
-      if (s > 0.f) cost_acc += (double)cst * (nuf / (double)s);
+      for (int i = 0; i < 4; ++i) q[i] = group_sum<G>(q[i]);
+      if (valid && gid == 0) emit(k, er, ec, q, s, cst);
     }
   }
   __syncthreads();
@@ -1478,7 +1574,14 @@ __device__ void solve_cell(const SweepArgs& a, int J, SinkSmem& sm, int rank, fl
 __global__ void __maxnreg__(168) k_sinkhorn(SweepArgs a) {
   __shared__ SinkSmem sm;
   __shared__ int s_pos, s_stop;
+  // the arguments, once per CTA in shared memory: the cell solve takes them
+  // by reference, and a reference to the kernel parameter itself would give
+  // every thread a copy in local memory, which does not fit in the L1 that
+  // the shared-memory carve-out leaves
+  __shared__ SweepArgs s_args;
   extern __shared__ float4 ys_small[];
+  if (threadIdx.x == 0) s_args = a;
+  __syncthreads();
   const int nbig = a.nbig ? *a.nbig : 0;
   const int ncells = a.ncells_dev ? *a.ncells_dev : a.ncells;
   // one cell per CTA, or (persistent) cells taken in launch order from a
@@ -1505,7 +1608,8 @@ __global__ void __maxnreg__(168) k_sinkhorn(SweepArgs a) {
     const int J = a.order ? a.order[pos] : pos;
     if (a.cell_times && threadIdx.x == 0) a.cell_times[2 * J] = globaltimer();
     // dynamic shared memory: the staged support points, then the Newton buffer
-    solve_cell<1, kMaxHW / 32>(a, J, sm, 0, ys_small, kStageSmall, reinterpret_cast<float*>(ys_small + kStageSmall));
+    solve_cell<1, kMaxHW / 32>(s_args, J, sm, 0, ys_small, kStageSmall,
+                               reinterpret_cast<float*>(ys_small + kStageSmall));
     if (a.cell_times && threadIdx.x == 0) a.cell_times[2 * J + 1] = globaltimer();
     __syncthreads();     // the cell's shared memory is free for the next one
   }
@@ -1515,15 +1619,18 @@ __global__ void __maxnreg__(168) k_sinkhorn(SweepArgs a) {
 // launch order (largest predicted work)
 __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256, 2) k_sinkhorn_cluster(SweepArgs a) {
   __shared__ SinkSmem sm;
+  __shared__ SweepArgs s_args;   // see k_sinkhorn
   const int c = blockIdx.x / kClusterCTAs;
   if (c >= *a.nbig) return;   // uniform over the cluster
   const int rank = (int)cg::this_cluster().block_rank();
   const int J = a.order[c];
   if (*a.err_flag & (4 | 8)) return;
   extern __shared__ float4 ys_big[];
+  if (threadIdx.x == 0) s_args = a;
+  __syncthreads();
   if (a.cell_times && threadIdx.x == 0 && rank == 0) a.cell_times[2 * J] = globaltimer();
   // dynamic shared memory: the staged support points, then the Newton buffer
-  solve_cell<kClusterCTAs, 1>(a, J, sm, rank, ys_big, kStageBig, reinterpret_cast<float*>(ys_big + kStageBig));
+  solve_cell<kClusterCTAs, 1>(s_args, J, sm, rank, ys_big, kStageBig, reinterpret_cast<float*>(ys_big + kStageBig));
   if (a.cell_times && threadIdx.x == 0 && rank == 0) a.cell_times[2 * J + 1] = globaltimer();
 }
 
@@ -1771,7 +1878,7 @@ __global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals*
   }
 }
 
-__global__ void __launch_bounds__(1024) k_collect_failed(SweepArgs a, int32_t* list, int* count) {
+__global__ void __launch_bounds__(1024) k_collect_failed(SweepArgs a, int32_t* list, int* count, double min_err) {
   __shared__ int s_n;
   if (*a.err_flag) {   // an earlier step failed: the statuses are not this half-sweep's
     if (threadIdx.x == 0) *count = 0;
@@ -1779,8 +1886,17 @@ __global__ void __launch_bounds__(1024) k_collect_failed(SweepArgs a, int32_t* l
   }
   if (threadIdx.x == 0) s_n = 0;
   __syncthreads();
-  for (int J = threadIdx.x; J < a.ncells; J += blockDim.x)
-    if ((a.cell_status[J] & 7) == 1) list[atomicAdd(&s_n, 1)] = J;   // stopped at max_iter, finite
+  // stopped at max_iter with a finite result, and still far from the
+  // tolerance: an X-error above min_err·‖μ_J‖ (a cell that stalls just above
+  // its tolerance is at the FP32 floor of its sums and gains nothing)
+  for (int J = threadIdx.x; J < a.ncells; J += blockDim.x) {
+    if ((a.cell_status[J] & 7) != 1) continue;
+    const CellGeom g = cell_geom(a.part, J, a.L.nb, a.L.b);
+    uint64_t m = 0;
+    for (int kr = 0; kr < g.nbr; ++kr)
+      for (int kc = 0; kc < g.nbc; ++kc) m += a.L.M_q[(g.bi0 + kr) * a.L.nb + g.bj0 + kc];
+    if (a.cell_errx[J] > min_err * ((double)m * (1.0 / kFixOne))) list[atomicAdd(&s_n, 1)] = J;
+  }
   __syncthreads();
   if (threadIdx.x == 0) *count = s_n;
 }
@@ -2254,8 +2370,50 @@ cudaError_t launch_init_product(LevelView L, int64_t* rp, int32_t* col, uint64_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_collect_failed(const SweepArgs& a, int32_t* list, int* count, cudaStream_t s) {
-  k_collect_failed<<<1, 1024, 0, s>>>(a, list, count);
+// §7.2 colour image of the basic marginals: every entry ν_i(y) adds
+// colour_i·ν_i(y) to pixel y (FP64 atomics) and ν_i(y) to its mass (64-bit
+// fixed point, exact); the image is the mass-weighted mean colour
+__global__ void __launch_bounds__(256) k_image_scatter(const int64_t* rp, const int32_t* col, const uint64_t* val,
+                                                       int nrows, const float* colours, double* acc,
+                                                       unsigned long long* mass) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (int)((gridDim.x * (int64_t)blockDim.x) >> 5);
+  for (int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); i < nrows; i += warps) {
+    const float c0 = colours[3 * i], c1 = colours[3 * i + 1], c2 = colours[3 * i + 2];
+    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += 32) {
+      const int y = col[e];
+      const uint64_t v = val[e];
+      const double m = (double)v * (1.0 / kFixOne);
+      atomicAdd(acc + 3 * (int64_t)y, (double)c0 * m);
+      atomicAdd(acc + 3 * (int64_t)y + 1, (double)c1 * m);
+      atomicAdd(acc + 3 * (int64_t)y + 2, (double)c2 * m);
+      atomicAdd(mass + y, (unsigned long long)v);
+    }
+  }
+}
+
+__global__ void k_image_finish(const double* acc, const unsigned long long* mass, int n2, float* rgb) {
+  for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n2; y += gridDim.x * blockDim.x) {
+    const double m = (double)mass[y] * (1.0 / kFixOne);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) rgb[3 * (int64_t)y + k] = m > 0.0 ? (float)(acc[3 * (int64_t)y + k] / m) : 0.f;
+  }
+}
+
+cudaError_t launch_coupling_image(const int64_t* rp, const int32_t* col, const uint64_t* val, int nrows, int n2,
+                                  const float* colours, double* acc, unsigned long long* mass, float* rgb,
+                                  cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * 3 * (size_t)n2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(mass, 0, sizeof(unsigned long long) * (size_t)n2, s);
+  if (e != cudaSuccess) return e;
+  k_image_scatter<<<std::max(1, std::min((nrows + 7) / 8, 152 * 16)), 256, 0, s>>>(rp, col, val, nrows, colours,
+                                                                                   acc, mass);
+  k_image_finish<<<std::max(1, std::min((n2 + 255) / 256, 152 * 16)), 256, 0, s>>>(acc, mass, n2, rgb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_collect_failed(const SweepArgs& a, int32_t* list, int* count, double min_err, cudaStream_t s) {
+  k_collect_failed<<<1, 1024, 0, s>>>(a, list, count, min_err);
   return cudaGetLastError();
 }
 

@@ -45,7 +45,8 @@ class dd_profile(C.Structure):
                 ("solve_ms", C.c_double), ("gather_launches", C.c_int64), ("gather_ms", C.c_double),
                 ("cluster_ms", C.c_double), ("kernel_evals", C.c_double), ("sinkhorn_iters", C.c_double), ("cells", C.c_int64),
                 ("newton_steps", C.c_int64), ("hessian_fma", C.c_double), ("learned_cells", C.c_int64),
-                ("compared_cells", C.c_int64), ("rescued_cells", C.c_int64), ("graph_reruns", C.c_int64)]
+                ("compared_cells", C.c_int64), ("rescued_cells", C.c_int64), ("graph_reruns", C.c_int64),
+                ("peak_nnz", C.c_int64), ("peak_state_bytes", C.c_int64), ("peak_work_bytes", C.c_int64)]
 
 
 class DDError(RuntimeError):
@@ -95,6 +96,7 @@ _lib.dd_interpolate_dual_host.argtypes = [C.c_int32, _P, _P]
 _lib.dd_relative_pd_gap_host.argtypes = [C.c_int32, _P, _P, C.c_double, _P, _P, _P, _P,
                                          C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
 _lib.dd_coupling_image_host.argtypes = [C.c_int32, C.c_int32, _P, _P, _P, _P, _P]
+_lib.dd_coupling_image.argtypes = [_P, _P, _P]
 _lib.dd_objective.argtypes = [_P, C.c_int32, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
                               C.POINTER(C.c_double)]
 _lib.dd_get_info.argtypes = [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -127,7 +129,7 @@ for _f in ("dd_create", "dd_set_state", "dd_half_sweep", "dd_refine", "dd_save",
            "dd_reset_profile", "dd_get_cell_stats", "dd_mlp_create", "dd_mlp_get_params", "dd_mlp_set_params",
            "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step", "dd_attach_mlp", "dd_cell_training_pairs",
            "dd_autotune", "dd_objective", "dd_glue_potential", "dd_glue_duals_host",
-           "dd_interpolate_dual_host", "dd_relative_pd_gap_host", "dd_coupling_image_host"):
+           "dd_interpolate_dual_host", "dd_relative_pd_gap_host", "dd_coupling_image_host", "dd_coupling_image"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", "dd_refine", "dd_save", "dd_load", "dd_sweep",
@@ -137,7 +139,7 @@ EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", 
             "dd_mlp_get_params", "dd_mlp_set_params", "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step",
             "dd_attach_mlp", "dd_cell_training_pairs", "dd_autotune", "dd_objective", "dd_glue_potential",
             "dd_glue_duals_host", "dd_interpolate_dual_host", "dd_relative_pd_gap_host",
-            "dd_coupling_image_host")
+            "dd_coupling_image_host", "dd_coupling_image")
 
 
 def _check(ctx, st, stats=None):
@@ -370,6 +372,18 @@ def dd_coupling_image_host(n, basic_marginals, colours):
     return out
 
 
+def dd_coupling_image(ctx, colours):
+    """§7.2 image of the current basic marginals, computed on the GPU;
+    colours: n_basic × 3. Returns n_l × n_l × 3 float32."""
+    _, nl, nbasic, _, _ = dd_get_info(ctx)
+    cl = np.ascontiguousarray(colours, dtype=np.float32).reshape(-1)
+    if cl.size != 3 * nbasic:
+        raise DDError(DD_ERR_ARG, "colours must hold 3 values per basic cell")
+    out = np.empty(3 * nl * nl, dtype=np.float32)
+    _check(ctx, _lib.dd_coupling_image(ctx, cl.ctypes.data, out.ctypes.data))
+    return out.reshape(nl, nl, 3)
+
+
 def write_ppm(path, rgb):
     """Write an n×m×3 image with values in [0, 1] as a binary PPM file."""
     img = (np.clip(np.asarray(rgb, dtype=np.float64), 0.0, 1.0) * 255.0 + 0.5).astype(np.uint8)
@@ -563,12 +577,15 @@ class DD:
     def objective(self, partition=-1, eps=0.0):
         return dd_objective(self.ctx, partition, eps)
 
-    def coupling_image(self, colours=None):
-        """§7.2 colour image (n_l×n_l×3) of the current basic marginals; the
-        default colours are a checkerboard over the basic cells."""
+    def coupling_image(self, colours=None, device=True):
+        """§7.2 colour image (n_l×n_l×3) of the current basic marginals, on
+        the GPU (device=True) or on the host from the downloaded marginals;
+        the default colours are a checkerboard over the basic cells."""
         _, nl, nbasic, _, _ = dd_get_info(self.ctx)
         if colours is None:
             colours = checkerboard_colours(int(round(nbasic ** 0.5)))
+        if device:
+            return dd_coupling_image(self.ctx, colours)
         return dd_coupling_image_host(nl, self.basic_marginals(), colours)
 
     def relative_pd_gap(self, mu, nu):

@@ -9,7 +9,9 @@ of synthetic Gaussian mixtures, and reports the rows of the table:
 * entries of (ν_i): the maximum on the finest layer (at its largest ε) and
   the final number;
 * relative primal-dual gap of eq. RelPDGap (glued duals, `DD.relative_pd_gap`);
-* L1 marginal errors of X and Y (`dd_cost`).
+* L1 marginal errors of X and Y (`dd_cost`);
+* beside the table: peak device memory of the sparse plan and the cells that
+  the local safeguard of §7.3 re-solved.
 
 Usage (on a machine with a GPU):
 
@@ -51,10 +53,12 @@ def run_one(n: int, pair: int, *, blobs: int = 6, floor: float = 1e-4, b: int = 
         seconds = time.perf_counter() - t0
         _, err_x, err_y = g.cost()
         rel, _, _ = g.relative_pd_gap(mu, nu)
+        prof = g.profile()
     finally:
         g.close()
     return {"time_s": seconds, "entries_max": nnz_max_finest, "entries_final": nnz_final,
-            "relative_pd_gap": rel, "l1_error_x": err_x, "l1_error_y": err_y}
+            "relative_pd_gap": rel, "l1_error_x": err_x, "l1_error_y": err_y,
+            "peak_state_bytes": prof.peak_state_bytes, "safeguard_cells": prof.rescued_cells}
 
 
 def _mean_std(xs):

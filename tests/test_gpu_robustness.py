@@ -17,9 +17,10 @@ pytestmark = pytest.mark.gpu
 
 PLAN_TOL = 1e-5
 COST_TOL = 1e-6
-# ε halved from 0.05 to 0.00625, two sweeps each: every cell solve starts
-# warm, so none needs more than max_iter iterations (a cold start at a small
-# ε from the product coupling can)
+# ε halved from 0.05 to 0.00625, two sweeps each, and Err = 1e-6: every cell
+# solve starts warm and its tolerance lies above the FP32 floor of the
+# X-marginal error, so none needs more than max_iter iterations (a cold start
+# at a small ε, or Err = 1e-7, can leave a few cells at max_iter)
 WARM_SCHEDULE = [(0.05, 2, 0), (0.025, 2, 0), (0.0125, 2, 0), (0.00625, 2, 0)]
 
 
@@ -74,7 +75,7 @@ def test_safeguard_rescues_every_forced_failure(lib):
     mu = syn.gaussian_mixture(32, 3, 50)
     nu = syn.gaussian_mixture(32, 3, 51)
     sched = WARM_SCHEDULE
-    g = lib.DD(mu, nu, 4, 1, sched, err_tol=1e-7, max_iter=5000, debug_flags=8)
+    g = lib.DD(mu, nu, 4, 1, sched, err_tol=1e-6, max_iter=5000, debug_flags=8)
     st = g.run_schedule(strict=True)
     prof = g.profile()
     rp, col, val = g.basic_marginals()
@@ -89,7 +90,7 @@ def test_safeguard_rescues_every_forced_failure(lib):
     want = odd.rows_to_dense(ref.rows, 32 * 32)
     assert np.abs(got - want).sum() / want.sum() < PLAN_TOL
     assert abs(cost - ref.history[-1][3].cost) / ref.history[-1][3].cost < COST_TOL
-    assert ey < 1e-12
+    assert ey < 1e-10          # only the mass that Truncate dropped (≤ 1e-15 per entry)
 
 
 def test_cells_at_max_iter_are_reported(lib):
@@ -121,7 +122,7 @@ def test_graph_overflow_reruns_with_per_kernel_launches(lib):
     sched = WARM_SCHEDULE + [(0.00625, 3, 0)]
     out = {}
     for mode, flags in ((0, 0), (1, 4)):
-        g = lib.DD(mu, nu, 4, 1, sched, err_tol=1e-7, max_iter=5000, mode=mode, debug_flags=flags)
+        g = lib.DD(mu, nu, 4, 1, sched, err_tol=1e-6, max_iter=5000, mode=mode, debug_flags=flags)
         g.run_schedule(strict=True)
         out[mode] = (_state(g), g.profile())
         g.close()
@@ -136,14 +137,14 @@ def test_injected_workspace_allocation_failure(lib):
     mu = syn.gaussian_mixture(32, 3, 56)
     nu = syn.gaussian_mixture(32, 3, 57)
     sched = WARM_SCHEDULE
-    g = lib.DD(mu, nu, 4, 1, sched, err_tol=1e-7, max_iter=5000, debug_flags=16)
+    g = lib.DD(mu, nu, 4, 1, sched, err_tol=1e-6, max_iter=5000, debug_flags=16)
     with pytest.raises(lib.DDError) as e:
         g.sweep(1)
     assert e.value.status == lib.DD_ERR_OOM and "injected" in str(e.value)
     g.run_schedule(strict=True)
     got = _state(g)
     g.close()
-    r = lib.DD(mu, nu, 4, 1, sched, err_tol=1e-7, max_iter=5000)
+    r = lib.DD(mu, nu, 4, 1, sched, err_tol=1e-6, max_iter=5000)
     r.run_schedule(strict=True)
     _assert_same_state(got, _state(r))
     r.close()
