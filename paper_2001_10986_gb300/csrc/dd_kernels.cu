@@ -1762,7 +1762,15 @@ __global__ void __launch_bounds__(kScanTile) k_compact(const int32_t* cnt, const
                                                        int64_t cap_out, int nrows, int* err_flag) {
   __shared__ int iws[32];
   __shared__ int64_t s_start[kScanTile];
-  if (*err_flag) return;   // an earlier step failed: leave the output rows alone
+  if (*err_flag) {
+    // an earlier step failed (for example the other half-sweep of a
+    // graph-replayed sweep overflowed its output): leave the output rows
+    // alone, and mark the compaction as skipped so that k_copy_rows, which
+    // copies on after an overflow of its own compaction (bit 8 alone), does
+    // not write rows of a stale layout into this output
+    if (threadIdx.x == 0) atomicOr(err_flag, 64);
+    return;
+  }
   const int i = blockIdx.x * kScanTile + threadIdx.x;
   const int c = i < nrows ? cnt[i] : 0;
   int tot;
