@@ -28,7 +28,11 @@ from . import synthetic as syn
 
 
 def run(dual_refine: int = 0, mlp=None, workload: str = "gm2048_b4_l5", err: float = 1e-6,
-        max_final: int = 60, mode: int = 1) -> dict:
+        max_final: int = 60, mode: int = 1, start_cells: float = 0.0) -> dict:
+    """start_cells: the coarsest level starts at ε = 2·(start_cells·Δ₀)² and
+    halves down to 2Δ₀² (synthetic.paper_schedule's eps_start; 0 keeps its
+    default 2·(1/8)², which at a 128² coarsest level makes the first plans
+    nearly dense)."""
     import torch
     from . import dd
     w = syn.WORKLOADS[workload]
@@ -36,7 +40,10 @@ def run(dual_refine: int = 0, mlp=None, workload: str = "gm2048_b4_l5", err: flo
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g = dd.DD(mu, nu, w.b, w.levels, syn.paper_schedule(w.n, w.levels, 1), err_tol=err, mode=mode,
+    d0 = 2.0 ** (w.levels - 1) / w.n
+    sched = (syn.paper_schedule(w.n, w.levels, 1, eps_start=2.0 * (start_cells * d0) ** 2) if start_cells > 0
+             else syn.paper_schedule(w.n, w.levels, 1))
+    g = dd.DD(mu, nu, w.b, w.levels, sched, err_tol=err, mode=mode,
               dual_refine=dual_refine, warm=1 if mlp is not None else 0, stream=stream)
     if mlp is not None:
         g.attach_mlp(mlp)
@@ -68,6 +75,7 @@ def run(dual_refine: int = 0, mlp=None, workload: str = "gm2048_b4_l5", err: flo
     g.close()
     tail = ms[-3:] if ms else [float("nan")]
     return {"workload": workload, "dual_refine": dual_refine, "learned": mlp is not None,
+            "eps_start": sched[0][0], "schedule_steps": len(sched),
             "seconds_schedule": t_sched, "seconds_to_converged": seconds, "converged": done, "final_sweeps": k,
             "cells_not_converged_after_schedule": nc_sched, "cells_not_converged_last": st.cells_not_converged,
             "rescued_cells_schedule": p_sched.rescued_cells, "rescued_cells": p.rescued_cells,
@@ -98,12 +106,16 @@ def main(argv=None):
     ap.add_argument("--dual-refine", type=int, nargs="+", default=[0, 1])
     ap.add_argument("--learned", action="store_true")
     ap.add_argument("--workload", default="gm2048_b4_l5")
+    ap.add_argument("--start-cells", type=float, default=0.0)
+    ap.add_argument("--max-final", type=int, default=60)
     args = ap.parse_args(argv)
     net = train_network() if args.learned else None
     for dr in args.dual_refine:
-        print(json.dumps(run(dr, workload=args.workload)), flush=True)
+        print(json.dumps(run(dr, workload=args.workload, start_cells=args.start_cells, max_final=args.max_final)),
+              flush=True)
         if net is not None:
-            print(json.dumps(run(dr, mlp=net, workload=args.workload)), flush=True)
+            print(json.dumps(run(dr, mlp=net, workload=args.workload, start_cells=args.start_cells,
+                                 max_final=args.max_final)), flush=True)
     if net is not None:
         net.close()
 
