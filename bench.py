@@ -42,10 +42,11 @@ SM_MAX_MHZ = 2070.0
 #    support point (the profile counts 64² per point).
 FMA_PER_ENTRY = 2.0
 HESS_SYM = 65.0 / 128.0
-# DRAM bytes per launch of the two cell-solve kernels from the last ncu
-# capture of the current kernels (profiles/k_sinkhorn_gm512_b4.md: 56.6 MB at
-# 512², scaled by the 4× cell count to 1024²); None if not captured
-SOLVE_TRAFFIC_BYTES = 4 * 56.6e6
+# DRAM bytes per launch of the per-CTA cell-solve kernel k_sinkhorn, from an
+# ncu capture of the current kernel (dram__bytes_read.sum + write.sum: 66.6 MB
+# for the A and 61.4 MB for the B half-sweep at 512², averaged) scaled by the
+# 4× cell count to 1024²; the cluster kernel beside it is not included
+SOLVE_TRAFFIC_BYTES = 4 * 64.0e6
 
 
 def parse():
@@ -517,7 +518,7 @@ def run_cuda(args):
     peak = NUM_SM * FP32_LANES_PER_SM * 2.0 * SM_MAX_MHZ * 1e6 / 1e12
     roofline = {"bound": "alu", "kernel": "k_sinkhorn + k_sinkhorn_cluster (one half-sweep's cell solves)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": SOLVE_TRAFFIC_BYTES,
+                "traffic": SOLVE_TRAFFIC_BYTES, "traffic_kernel": "k_sinkhorn (per-CTA solves)",
                 "peak_source": f"FP32 FMA: {NUM_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz "
                                "(unit counts and maximum clock)",
                 "fma_per_launch": fma, "kernel_entries_per_launch": prof_k.kernel_evals / launches,
