@@ -377,11 +377,15 @@ dd_status dd_get_info(dd_ctx* ctx, int32_t* level, int32_t* n_level, int32_t* n_
 
 /* Per composite cell of the last half-sweep (in the cell order of its
  * partition: row-major over the grid of composite cells): Sinkhorn
- * iterations, final X-marginal L1 error, support size N_y of ν_cell and a
- * status word (bit 0: stopped at max_iter, bit 1: non-finite). Any array may
- * be NULL; cap is their length; *n_cells receives the number of cells. */
+ * iterations, final X-marginal L1 error, support size N_y of ν_cell, a
+ * status word (bit 0: stopped at max_iter, bit 1: non-finite), the transport
+ * cost ⟨c, π_J⟩ of the cell's plan (FP64; the terms of dd_cost's cost) and
+ * whether its main solve ran on a cluster of CTAs (1) or one CTA (0). Any
+ * array may be NULL; cap is their length; *n_cells receives the number of
+ * cells. */
 dd_status dd_get_cell_stats(dd_ctx* ctx, int32_t* iters, double* err_x, int32_t* n_y,
-                            int32_t* status, int32_t cap, int32_t* n_cells);
+                            int32_t* status, double* cost, int32_t* cluster, int32_t cap,
+                            int32_t* n_cells);
 
 /* Copy the context's counters to *out. */
 dd_status dd_get_profile(dd_ctx* ctx, dd_profile* out);

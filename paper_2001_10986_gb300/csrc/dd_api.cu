@@ -1682,12 +1682,25 @@ dd_status dd_get_info(dd_ctx* c, int32_t* level, int32_t* n_level, int32_t* n_ba
 }
 
 dd_status dd_get_cell_stats(dd_ctx* c, int32_t* iters, double* err_x, int32_t* n_y, int32_t* status,
-                            int32_t cap, int32_t* n_cells) {
+                            double* cost, int32_t* cluster, int32_t cap, int32_t* n_cells) {
   return guarded(c, [&] {
     if (c->last_part < 0) throw DdError{DD_ERR_STATE, "no half-sweep has run at this level"};
     const int nc = num_cells(c->last_part, c->lh[c->lev].nb);
     if (n_cells) *n_cells = nc;
-    if ((iters || err_x || n_y || status) && cap < nc) throw DdError{DD_ERR_CAPACITY, "buffer too small"};
+    if ((iters || err_x || n_y || status || cost || cluster) && cap < nc)
+      throw DdError{DD_ERR_CAPACITY, "buffer too small"};
+    if (cost) DD_CUDA(cudaMemcpyAsync(cost, c->cell_cost, 8 * (size_t)nc, cudaMemcpyDeviceToHost, c->stream));
+    if (cluster) {
+      // the first *nbig cells of the launch order went to clusters
+      std::vector<int32_t> order((size_t)nc);
+      int nbig = 0;
+      DD_CUDA(cudaMemcpyAsync(order.data(), c->order, 4 * (size_t)nc, cudaMemcpyDeviceToHost, c->stream));
+      DD_CUDA(cudaMemcpyAsync(&nbig, c->nbig, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      DD_CUDA(cudaStreamSynchronize(c->stream));
+      for (int J = 0; J < nc; ++J) cluster[J] = 0;
+      for (int p = 0; p < std::min(nbig, nc); ++p)
+        if (order[p] >= 0 && order[p] < nc) cluster[order[p]] = 1;
+    }
     if (iters) DD_CUDA(cudaMemcpyAsync(iters, c->cell_iters, 4 * (size_t)nc, cudaMemcpyDeviceToHost, c->stream));
     if (err_x) DD_CUDA(cudaMemcpyAsync(err_x, c->cell_errx, 8 * (size_t)nc, cudaMemcpyDeviceToHost, c->stream));
     if (n_y) DD_CUDA(cudaMemcpyAsync(n_y, c->cell_ny, 4 * (size_t)nc, cudaMemcpyDeviceToHost, c->stream));

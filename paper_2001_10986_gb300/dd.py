@@ -104,7 +104,7 @@ _lib.dd_get_info.argtypes = [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.P
 _lib.dd_solve_cell_noalloc.argtypes = [_P, C.c_int32, C.c_double, C.c_int32, _P, _P, _P, C.c_double,
                                        C.c_double, C.c_int32, C.c_double, _P, _P, _P]
 _lib.dd_solve_cell_noalloc.restype = C.c_int
-_lib.dd_get_cell_stats.argtypes = [_P, _P, _P, _P, _P, C.c_int32, C.POINTER(C.c_int32)]
+_lib.dd_get_cell_stats.argtypes = [_P, _P, _P, _P, _P, _P, _P, C.c_int32, C.POINTER(C.c_int32)]
 _lib.dd_get_profile.argtypes = [_P, C.POINTER(dd_profile)]
 _lib.dd_reset_profile.argtypes = [_P]
 _lib.dd_destroy.argtypes = [_P]
@@ -400,16 +400,19 @@ def dd_get_duals(ctx, partition):
 
 
 def dd_get_cell_stats(ctx):
-    """Returns dict of per-cell arrays (iters, err_x, n_y, status) of the last half-sweep."""
+    """Returns dict of per-cell arrays (iters, err_x, n_y, status, cost,
+    cluster) of the last half-sweep."""
     nc = C.c_int32()
-    _check(ctx, _lib.dd_get_cell_stats(ctx, None, None, None, None, 0, C.byref(nc)))
+    _check(ctx, _lib.dd_get_cell_stats(ctx, None, None, None, None, None, None, 0, C.byref(nc)))
     it = np.zeros(nc.value, np.int32)
     ex = np.zeros(nc.value, np.float64)
     ny = np.zeros(nc.value, np.int32)
     st = np.zeros(nc.value, np.int32)
+    co = np.zeros(nc.value, np.float64)
+    cl = np.zeros(nc.value, np.int32)
     _check(ctx, _lib.dd_get_cell_stats(ctx, it.ctypes.data, ex.ctypes.data, ny.ctypes.data, st.ctypes.data,
-                                       nc.value, C.byref(nc)))
-    return {"iters": it, "err_x": ex, "n_y": ny, "status": st}
+                                       co.ctypes.data, cl.ctypes.data, nc.value, C.byref(nc)))
+    return {"iters": it, "err_x": ex, "n_y": ny, "status": st, "cost": co, "cluster": cl}
 
 
 def dd_solve_cell_noalloc(mu, b, spacing, n_y, y_row, y_col, nu, eps, err_tol, max_iter, trunc,

@@ -190,6 +190,67 @@ def test_sampled_cells_full_size(lib):
     assert num / den < PLAN_TOL, num / den
 
 
+def test_sampled_cells_full_size_with_cluster_cells(lib):
+    # 1024², 4×4 cells: a feasible synthetic state in which three basic cells
+    # send their mass to wide bumps, so that their composite cells get
+    # supports large enough for the 8-CTA cluster solver; one A half-sweep at
+    # ε = 2h², compared on every cluster-solved cell and a random sample of
+    # the others: basic marginals (relative L1) and each cell's transport cost
+    n, b = 1024, 4
+    eps = 2.0 / n**2
+    mu, _ = syn.image_pair("gm1024_b4", 0)
+    _, rp0, col0, val0 = syn.feasible_state(mu, b, seed=7, radius_px=3)
+    _, rpw, colw, valw = syn.feasible_state(mu, b, seed=7, radius_px=26, blur_px=8.0)
+    nb = n // b
+    wide = {100 * nb + 100, 180 * nb + 62, 40 * nb + 200}
+    rows = []
+    for i in range(nb * nb):
+        rp, col, val = (rpw, colw, valw) if i in wide else (rp0, col0, val0)
+        rows.append((col[rp[i]:rp[i + 1]].astype(np.int64), val[rp[i]:rp[i + 1]]))
+    nu = np.zeros(n * n)
+    for c, v in rows:
+        nu[c] += v
+    rp = np.zeros(nb * nb + 1, dtype=np.int64)
+    rp[1:] = np.cumsum([c.size for c, _ in rows])
+    col = np.concatenate([c for c, _ in rows]).astype(np.int32)
+    val = np.concatenate([v for _, v in rows])
+    g = lib.DD(mu, nu.reshape(n, n), b, 1, [(eps, 1, 0)], err_tol=1e-6)
+    g.set_state(rp, col, val)
+    g.half_sweep(0, eps)
+    grp, gcol, gval = g.basic_marginals()
+    cs = g.cell_stats()
+    g.close()
+    clusters = np.flatnonzero(cs["cluster"]).tolist()
+    wide_cells = sorted({(i // nb // 2) * (nb // 2) + (i % nb) // 2 for i in wide})
+    assert set(wide_cells) <= set(clusters), (wide_cells, clusters[:10])
+    prob = odd.GridProblem(mu / mu.sum(), nu.reshape(n, n) / nu.sum(), b, 1.0 / n)
+    orows = odd.rows_from_csr(rp, col, val / nu.sum())
+    rng = np.random.default_rng(5)
+    cells = sorted(set(rng.choice(len(prob.parts["A"]), 24, replace=False).tolist()) | set(clusters[:8]))
+    plans = {}
+    new_rows, _ = odd.half_sweep(prob, "A", orows, np.zeros(n * n), eps, odd.Params(err=1e-10, max_iter=100000),
+                                 cells=cells, plans=plans)
+    num = den = 0.0
+    got_cost = ref_cost = 0.0
+    for jn in cells:
+        for i in prob.parts["A"][jn]:
+            c_ref, v_ref = new_rows[i]
+            c_gpu, v_gpu = gcol[grp[i]:grp[i + 1]], gval[grp[i]:grp[i + 1]]
+            u = np.union1d(c_ref, c_gpu)
+            a = np.zeros(u.size); a[np.searchsorted(u, c_gpu)] = v_gpu
+            e = np.zeros(u.size); e[np.searchsorted(u, c_ref)] = v_ref
+            num += np.abs(a - e).sum()
+            den += e.sum()
+        X, ycols, P = plans[jn]
+        cj = float((prob.cost(X, ycols) * P).sum())
+        # one cell solved to Err = 1e-6 moves its cost by up to about that much
+        assert abs(cs["cost"][jn] - cj) / cj < 10 * COST_TOL, (jn, cs["cost"][jn], cj)
+        got_cost += cs["cost"][jn]
+        ref_cost += cj
+    assert num / den < PLAN_TOL, num / den
+    assert abs(got_cost - ref_cost) / ref_cost < COST_TOL
+
+
 def test_set_state_rejects_unsorted(lib):
     n, b = 16, 4
     mu = syn.gaussian_mixture(n, 2, 70)
