@@ -101,7 +101,8 @@ typedef struct {
                             from the last partition's duals refined cell by
                             cell (first-order, within each coarse cell).
                             1 (hybrid): A as 0; B from the glued coarse dual
-                            of both partitions (§6.3, on the host) interpolated
+                            of both partitions (§6.3, on the GPU; on the host
+                            beyond 256 A cells per side) interpolated
                             linearly (§6.4). Default 0.                        */
   int32_t mode;          /* 0: every half-sweep as separate launches with a host
                             check in between. 1: per-CTA cell solves as one
@@ -127,6 +128,10 @@ typedef struct {
                             bit 4: the first growth of the half-sweep
                             workspace fails as a failed cudaMalloc would
                             (DD_ERR_OOM, state untouched; one shot).
+                            bit 5: the hybrid refinement (dual_refine = 1)
+                            glues on the host at every size, as it does
+                            beyond 256 A cells per side (for comparing the
+                            two paths).
                             Bits 0 and 1 turn the graph replay of mode 1
                             off.                                               */
   int32_t safeguard;     /* 1: a cell whose solve stops at max_iter with an
@@ -278,8 +283,8 @@ dd_status dd_get_plan(dd_ctx* ctx, double trunc, int64_t* nnz, int64_t* row_ptr,
  *             depend on the per-cell constants of the duals beyond
  *             (‖ν_cell‖ − ‖μ_J‖)·constant/ε, the mass lost to Truncate.
  * Entries are FP32 exponentials (as in dd_get_plan), logs and sums FP64. The
- * global primal-dual gap of eq. RelPDGap needs the glued duals of §6.3 and
- * is not computed. Allocates (and frees) 16 bytes per composite cell of
+ * global primal-dual gap of eq. RelPDGap needs the glued duals of §6.3:
+ * dd_relative_pd_gap. Allocates (and frees) 16 bytes per composite cell of
  * device memory; synchronises the stream; leaves the state and the
  * statistics of the last half-sweep as they were. Any output pointer may be
  * NULL.
@@ -287,6 +292,48 @@ dd_status dd_get_plan(dd_ctx* ctx, double trunc, int64_t* nnz, int64_t* row_ptr,
  * DD_ERR_ARG for another partition or a non-positive eps. */
 dd_status dd_objective(dd_ctx* ctx, int32_t partition, double eps, double* primal, double* gap,
                        double* gap_abs);
+
+/* The glued X-dual of §6.3 ("Estimating the primal-dual gap") of the
+ * context's current level, computed on the GPU from the duals of both
+ * partitions at the current ε: per basic cell i the μ-weighted means s±_i =
+ * log ⨍_i exp(±(α_A − α_B)/ε) dμ; every ordered pair (i, i') of distinct
+ * basic cells of one B cell is an edge between the A cells holding them with
+ * log q = s⁺_i + s⁻_{i'}; the potential V on the A cells minimises
+ * Σ_e ((V(j1) − V(j2)) + log q_e)² with Σ V = 0 (conjugate gradients,
+ * Jacobi-preconditioned, relative residual 1e-13, at most 100 000
+ * iterations); α̂ = α_A + ε·V[A cell]. The same construction as
+ * dd_glue_duals_host, whose results it reproduces up to rounding.
+ * Outputs (host, each may be NULL): alpha_hat (n_l² FP64, absolute frame as
+ * dd_get_duals, 0 on pixels without mass), V ((n_l/2b)² FP64, row-major over
+ * the A cells), *cg_iters, *rel_residual. Allocates and frees device scratch
+ * (about 16 bytes per pixel); synchronises the stream; leaves the state as it
+ * was. DD_ERR_CAPACITY when the A cells exceed 256 per side (the CG runs on
+ * one cluster of 8 CTAs that holds at most 256 rows of 256 cells);
+ * DD_ERR_NOT_CONVERGED (outputs written) when the CG stopped at its
+ * iteration limit. */
+dd_status dd_glue_duals(dd_ctx* ctx, double* alpha_hat, double* V, int32_t* cg_iters, double* rel_residual);
+
+/* eq. RelPDGap on the GPU for the coupling of the last partition (the one
+ * dd_get_plan and dd_objective reconstruct: support X_J × supp ν_cell per
+ * cell, entries from the stored duals and one Y-iteration) and the glued
+ * X-dual α̂ of dd_glue_duals: with K = e^{−c/ε}·μ⊗ν (masses normalised to 1),
+ *   *primal = KL(π|K) − ‖K‖ (dd_objective's primal),
+ *   v̂(y) = 1/S(y), S(y) = Σ_{x: π(x,y) > 0} û(x) μ(x) e^{−c(x,y)/ε}, the Y-dual
+ *            that maximises J(û, ·) for the kernel restricted to supp π,
+ *   *gap = KL(π|K) − J(û, v̂) = primal − (⟨μ, log û⟩ − ⟨ν, log S⟩ − Σ_{y
+ *            covered} ν(y)),
+ *   *rel = gap / primal.
+ * The same quantities as dd_relative_pd_gap_host on dd_get_plan's coupling
+ * (with no truncation) and dd_glue_duals_host's α̂. Logs and sums FP64,
+ * exponentials of the inner sums FP32 after an FP64 shift by their maximum
+ * (the precision of the coupling's entries); S is accumulated with atomic
+ * additions, so the last digits may vary from call to call. Outputs may be
+ * NULL. Allocates and frees device scratch (about 40 bytes per pixel and 8
+ * per stored entry); synchronises the stream; leaves the state as it was.
+ * DD_ERR_STATE before the first half-sweep of a level or when a pixel with
+ * ν > 0 carries no entry of the coupling; DD_ERR_CAPACITY and
+ * DD_ERR_NOT_CONVERGED as dd_glue_duals. */
+dd_status dd_relative_pd_gap(dd_ctx* ctx, double* rel, double* gap, double* primal);
 
 /* The least-squares step of the dual gluing (§6.3, "Estimating the
  * primal-dual gap"): on a graph of n_nodes vertices (the cells of partition

@@ -1,6 +1,6 @@
 """Builds the CUDA library libddot.so in-tree for sm_103a with nvcc.
 
-The two translation units are compiled in parallel and linked into
+The translation units are compiled in parallel and linked into
 paper_2001_10986_gb300/_build/libddot.so (static CUDA runtime).
 """
 from __future__ import annotations
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libddot.so")
-SOURCES = ["dd_kernels.cu", "dd_api.cu", "dd_noalloc.cu", "dd_mlp.cu", "dd_glue.cu"]
+SOURCES = ["dd_kernels.cu", "dd_api.cu", "dd_noalloc.cu", "dd_mlp.cu", "dd_glue.cu", "dd_gluing.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

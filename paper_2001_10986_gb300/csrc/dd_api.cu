@@ -600,6 +600,47 @@ void half_sweep(dd_ctx* c, int part, double eps) {
   }
 }
 
+// device buffers freed when the holder goes out of scope
+struct Scratch {
+  std::vector<void*> ptrs;
+  template <typename T>
+  T* get(size_t count) {
+    T* p = nullptr;
+    dev_alloc(p, count);
+    ptrs.push_back(p);
+    return p;
+  }
+  Scratch() = default;
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  ~Scratch() {
+    for (void* p : ptrs) dev_free(p);
+  }
+};
+
+constexpr double kGlueTol = 1e-13;     // relative residual of the gluing's CG
+constexpr int kGlueMaxIter = 100000;
+
+// the glued X-dual of §6.3 of the current level on the GPU from the duals of
+// both partitions: α̂ (n² doubles) and the potential V ((nb/2)² doubles) into
+// device buffers; fill_massless as launch_glue_apply. Returns the CG report.
+GlueInfo glue_device(dd_ctx* c, double eps, int fill_massless, double* ahat, double* V) {
+  const LevelHost& h = c->lh[c->lev];
+  Scratch s;
+  double* sp = s.get<double>((size_t)h.nb * h.nb);
+  double* sm = s.get<double>((size_t)h.nb * h.nb);
+  GlueInfo* info = s.get<GlueInfo>(1);
+  const LevelView L = view(c);
+  DD_CUDA(launch_glue_potential(L, c->alpha[0], c->anchor[0], c->alpha[1], c->anchor[1], eps, kGlueTol,
+                                kGlueMaxIter, sp, sm, V, info, c->stream));
+  DD_CUDA(launch_glue_apply(L, c->alpha[0], c->anchor[0], V, eps, fill_massless, ahat, c->stream));
+  GlueInfo hi{};
+  DD_CUDA(cudaMemcpyAsync(&hi, info, sizeof(GlueInfo), cudaMemcpyDeviceToHost, c->stream));
+  DD_CUDA(cudaStreamSynchronize(c->stream));
+  c->prof.launches += 3;
+  return hi;
+}
+
 // move the state one level finer (§6.4)
 // α = ε·log u of partition `part` at the current level in the absolute frame
 // (the conversion of dd_get_duals), FP64 on the host
@@ -713,10 +754,21 @@ void upload_duals(dd_ctx* c, int lev, int part, const double* al, float* alpha, 
 void refine(dd_ctx* c) {
   ensure_state(c);
   const int lc = c->lev, lf = lc + 1;
-  // hybrid dual refinement: the coarse duals of both partitions glued on the
-  // host (§6.3) before the coarse buffers go away
+  // hybrid dual refinement: the coarse duals of both partitions glued (§6.3)
+  // before the coarse buffers go away — on the GPU (pixels without mass
+  // filled by the affine fit of their A cell, see below), or on the host for
+  // grids of A cells beyond the one-cluster CG
   std::vector<double> glued;
-  if (c->opt.dual_refine == 1 && c->eps_cur > 0.0) {
+  Scratch keep;
+  double* glued_dev = nullptr;
+  const bool glue_on_host = (c->opt.debug_flags & 32) != 0 || c->lh[lc].nb / 2 > glue_max_cells_per_side();
+  if (c->opt.dual_refine == 1 && c->eps_cur > 0.0 && !glue_on_host) {
+    const LevelHost& h0 = c->lh[lc];
+    glued_dev = keep.get<double>((size_t)h0.n * h0.n);
+    double* V = keep.get<double>((size_t)(h0.nb / 2) * (h0.nb / 2));
+    const GlueInfo gi = glue_device(c, c->eps_cur, 1, glued_dev, V);
+    if (!gi.converged) throw DdError{DD_ERR_NOT_CONVERGED, "dual gluing at the refinement did not converge"};
+  } else if (c->opt.dual_refine == 1 && c->eps_cur > 0.0) {
     const LevelHost& h0 = c->lh[lc];
     const std::vector<double> aA = host_duals(c, 0), aB = host_duals(c, 1);
     std::vector<double> mu((size_t)h0.n * h0.n);
@@ -811,7 +863,12 @@ void refine(dd_ctx* c) {
   c->prof.launches += 7;
   check_debug(c, "refine_duals");
   DD_CUDA(cudaStreamSynchronize(c->stream));
-  if (!glued.empty()) {
+  if (glued_dev) {
+    // B starts from the glued coarse dual interpolated linearly (§6.4)
+    DD_CUDA(launch_glue_frames(hc.n, glued_dev, F, 1, a1, n1, c->stream));
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    c->prof.launches += 1;
+  } else if (!glued.empty()) {
     // B starts from the glued coarse dual interpolated linearly (§6.4)
     std::vector<double> af((size_t)hf.n * hf.n);
     const dd_status st = dd_interpolate_dual_host(hc.n, glued.data(), af.data());
@@ -1605,6 +1662,74 @@ dd_status dd_objective(dd_ctx* c, int32_t partition, double eps, double* primal,
     if (primal) *primal = h[0];
     if (gap) *gap = h[1];
     if (gap_abs) *gap_abs = h[2];
+  });
+}
+
+dd_status dd_glue_duals(dd_ctx* c, double* alpha_hat, double* V, int32_t* cg_iters, double* rel_residual) {
+  return guarded(c, [&] {
+    ensure_state(c);
+    const LevelHost& h = c->lh[c->lev];
+    const int na = h.nb / 2;
+    if (na > glue_max_cells_per_side())
+      throw DdError{DD_ERR_CAPACITY, "more A cells per side than the GPU gluing holds (" +
+                                         std::to_string(glue_max_cells_per_side()) + ")"};
+    const size_t n2 = (size_t)h.n * h.n;
+    Scratch s;
+    double* ahat = s.get<double>(n2);
+    double* Vd = s.get<double>((size_t)na * na);
+    const GlueInfo gi = glue_device(c, c->eps_cur, 0, ahat, Vd);
+    if (alpha_hat) DD_CUDA(cudaMemcpy(alpha_hat, ahat, 8 * n2, cudaMemcpyDeviceToHost));
+    if (V) DD_CUDA(cudaMemcpy(V, Vd, 8 * (size_t)na * na, cudaMemcpyDeviceToHost));
+    if (cg_iters) *cg_iters = gi.iters;
+    if (rel_residual) *rel_residual = gi.rel_residual;
+    if (!gi.converged) throw DdError{DD_ERR_NOT_CONVERGED, "the gluing's CG did not reach its tolerance"};
+  });
+}
+
+dd_status dd_relative_pd_gap(dd_ctx* c, double* rel, double* gap, double* primal) {
+  return guarded(c, [&] {
+    if (c->last_part < 0) throw DdError{DD_ERR_STATE, "no half-sweep has run at this level"};
+    ensure_state(c);
+    const LevelHost& h = c->lh[c->lev];
+    const int na = h.nb / 2;
+    if (na > glue_max_cells_per_side())
+      throw DdError{DD_ERR_CAPACITY, "more A cells per side than the GPU gluing holds (" +
+                                         std::to_string(glue_max_cells_per_side()) + ")"};
+    const size_t n2 = (size_t)h.n * h.n;
+    Scratch s;
+    double* ahat = s.get<double>(n2);
+    double* Vd = s.get<double>((size_t)na * na);
+    const GlueInfo gi = glue_device(c, c->eps_cur, 0, ahat, Vd);
+    if (!gi.converged) throw DdError{DD_ERR_NOT_CONVERGED, "the gluing's CG did not reach its tolerance"};
+    // the coupling of the last partition (as dd_get_plan and dd_objective
+    // reconstruct it): gather, the primal score, then the dual terms
+    ensure_sweep_capacity(c, c->nnz);
+    DD_CUDA(cudaMemsetAsync(c->ws_counter, 0, sizeof(unsigned long long), c->stream));
+    DD_CUDA(cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream));
+    const SweepArgs a = sweep_args(c, c->last_part, c->eps_cur);
+    DD_CUDA(launch_gather(a, c->stream));
+    double* cell_obj = s.get<double>(2 * (size_t)std::max(a.ncells, 1));
+    double* out3 = s.get<double>(3);
+    DD_CUDA(launch_objective(a, cell_obj, out3, c->stream));
+    constexpr int kParts = 4 * 152;
+    double* tws = s.get<double>((size_t)std::max<int64_t>(c->ws_cap, 1));
+    long long* Mkey = s.get<long long>(n2);
+    double* St = s.get<double>(n2);
+    double* part = s.get<double>(4 * (size_t)kParts);
+    double* out4 = s.get<double>(4);
+    DD_CUDA(launch_gap(a, ahat, tws, Mkey, St, part, kParts, out4, c->stream));
+    double h3[3], h4[4];
+    DD_CUDA(cudaMemcpyAsync(h3, out3, sizeof(h3), cudaMemcpyDeviceToHost, c->stream));
+    DD_CUDA(cudaMemcpyAsync(h4, out4, sizeof(h4), cudaMemcpyDeviceToHost, c->stream));
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    c->prof.launches += 8;
+    if (h4[3] > 0.0)
+      throw DdError{DD_ERR_STATE, std::to_string((long long)h4[3]) + " pixels with ν > 0 carry no entry of the coupling"};
+    const double pr = h3[0];
+    const double g = pr - (h4[0] + h4[1] - h4[2]);
+    if (primal) *primal = pr;
+    if (gap) *gap = g;
+    if (rel) *rel = g / pr;
   });
 }
 

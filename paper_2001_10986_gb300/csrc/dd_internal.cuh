@@ -223,6 +223,37 @@ cudaError_t launch_cell_targets(const SweepArgs& a, const int2* fanchor, const i
 cudaError_t launch_warm_compare(const SweepArgs& a, const float* pred, const int2* fanchor, const int32_t* ok,
                          cudaStream_t s);
 
+// ---- dual gluing (§6.3) and eq. RelPDGap (dd_gluing.cu) ----
+struct GlueInfo {
+  int iters;            // CG iterations run
+  int converged;        // 1 if the relative residual reached the tolerance
+  double rel_residual;  // ‖L V + Dᵀ log q‖ / ‖Dᵀ log q‖ at the end
+};
+// largest side na of the A-cell grid that the one-cluster CG holds
+int glue_max_cells_per_side();
+// s±_i of every basic cell (sp, sm: nb² doubles) from the duals of both
+// partitions, then the potential V (na² doubles, mean zero) of the gluing
+// graph by preconditioned CG to ‖residual‖ ≤ tol·‖rhs‖ or max_iter
+// iterations; cudaErrorInvalidValue when na exceeds glue_max_cells_per_side()
+cudaError_t launch_glue_potential(LevelView L, const float* alpha_A, const int2* anchor_A, const float* alpha_B,
+                                  const int2* anchor_B, double eps, double tol, int max_iter, double* sp,
+                                  double* sm, double* V, GlueInfo* info, cudaStream_t s);
+// α̂ = α_A + ε·V[A cell] (absolute frame, n² doubles); pixels without mass
+// get 0, or with fill_massless the affine fit of their A cell's α̂
+cudaError_t launch_glue_apply(LevelView L, const float* alpha_A, const int2* anchor_A, const double* V, double eps,
+                              int fill_massless, double* alpha_hat, cudaStream_t s);
+// α̂ (n_c² doubles) interpolated linearly onto level F (n_f = 2·n_c) and
+// written into the cell frames (α̃, anchors) of partition fpart of F
+cudaError_t launch_glue_frames(int n_c, const double* alpha_c, LevelView F, int fpart, float* alpha_f,
+                               int2* anchor_f, cudaStream_t s);
+// eq. RelPDGap's dual terms for the coupling of the half-sweep in `a`
+// (after its gather) and the glued X-dual α̂: out[4] = {Σ_x μ α̂/ε,
+// −Σ_y ν log S(y), Σ_{y: S > 0} ν(y), #{y: ν(y) > 0, S(y) = 0}}; tws (one
+// double per support entry), Mkey and St (n² each) and part (4·nparts) are
+// scratch
+cudaError_t launch_gap(const SweepArgs& a, const double* alpha_hat, double* tws, long long* Mkey, double* St,
+                       double* part, int nparts, double* out, cudaStream_t s);
+
 }  // namespace ddk
 
 struct dd_mlp;

@@ -99,6 +99,8 @@ _lib.dd_coupling_image_host.argtypes = [C.c_int32, C.c_int32, _P, _P, _P, _P, _P
 _lib.dd_coupling_image.argtypes = [_P, _P, _P]
 _lib.dd_objective.argtypes = [_P, C.c_int32, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
                               C.POINTER(C.c_double)]
+_lib.dd_glue_duals.argtypes = [_P, _P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+_lib.dd_relative_pd_gap.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
 _lib.dd_get_info.argtypes = [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                              C.POINTER(C.c_double), C.POINTER(C.c_int64)]
 _lib.dd_solve_cell_noalloc.argtypes = [_P, C.c_int32, C.c_double, C.c_int32, _P, _P, _P, C.c_double,
@@ -129,7 +131,8 @@ for _f in ("dd_create", "dd_set_state", "dd_half_sweep", "dd_refine", "dd_save",
            "dd_reset_profile", "dd_get_cell_stats", "dd_mlp_create", "dd_mlp_get_params", "dd_mlp_set_params",
            "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step", "dd_attach_mlp", "dd_cell_training_pairs",
            "dd_autotune", "dd_objective", "dd_glue_potential", "dd_glue_duals_host",
-           "dd_interpolate_dual_host", "dd_relative_pd_gap_host", "dd_coupling_image_host", "dd_coupling_image"):
+           "dd_interpolate_dual_host", "dd_relative_pd_gap_host", "dd_coupling_image_host", "dd_coupling_image",
+           "dd_glue_duals", "dd_relative_pd_gap"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", "dd_refine", "dd_save", "dd_load", "dd_sweep",
@@ -139,7 +142,7 @@ EXPORTED = ("dd_options_default", "dd_create", "dd_set_state", "dd_half_sweep", 
             "dd_mlp_get_params", "dd_mlp_set_params", "dd_mlp_forward", "dd_mlp_loss_grad", "dd_mlp_train_step",
             "dd_attach_mlp", "dd_cell_training_pairs", "dd_autotune", "dd_objective", "dd_glue_potential",
             "dd_glue_duals_host", "dd_interpolate_dual_host", "dd_relative_pd_gap_host",
-            "dd_coupling_image_host", "dd_coupling_image")
+            "dd_coupling_image_host", "dd_coupling_image", "dd_glue_duals", "dd_relative_pd_gap")
 
 
 def _check(ctx, st, stats=None):
@@ -276,6 +279,27 @@ def dd_objective(ctx, partition=-1, eps=0.0):
     p, g, ga = C.c_double(), C.c_double(), C.c_double()
     _check(ctx, _lib.dd_objective(ctx, int(partition), float(eps), C.byref(p), C.byref(g), C.byref(ga)))
     return p.value, g.value, ga.value
+
+
+def dd_glue_duals(ctx):
+    """Glued X-dual of §6.3 of the context's current level, on the GPU.
+    Returns (alpha_hat (n_l² FP64), V ((n_l/2b)² FP64), CG iterations,
+    relative residual)."""
+    _, nl, nbasic, _, _ = dd_get_info(ctx)
+    na = int(round(nbasic ** 0.5)) // 2
+    a = np.zeros(nl * nl, dtype=np.float64)
+    V = np.zeros(na * na, dtype=np.float64)
+    it, rr = C.c_int32(), C.c_double()
+    _check(ctx, _lib.dd_glue_duals(ctx, a.ctypes.data, V.ctypes.data, C.byref(it), C.byref(rr)))
+    return a, V, it.value, rr.value
+
+
+def dd_relative_pd_gap(ctx):
+    """eq. RelPDGap of the last partition's coupling with the glued duals, on
+    the GPU. Returns (rel, gap, primal)."""
+    r, g, p = C.c_double(), C.c_double(), C.c_double()
+    _check(ctx, _lib.dd_relative_pd_gap(ctx, C.byref(r), C.byref(g), C.byref(p)))
+    return r.value, g.value, p.value
 
 
 def dd_glue_potential(n_nodes, j1, j2, logq, tol=1e-12, max_iter=100000):
@@ -591,11 +615,19 @@ class DD:
             return dd_coupling_image(self.ctx, colours)
         return dd_coupling_image_host(nl, self.basic_marginals(), colours)
 
-    def relative_pd_gap(self, mu, nu):
-        """eq. RelPDGap of the current state (§6.3): the duals of both
-        partitions glued on the host, the coupling of the last partition from
-        the GPU. mu, nu: the images at the current level. Returns
-        (rel, gap, primal)."""
+    def glue_duals(self):
+        """(alpha_hat, V, CG iterations, relative residual): the glued X-dual
+        of §6.3 of the current level, computed on the GPU."""
+        return dd_glue_duals(self.ctx)
+
+    def relative_pd_gap(self, mu=None, nu=None, device=True):
+        """eq. RelPDGap of the current state (§6.3): (rel, gap, primal) for the
+        coupling of the last partition and the glued duals of both
+        partitions. device=True: all on the GPU. device=False: gluing and
+        gap on the host from the downloaded duals and coupling; mu, nu are
+        then the images at the current level."""
+        if device:
+            return dd_relative_pd_gap(self.ctx)
         _, nl, _, eps, _ = dd_get_info(self.ctx)
         a_hat, _ = dd_glue_duals_host(mu, self.duals(0), self.duals(1), self.b, eps)
         return dd_relative_pd_gap_host(mu, nu, eps, self.plan(0.0), a_hat)

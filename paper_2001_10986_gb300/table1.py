@@ -8,7 +8,9 @@ of synthetic Gaussian mixtures, and reports the rows of the table:
 * total runtime (wall clock from host images to the last sweep, one GPU);
 * entries of (ν_i): the maximum on the finest layer (at its largest ε) and
   the final number;
-* relative primal-dual gap of eq. RelPDGap (glued duals, `DD.relative_pd_gap`);
+* relative primal-dual gap of eq. RelPDGap (glued duals and gap on the GPU,
+  `DD.relative_pd_gap`; with --host-gap also the host evaluation of the same
+  state, and both times);
 * L1 marginal errors of X and Y (`dd_cost`);
 * beside the table: peak device memory of the sparse plan and the cells that
   the local safeguard of §7.3 re-solved.
@@ -34,7 +36,7 @@ from . import synthetic as syn
 
 
 def run_one(n: int, pair: int, *, blobs: int = 6, floor: float = 1e-4, b: int = 4, err: float = 1e-4,
-            **opts) -> dict:
+            host_gap: bool = False, **opts) -> dict:
     from . import dd
     mu = syn.gaussian_mixture(n, blobs, 2 * pair, floor=floor)
     nu = syn.gaussian_mixture(n, blobs, 2 * pair + 1, floor=floor)
@@ -52,13 +54,20 @@ def run_one(n: int, pair: int, *, blobs: int = 6, floor: float = 1e-4, b: int = 
             nnz_final = int(st.nnz)
         seconds = time.perf_counter() - t0
         _, err_x, err_y = g.cost()
-        rel, _, _ = g.relative_pd_gap(mu, nu)
+        t1 = time.perf_counter()
+        rel, _, _ = g.relative_pd_gap()
+        gap_s = time.perf_counter() - t1
+        extra = {}
+        if host_gap:
+            t1 = time.perf_counter()
+            extra["relative_pd_gap_host"] = g.relative_pd_gap(mu, nu, device=False)[0]
+            extra["gap_host_s"] = time.perf_counter() - t1
         prof = g.profile()
     finally:
         g.close()
     return {"time_s": seconds, "entries_max": nnz_max_finest, "entries_final": nnz_final,
-            "relative_pd_gap": rel, "l1_error_x": err_x, "l1_error_y": err_y,
-            "peak_state_bytes": prof.peak_state_bytes, "safeguard_cells": prof.rescued_cells}
+            "relative_pd_gap": rel, "gap_s": gap_s, "l1_error_x": err_x, "l1_error_y": err_y,
+            "peak_state_bytes": prof.peak_state_bytes, "safeguard_cells": prof.rescued_cells, **extra}
 
 
 def _mean_std(xs):
@@ -72,9 +81,11 @@ def main(argv=None):
     ap.add_argument("--blobs", type=int, default=6)
     ap.add_argument("--mode", type=int, default=1)
     ap.add_argument("--dual-refine", type=int, default=0)
+    ap.add_argument("--host-gap", action="store_true")
     args = ap.parse_args(argv)
     for n in args.sizes:
-        runs = [run_one(n, k, blobs=args.blobs, mode=args.mode, dual_refine=args.dual_refine)
+        runs = [run_one(n, k, blobs=args.blobs, mode=args.mode, dual_refine=args.dual_refine,
+                        host_gap=args.host_gap)
                 for k in range(args.pairs)]
         out = {"image_size": n, "pairs": args.pairs, "iterations": (int(np.log2(n)) - 2) * 8 + 2}
         for key in runs[0]:
