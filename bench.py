@@ -554,6 +554,9 @@ def run_cuda(args):
     par256 = None
     if not args.no_ttc:
         ttc = {"plain": time_to_converged(dd, syn, mu, nu, w, args, stream)}
+        # the hybrid refinement: B cells of each new level start from the
+        # glued coarse dual (§6.3) interpolated linearly (§6.4), on the GPU
+        ttc["glued_refinement"] = time_to_converged(dd, syn, mu, nu, w, args, stream, dual_refine=1)
         par256 = {"plain": oracle_parity_256(dd, syn, args, stream)}
         if not args.no_learned:
             # learned warm start: network trained on pairs logged from plain

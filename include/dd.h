@@ -134,16 +134,22 @@ typedef struct {
                             two paths).
                             Bits 0 and 1 turn the graph replay of mode 1
                             off.                                               */
-  int32_t safeguard;     /* 1: a cell whose solve stops at max_iter with an
-                            X-error above 10·Err·‖μ_J‖ is solved again,
-                            warm-started from where it stopped, first at 4·ε
-                            and then at ε (the local safeguard of §7.3,
-                            "temporarily increasing ε"). Cells still at
-                            max_iter afterwards (also those just above their
-                            tolerance, at the FP32 floor of their sums) make
-                            the call return DD_ERR_NOT_CONVERGED after
-                            completing it. 0: off (the half-sweep keeps the
-                            cut-off solves). Default 1.                        */
+  int32_t safeguard;     /* 1: a cell whose solve stops at max_iter, or
+                            stagnates (its X-error falls by less than 1 % over
+                            128 iterations), with an X-error above
+                            10·Err·‖μ_J‖ is solved again, warm-started from
+                            where it stopped (the local safeguard of §7.3,
+                            "temporarily increasing ε"): at 4ε, then at ε from
+                            that result (4ε again if ε fails), otherwise at
+                            16ε, 64ε, … 4096ε, keeping the first solve that
+                            converges. A kept solve at a larger ε sets bit 3
+                            of the cell's status and counts in
+                            cells_escalated. Cells still not converged
+                            afterwards (also those just above their
+                            tolerance) make the call return
+                            DD_ERR_NOT_CONVERGED after completing it. 0: off
+                            (the half-sweep keeps the cut-off solves).
+                            Default 1.                                         */
 } dd_options;
 
 /* Counters of the work done by a context since creation or the last
@@ -179,6 +185,8 @@ typedef struct {
   int64_t peak_work_bytes;   /* largest device memory of the half-sweep buffers
                                 that scale with the entries (gathered supports,
                                 stabilisers, extracted rows)                     */
+  int64_t escalated_cells;   /* cell solves that the safeguard kept at a larger
+                                ε than the half-sweep's (status bit 3)           */
 } dd_profile;
 
 /* Statistics of the last sweep run by dd_sweep / dd_run_schedule. */
@@ -193,6 +201,8 @@ typedef struct {
   int64_t sweeps_done;    /* total sweeps since dd_create                     */
   int32_t cells_rescued;  /* cells of the last half-sweep that the safeguard
                              solved again                                     */
+  int32_t cells_escalated; /* of these, cells whose kept solve is at a larger
+                             ε (4ε … 4096ε; status bit 3)                     */
 } dd_sweep_stats;
 
 /* Fill *opt with the defaults listed above. */
@@ -425,7 +435,9 @@ dd_status dd_get_info(dd_ctx* ctx, int32_t* level, int32_t* n_level, int32_t* n_
 /* Per composite cell of the last half-sweep (in the cell order of its
  * partition: row-major over the grid of composite cells): Sinkhorn
  * iterations, final X-marginal L1 error, support size N_y of ν_cell, a
- * status word (bit 0: stopped at max_iter, bit 1: non-finite), the transport
+ * status word (bit 0: stopped at max_iter or stagnated, bit 1: non-finite,
+ * bit 2: workspace overflow, bit 3: the safeguard kept a solve at a larger ε),
+ * the transport
  * cost ⟨c, π_J⟩ of the cell's plan (FP64; the terms of dd_cost's cost) and
  * whether its main solve ran on a cluster of CTAs (1) or one CTA (0). Any
  * array may be NULL; cap is their length; *n_cells receives the number of

@@ -424,16 +424,17 @@ void launch_cta_solves(dd_ctx* c, SweepArgs a) {
   }
 }
 
-// The safeguard of §7.3 for cells whose solve stopped at max_iter with an
-// X-error above 10·Err·‖μ_J‖: such cells are collected on the device and
-// re-solved, warm-started from
-// the duals their solve ended with, first at a temporarily larger ε
-// (kSafeguardFactor·ε, where the cell problem is smoother and Sinkhorn
-// contracts faster) and then at ε from the result. Each re-solve is a full
-// cell solve with extraction, BalanceMeasures and Truncate, so the cell's
-// basic marginals end up those of the solve at ε. Two persistent launches
-// that exit at once when no cell failed; no host synchronisation.
-constexpr double kSafeguardFactor = 4.0;
+// The safeguard of §7.3 for cells whose solve stopped at max_iter (or
+// stagnated) with an X-error above 10·Err·‖μ_J‖: such cells are collected on
+// the device and solved again in one persistent launch, warm-started from the
+// duals their last solve ended with, at a temporarily larger ε: 4ε, then ε
+// from that result (and 4ε again if ε fails), else 16ε, 64ε, … up to
+// 4^kSafeguardSteps·ε, keeping the first that converges (status bit 3 marks a
+// cell whose plan is that of a larger ε). Each solve is a full cell solve with
+// extraction, BalanceMeasures and Truncate, so the state stays feasible
+// whichever solve is kept. The launch exits at once when no cell failed; no
+// host synchronisation.
+constexpr int kSafeguardSteps = 6;   // up to 4^6·ε
 
 void enqueue_safeguard(dd_ctx* c, const SweepArgs& a, double eps) {
   if (!c->opt.safeguard) return;
@@ -446,13 +447,12 @@ void enqueue_safeguard(dd_ctx* c, const SweepArgs& a, double eps) {
   r.nbig = nullptr;
   r.cell_learned = nullptr;
   r.max_iter = c->opt.max_iter;
-  for (const double f : {kSafeguardFactor, 1.0}) {
-    r.eps = (float)(eps * f);
-    DD_CUDA(cudaMemsetAsync(c->work_next, 0, sizeof(int), c->stream));
-    r.work_next = c->work_next;
-    DD_CUDA(launch_sinkhorn(r, threads_per_cell(c), c->stream, true));
-  }
-  c->prof.launches += 3;
+  r.eps = (float)eps;
+  r.escalate = kSafeguardSteps;
+  DD_CUDA(cudaMemsetAsync(c->work_next, 0, sizeof(int), c->stream));
+  r.work_next = c->work_next;
+  DD_CUDA(launch_sinkhorn_safeguard(r, threads_per_cell(c), c->stream));
+  c->prof.launches += 2;
 }
 
 int threads_per_cell(dd_ctx* c) {
@@ -561,6 +561,7 @@ void half_sweep(dd_ctx* c, int part, double eps) {
   }
   c->prof.cells += a.ncells;
   c->prof.rescued_cells += c->last_tot.rescued;
+  c->prof.escalated_cells += c->last_tot.escalated;
   c->unconverged_in_call += c->last_tot.not_converged;
   track_peaks(c);
   if (c->cell_times && std::getenv("DD_TRACE_TIMES_FILE")) {
@@ -584,7 +585,7 @@ void half_sweep(dd_ctx* c, int part, double eps) {
     DD_CUDA(cudaMemcpy(t.data(), c->trace_buf, 4096, cudaMemcpyDeviceToHost));
     std::fprintf(stderr, "trace part %d cell %d:", part, c->trace_cell);
     for (int k = 0; k < 512 && t[2 * k] != 0.f; k += (k < 40 ? 1 : 50))
-      std::fprintf(stderr, " %d:%.3g(w%.2f)", k + 1, t[2 * k], t[2 * k + 1]);
+      std::fprintf(stderr, " %d:%.3g(w%.2f)", k + 1, t[2 * k], t[2 * k + 1]);   // w: see the kernel's trace
     std::fprintf(stderr, "\n");
     DD_CUDA(cudaMemset(c->trace_buf, 0, 4096));
   }
@@ -1155,6 +1156,7 @@ void account_half_sweep(dd_ctx* c, const SweepTotals& t, int ncells) {
   c->prof.hessian_fma += t.hessian_fma;
   c->prof.cells += ncells;
   c->prof.rescued_cells += t.rescued;
+  c->prof.escalated_cells += t.escalated;
   c->unconverged_in_call += t.not_converged;
 }
 
@@ -1300,6 +1302,7 @@ void fill_stats(dd_ctx* c, dd_sweep_stats* st) {
   st->cells_not_converged = c->last_tot.not_converged;
   st->sweeps_done = c->sweeps_done;
   st->cells_rescued = c->last_tot.rescued;
+  st->cells_escalated = c->last_tot.escalated;
 }
 
 }  // namespace

@@ -7,8 +7,9 @@
 //   k_glue_cg      the least-squares potential V on the cells of A: one
 //                  cluster of 8 CTAs runs Jacobi-preconditioned conjugate
 //                  gradients on the gluing graph's Laplacian, each CTA on a
-//                  band of A-cell rows, the neighbouring bands' search
-//                  direction read through distributed shared memory.
+//                  band of A-cell rows, the halo rows of the search direction
+//                  copied from the neighbouring bands through distributed
+//                  shared memory.
 //   k_glue_apply   α̂ = α_A + ε·V[A cell]; pixels without mass get 0 or the
 //                  affine least-squares fit of their A cell's α̂.
 //   k_glue_frames  α̂ of a level interpolated linearly onto the level twice as
@@ -198,19 +199,22 @@ __global__ void __launch_bounds__(256) k_glue_sides(LevelView L, const float* al
 // ---------------------------------------------------------------------------
 // the potential V: preconditioned CG on one cluster
 // ---------------------------------------------------------------------------
-// CTA k owns the A-cell rows [k·rpc, min(na, (k+1)·rpc)); its search
-// direction p and residual r live in shared memory (2·rpc·na doubles), the
-// iterate x in V. Scalars are reduced per CTA, exchanged through shared
-// memory slots and summed in rank order, so every CTA takes the same
-// decisions. Barriers per iteration: after the p·Lp partials, after the
-// residual partials, after the update of p.
+// CTA k owns the A-cell rows [k·rpc, min(na, (k+1)·rpc)). Its search
+// direction p lives in shared memory with one halo row above and below
+// ((rpc + 2)·na doubles, then rpc·na for the preconditioner's diagonal), copied from the neighbouring CTAs through
+// distributed shared memory once per iteration, so that the stencil reads
+// only local shared memory; the residual r and L p stay in registers (at
+// most kGlueNodesPerThread nodes per thread), the iterate x in V. Scalars are reduced per CTA, exchanged through
+// shared-memory slots and summed in rank order, so every CTA takes the same
+// decisions. Cluster barriers per iteration: after the p·Lp partials, after
+// the residual partials, after the update of p.
 __global__ void __cluster_dims__(kGlueCTAs, 1, 1) __launch_bounds__(kGlueThreads, 1)
     k_glue_cg(int na, int nb, const double* sp, const double* sm, double tol, int max_iter, double* V,
               GlueInfo* info) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   extern __shared__ double glue_smem[];
-  __shared__ double ws[32];
+  __shared__ double ws0[32], ws1[32];
   // one exchange slot per reduction site: a slot is written again only after
   // a later cluster barrier, which every CTA reaches after its reads of it
   __shared__ double slotA[2], slotB[2], slotC[2], bcast[2];
@@ -218,20 +222,32 @@ __global__ void __cluster_dims__(kGlueCTAs, 1, 1) __launch_bounds__(kGlueThreads
   const int row0 = rank * rpc;
   const int rows = max(0, min(na, row0 + rpc) - row0);
   const int nloc = rows * na;
-  double* p_s = glue_smem;
-  double* r_s = glue_smem + (size_t)rpc * na;
+  double* p_h = glue_smem;        // row −1 of the band
+  double* p_s = glue_smem + na;   // rows 0 … rows−1, then row `rows`
+  double* dinv_s = glue_smem + (size_t)(rpc + 2) * na;   // 1/degree per node of the band
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-  // the sum over the cluster of one or two per-thread values, in rank order
+  // the sum over the cluster of two per-thread values, in rank order
   auto cluster_sum = [&](double v0, double v1, double* slot, double& s0, double& s1) {
-    v0 = block_sum_d(v0, ws);
-    v1 = block_sum_d(v1, ws);
-    if (threadIdx.x == 0) {
-      slot[0] = v0;
-      slot[1] = v1;
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    if (lane == 0) {
+      ws0[warp] = v0;
+      ws1[warp] = v1;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double a = lane < kGlueThreads / 32 ? ws0[lane] : 0.0;
+      double b = lane < kGlueThreads / 32 ? ws1[lane] : 0.0;
+      a = warp_sum(a);
+      b = warp_sum(b);
+      if (lane == 0) {
+        slot[0] = a;
+        slot[1] = b;
+      }
     }
     cluster.sync();
-    if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
+    if (warp == 0) {
       double a = 0.0, b = 0.0;
       if (lane < kGlueCTAs) {
         const double* rs = cluster.map_shared_rank(slot, lane);
@@ -248,11 +264,22 @@ __global__ void __cluster_dims__(kGlueCTAs, 1, 1) __launch_bounds__(kGlueThreads
     __syncthreads();
     s0 = bcast[0];
     s1 = bcast[1];
-    __syncthreads();
   };
-  auto pval = [&](int R, int C) -> double {   // p at A cell (R, C) of any band
-    const int o = R / rpc;
-    return cluster.map_shared_rank(p_s, o)[(size_t)(R - o * rpc) * na + C];
+  // halo rows of p from the CTAs owning rows row0 − 1 and row0 + rows
+  auto fetch_halo = [&]() {
+    if (rows > 0) {
+      if (row0 > 0) {
+        const int o = (row0 - 1) / rpc;
+        const double* src = cluster.map_shared_rank(p_s, o) + (size_t)(row0 - 1 - o * rpc) * na;
+        for (int c = threadIdx.x; c < na; c += blockDim.x) p_h[c] = src[c];
+      }
+      if (row0 + rows < na) {
+        const int o = (row0 + rows) / rpc;
+        const double* src = cluster.map_shared_rank(p_s, o) + (size_t)(row0 + rows - o * rpc) * na;
+        for (int c = threadIdx.x; c < na; c += blockDim.x) p_s[(size_t)rows * na + c] = src[c];
+      }
+    }
+    __syncthreads();
   };
   auto degree = [&](int R, int C) -> double {
     const bool up = R > 0, dn = R < na - 1, lf = C > 0, rt = C < na - 1;
@@ -262,28 +289,39 @@ __global__ void __cluster_dims__(kGlueCTAs, 1, 1) __launch_bounds__(kGlueThreads
 
   // right-hand side b = −Dᵀ log q, built from the B cells at the four
   // corners of each A cell; x = 0, r = b, p = z = b/deg
-  double bb = 0.0, rz = 0.0;
+  double rreg[kGlueNodesPerThread];
   for (int l = threadIdx.x; l < nloc; l += blockDim.x) {
-    const int R = row0 + l / na, C = l % na;
-    double b = 0.0;
-    for (int dr = 0; dr < 2; ++dr)
-      for (int dc = 0; dc < 2; ++dc) {
-        const int Rb = R + dr, Cb = C + dc;                 // B cell (Rb, Cb)
-        const int mi = 2 * R + dr, mj = 2 * C + dc;         // this A cell's basic cell in it
-        const double spJ = sp[sidx(mi, mj)], smJ = sm[sidx(mi, mj)];
-        for (int ei = 2 * Rb - 1; ei <= 2 * Rb; ++ei)
-          for (int ej = 2 * Cb - 1; ej <= 2 * Cb; ++ej) {
-            if (ei < 0 || ei >= nb || ej < 0 || ej >= nb || (ei == mi && ej == mj)) continue;
-            b += sp[sidx(ei, ej)] + smJ - spJ - sm[sidx(ei, ej)];
-          }
-      }
-    const double d = degree(R, C);
-    const double z = d > 0.0 ? b / d : 0.0;
-    r_s[l] = b;
-    p_s[l] = z;
-    V[(size_t)R * na + C] = 0.0;
-    bb += b * b;
-    rz += b * z;
+    const double d = degree(row0 + l / na, l % na);
+    dinv_s[l] = d > 0.0 ? 1.0 / d : 0.0;   // the preconditioner's diagonal
+  }
+  __syncthreads();
+  auto dinv = [&](int l) { return dinv_s[l]; };
+  double bb = 0.0, rz = 0.0;
+#pragma unroll
+  for (int k = 0; k < kGlueNodesPerThread; ++k) {
+    const int l = threadIdx.x + k * kGlueThreads;
+    rreg[k] = 0.0;
+    if (l < nloc) {
+      const int R = row0 + l / na, C = l % na;
+      double b = 0.0;
+      for (int dr = 0; dr < 2; ++dr)
+        for (int dc = 0; dc < 2; ++dc) {
+          const int Rb = R + dr, Cb = C + dc;                 // B cell (Rb, Cb)
+          const int mi = 2 * R + dr, mj = 2 * C + dc;         // this A cell's basic cell in it
+          const double spJ = sp[sidx(mi, mj)], smJ = sm[sidx(mi, mj)];
+          for (int ei = 2 * Rb - 1; ei <= 2 * Rb; ++ei)
+            for (int ej = 2 * Cb - 1; ej <= 2 * Cb; ++ej) {
+              if (ei < 0 || ei >= nb || ej < 0 || ej >= nb || (ei == mi && ej == mj)) continue;
+              b += sp[sidx(ei, ej)] + smJ - spJ - sm[sidx(ei, ej)];
+            }
+        }
+      const double di = dinv(l);
+      rreg[k] = b;
+      p_s[l] = b * di;
+      V[(size_t)R * na + C] = 0.0;
+      bb += b * b;
+      rz += b * b * di;
+    }
   }
   cluster_sum(bb, rz, slotB, bb, rz);
   const double bnorm = sqrt(bb);
@@ -292,26 +330,32 @@ __global__ void __cluster_dims__(kGlueCTAs, 1, 1) __launch_bounds__(kGlueThreads
   int converged = !(bnorm > 0.0);
   double qreg[kGlueNodesPerThread];
   if (!converged) {
+    fetch_halo();
     for (; it < max_iter; ++it) {
-      // q = L p (p of the neighbouring bands through distributed shared memory)
+      // q = L p on the band (row −1 at p_h, row `rows` after the band)
       double pq = 0.0;
 #pragma unroll
       for (int k = 0; k < kGlueNodesPerThread; ++k) {
         const int l = threadIdx.x + k * kGlueThreads;
         qreg[k] = 0.0;
         if (l < nloc) {
-          const int R = row0 + l / na, C = l % na;
-          const double pc = p_s[l];
-          double q = degree(R, C) * pc;
-          for (int dr = -1; dr <= 1; ++dr) {
-            const int R2 = R + dr;
-            if (R2 < 0 || R2 >= na) continue;
-            for (int dc = -1; dc <= 1; ++dc) {
-              const int C2 = C + dc;
-              if ((dr == 0 && dc == 0) || C2 < 0 || C2 >= na) continue;
-              q -= ((dr == 0 || dc == 0) ? 4.0 : 2.0) * pval(R2, C2);
-            }
+          const int lr = l / na, C = l - (l / na) * na, R = row0 + lr;
+          const double* up = lr > 0 ? p_s + (size_t)(lr - 1) * na : p_h;
+          const double* mid = p_s + (size_t)lr * na;
+          const double* dn = mid + na;
+          const bool hu = R > 0, hd = R < na - 1, hl = C > 0, hr = C < na - 1;
+          const double pc = mid[C];
+          double nb4 = (hl ? mid[C - 1] : 0.0) + (hr ? mid[C + 1] : 0.0);
+          double nb2 = 0.0;
+          if (hu) {
+            nb4 += up[C];
+            nb2 += (hl ? up[C - 1] : 0.0) + (hr ? up[C + 1] : 0.0);
           }
+          if (hd) {
+            nb4 += dn[C];
+            nb2 += (hl ? dn[C - 1] : 0.0) + (hr ? dn[C + 1] : 0.0);
+          }
+          const double q = degree(R, C) * pc - 4.0 * nb4 - 2.0 * nb2;
           qreg[k] = q;
           pq += pc * q;
         }
@@ -325,13 +369,11 @@ __global__ void __cluster_dims__(kGlueCTAs, 1, 1) __launch_bounds__(kGlueThreads
       for (int k = 0; k < kGlueNodesPerThread; ++k) {
         const int l = threadIdx.x + k * kGlueThreads;
         if (l < nloc) {
-          const int R = row0 + l / na, C = l % na;
-          V[(size_t)R * na + C] += a * p_s[l];
-          const double r = r_s[l] - a * qreg[k];
-          r_s[l] = r;
-          const double d = degree(R, C);
-          rr += r * r;
-          rzn += d > 0.0 ? r * r / d : 0.0;
+          const size_t v = (size_t)(row0 + l / na) * na + l % na;
+          V[v] += a * p_s[l];
+          rreg[k] -= a * qreg[k];
+          rr += rreg[k] * rreg[k];
+          rzn += rreg[k] * rreg[k] * dinv(l);
         }
       }
       cluster_sum(rr, rzn, slotB, rr, rzn);
@@ -343,12 +385,13 @@ __global__ void __cluster_dims__(kGlueCTAs, 1, 1) __launch_bounds__(kGlueThreads
       }
       const double beta = rzn / rz;
       rz = rzn;
-      for (int l = threadIdx.x; l < nloc; l += blockDim.x) {
-        const int R = row0 + l / na, C = l % na;
-        const double d = degree(R, C);
-        p_s[l] = (d > 0.0 ? r_s[l] / d : 0.0) + beta * p_s[l];
+#pragma unroll
+      for (int k = 0; k < kGlueNodesPerThread; ++k) {
+        const int l = threadIdx.x + k * kGlueThreads;
+        if (l < nloc) p_s[l] = rreg[k] * dinv(l) + beta * p_s[l];
       }
-      cluster.sync();   // the neighbouring bands see the new p
+      cluster.sync();   // the neighbouring bands' new p is complete
+      fetch_halo();
     }
   }
   // mean zero (the grid graph is connected: the gauge Σ V = 0)
@@ -556,7 +599,7 @@ cudaError_t launch_glue_potential(LevelView L, const float* alpha_A, const int2*
   const int na = L.nb / 2;
   if (na > glue_max_cells_per_side()) return cudaErrorInvalidValue;
   const int rpc = (na + kGlueCTAs - 1) / kGlueCTAs;
-  const size_t smem = 2 * sizeof(double) * (size_t)rpc * na;
+  const size_t smem = sizeof(double) * (size_t)(2 * rpc + 2) * na;
   e = cudaFuncSetAttribute(k_glue_cg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_glue_cg<<<kGlueCTAs, kGlueThreads, smem, s>>>(na, L.nb, sp, sm, tol, max_iter, V, info);

@@ -122,7 +122,10 @@ struct SweepArgs {
   int newton;               // Newton X-iterations allowed
   int32_t* cell_learned;    // per cell: 1 learned duals used, 0 compared and not used,
                             // −1 not compared (nullable: no prediction this half-sweep)
-  int32_t* cell_status;     // bit0 not converged, bit1 non-finite, bit2 workspace overflow
+  int32_t* cell_status;     // bit0 not converged, bit1 non-finite, bit2 workspace overflow,
+                            // bit3 converged only at a larger ε in the safeguard
+  int escalate;             // the safeguard's launch: solves at 4ε, 16ε, … up to 4^escalate·ε until
+                            // one converges (see k_sinkhorn_safeguard); unused elsewhere
   int* err_flag;
   const int32_t* order;     // launch order of the cells (NULL: natural order)
   const int* nbig;          // the first *nbig cells of `order` are solved by clusters (NULL: none)
@@ -145,6 +148,10 @@ cudaError_t launch_sinkhorn_cluster(const SweepArgs& a, cudaStream_t s);
 // per-CTA cell solves; persistent: one wave of CTAs that take cells from
 // a.work_next (which must be 0 at launch) until none are left
 cudaError_t launch_sinkhorn(const SweepArgs& a, int threads, cudaStream_t s, bool persistent = false);
+// the safeguard's re-solves (a.escalate attempts with growing ε, see
+// k_sinkhorn_safeguard) of the cells a.order[0 .. *a.ncells_dev) as one
+// persistent wave; a.work_next must be 0 at launch
+cudaError_t launch_sinkhorn_safeguard(const SweepArgs& a, int threads, cudaStream_t s);
 // exclusive scan of the row lengths into rp_out[0..nrows]; skipped when
 // *err_flag (nullable) is non-zero
 cudaError_t launch_row_scan(const int32_t* cnt, int64_t* rp_out, int64_t* tile_sum, int nrows, cudaStream_t s,
@@ -168,6 +175,7 @@ struct SweepTotals {
   int learned;               // cells started from the learned duals
   int compared;              // cells whose prediction was compared
   int rescued;               // cells re-solved by the safeguard
+  int escalated;             // cells whose plan is that of a larger ε (status bit 3)
 };
 cudaError_t launch_reduce_cells(const SweepArgs& a, SweepTotals* out_dev, cudaStream_t s);
 // §7.2 image of basic marginals (CSR, nrows rows, Y pixels < n2): rgb[3y+k]

@@ -342,6 +342,9 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(SweepArgs a) {
 
 constexpr int kMaxHW = 256;
 constexpr int kTraceLen = 512;
+constexpr int kStagnationPeriod = 128;     // iterations between stagnation checks (a power of 2)
+constexpr float kStagnationRatio = 0.99f;  // error ratio over one period that counts as stagnation
+constexpr float kSafeguardFactor = 4.0f;   // ε factor of each safeguard attempt
 constexpr int kClusterCTAs = 8;    // CTAs sharing one large cell
 constexpr int kMaxBig = 256;       // cells solved by clusters per launch
 constexpr int kStageSmall = 1408;  // support points staged in shared memory per CTA (per-CTA solves)
@@ -558,7 +561,7 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
   // rescaled to ‖ν_cell‖ (the §6.2 rule when nothing was truncated)
   const float mscale = muJ > 0.f ? nuJ / muJ : 1.f;
   // over-relaxation state, identical in every thread
-  float omega = 1.0f, e3 = 0.f, emin = 3.0e38f;
+  float omega = 1.0f, e3 = 0.f, emin = 3.0e38f, e_stag = 3.0e38f;
   bool relax_off = false;
   int phase = 0;
   // Newton steps for the X-iteration (cells of at most 64 pixels, CTAs of 128
@@ -1125,9 +1128,20 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     ++it;
     // every thread takes the same decisions from the same ep
     int stop = 0;
+    // A solve whose error falls by less than 1 % over 128 iterations
+    // (contraction above 0.99992 per iteration) stops as one at max_iter
+    // would: such a cell needs far more iterations than any max_iter allows
+    // (its support lies so far from the cell that c/ε differs by thousands
+    // between its pixels and the cell problem is an assignment problem in
+    // all but name), and the safeguard's larger ε is what solves it.
+    bool stagnant = false;
+    if ((it & (kStagnationPeriod - 1)) == 0) {
+      stagnant = it >= 2 * kStagnationPeriod && ep > kStagnationRatio * e_stag;
+      e_stag = ep;
+    }
     if (!(ep == ep) || isinf(ep)) stop = 2;
     else if (ep <= tol) stop = 1;
-    else if (it >= a.max_iter) stop = 3;
+    else if (it >= a.max_iter || stagnant) stop = 3;
     // Over-relaxed X-iteration u ← u·(μ/P_X π)^ω (same fixed point, same
     // stopping rule, always ending on a Y-iteration). ω follows from the
     // contraction ρ of the plain iteration measured over iterations 3..6,
@@ -1146,8 +1160,11 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     }
     emin = fminf(emin, ep);
     if (tid == 0 && rank == 0 && J == a.trace_cell && a.trace && it <= kTraceLen) {
+      // relative error; ω + 10·(Newton steps so far) + 1000 while Newton
+      // X-iterations are on + 2000 once they are off for this solve
       a.trace[2 * (it - 1)] = ep / muJ;
-      a.trace[2 * (it - 1) + 1] = omega;
+      a.trace[2 * (it - 1) + 1] = omega + 10.0f * (float)nsteps + (newton ? 1000.f : 0.f) +
+                                  (newton_off ? 2000.f : 0.f);
     }
     if (stop) {
       // the reported error is the unscaled Σ_x |P_X π − μ|
@@ -1615,6 +1632,77 @@ __global__ void __maxnreg__(168) k_sinkhorn(SweepArgs a) {
   }
 }
 
+// The safeguard of §7.3 (a persistent wave over the cells in `order`): per
+// cell, solves at 4ε, 16ε, … up to 4^escalate·ε, each warm-started from the
+// duals the last one ended with, until one converges. After a solve converged
+// at 4ε the cell is solved at ε from that result, and again at 4ε if that
+// fails; a kept solve at a larger ε sets status bit 3. A kernel of its own,
+// so that the attempt loop leaves the main solve kernel's registers alone.
+__global__ void __maxnreg__(168) k_sinkhorn_safeguard(SweepArgs a) {
+  __shared__ SinkSmem sm;
+  __shared__ int s_pos, s_stop, s_step, s_phase, s_more;
+  __shared__ float s_f;
+  __shared__ SweepArgs s_args;   // see k_sinkhorn
+  extern __shared__ float4 ys_small[];
+  if (threadIdx.x == 0) s_args = a;
+  __syncthreads();
+  const int ncells = a.ncells_dev ? *a.ncells_dev : a.ncells;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_pos = atomicAdd(a.work_next, 1);
+      s_stop = *a.err_flag & (4 | 8);
+    }
+    __syncthreads();
+    const int pos = s_pos, stop = s_stop;
+    __syncthreads();   // every thread has read s_pos before it is overwritten
+    if (pos >= ncells || stop) break;
+    const int J = a.order[pos];
+    // The attempt state lives in shared memory and is advanced by thread 0,
+    // so that nothing stays live in registers across the solve.
+    if (threadIdx.x == 0) {
+      s_f = kSafeguardFactor;
+      s_step = 1;
+      s_phase = 0;   // 0: escalating; 1: at ε after 4ε converged; 2: 4ε again
+      s_args.eps = a.eps * s_f;
+    }
+    __syncthreads();
+    for (;;) {
+      // dynamic shared memory: the staged support points, then the Newton buffer
+      solve_cell<1, kMaxHW / 32>(s_args, J, sm, 0, ys_small, kStageSmall,
+                                 reinterpret_cast<float*>(ys_small + kStageSmall));
+      __syncthreads();   // the status written by thread 0; the cell's shared memory is free
+      if (threadIdx.x == 0) {
+        bool more = false, keep = false;
+        const bool ok = (a.cell_status[J] & 7) == 0;
+        if (s_phase == 0) {
+          if (ok && s_step == 1) {
+            s_phase = 1;
+            s_f = 1.0f;
+            more = true;
+          } else if (ok) {
+            keep = true;
+          } else if (++s_step <= a.escalate) {
+            s_f *= kSafeguardFactor;
+            more = true;
+          }
+        } else if (s_phase == 1 && !ok) {
+          s_phase = 2;
+          s_f = kSafeguardFactor;
+          more = true;
+        } else if (s_phase == 2) {
+          keep = ok;
+        }
+        if (keep) a.cell_status[J] |= 8;
+        s_args.eps = more ? a.eps * s_f : a.eps;
+        s_more = more;
+      }
+      __syncthreads();
+      if (!s_more) break;
+    }
+    __syncthreads();     // the cell's shared memory is free for the next one
+  }
+}
+
 // a cluster of kClusterCTAs CTAs per cell, for the first nbig cells of the
 // launch order (largest predicted work)
 __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256, 2) k_sinkhorn_cluster(SweepArgs a) {
@@ -1830,7 +1918,7 @@ __global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals*
   __shared__ int iws[32];
   double c = 0.0, e = 0.0, ev = 0.0, hf = 0.0;
   long long its = 0, nst = 0;
-  int mx = 0, nc = 0, nf = 0, ov = 0, nl = 0, nj = 0;
+  int mx = 0, nc = 0, nf = 0, ov = 0, nl = 0, nj = 0, nesc = 0;
   for (int J = threadIdx.x; J < a.ncells; J += blockDim.x) {
     const int st = a.cell_status[J];
     if (a.cell_learned) {
@@ -1850,6 +1938,7 @@ __global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals*
     mx = max(mx, a.cell_iters[J]);
     nc += (st & 1) ? 1 : 0;
     nf += (st & 2) ? 1 : 0;
+    nesc += (st & 8) ? 1 : 0;
   }
   c = block_sum<double>(c, dws);
   e = block_sum<double>(e, dws);
@@ -1862,6 +1951,7 @@ __global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals*
   ov = block_sum<int>(ov, iws);
   nl = block_sum<int>(nl, iws);
   nj = block_sum<int>(nj, iws);
+  nesc = block_sum<int>(nesc, iws);
   // max via shuffles
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   __syncthreads();
@@ -1883,6 +1973,7 @@ __global__ void __launch_bounds__(1024) k_reduce_cells(SweepArgs a, SweepTotals*
     out->learned = nl;
     out->compared = nj;
     out->rescued = a.rescued_dev ? *a.rescued_dev : 0;
+    out->escalated = nesc;
   }
 }
 
@@ -2300,6 +2391,38 @@ static cudaError_t ensure_dyn_smem(K kernel, int bytes, std::atomic<bool>* done)
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess && cached) done[dev].store(true, std::memory_order_release);
   return e;
+}
+
+// resident CTAs of `kernel` on the whole GPU for a block size, queried once
+// per device (so that a launch inside a stream capture makes no query)
+template <typename K>
+static cudaError_t resident_wave(K kernel, int threads, int smem, std::atomic<int> (*cache)[4], int& w) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int ti = threads == 32 ? 0 : threads == 64 ? 1 : threads == 128 ? 2 : 3;
+  w = (dev >= 0 && dev < 64) ? cache[dev][ti].load() : 0;
+  if (w > 0) return cudaSuccess;
+  int sms = 0, per_sm = 0;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem)) != cudaSuccess) return e;
+  w = sms * std::max(per_sm, 1);
+  if (dev >= 0 && dev < 64) cache[dev][ti].store(w);
+  return cudaSuccess;
+}
+
+cudaError_t launch_sinkhorn_safeguard(const SweepArgs& a, int threads, cudaStream_t s) {
+  static std::atomic<bool> done[64];
+  static std::atomic<int> wave[64][4];
+  if (threads != 32 && threads != 64 && threads != 128 && threads != 256) threads = 128;
+  if (!a.work_next || !a.order) return cudaErrorInvalidValue;
+  const int smem = (int)(kStageSmall * sizeof(float4) + kNewtonFloats * sizeof(float));
+  cudaError_t e = ensure_dyn_smem(k_sinkhorn_safeguard, smem, done);
+  if (e != cudaSuccess) return e;
+  int w = 0;
+  if ((e = resident_wave(k_sinkhorn_safeguard, threads, smem, wave, w)) != cudaSuccess) return e;
+  k_sinkhorn_safeguard<<<std::max(1, std::min(a.ncells, w)), threads, smem, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sinkhorn(const SweepArgs& a, int threads, cudaStream_t s, bool persistent) {

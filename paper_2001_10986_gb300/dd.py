@@ -37,7 +37,7 @@ class dd_options(C.Structure):
 class dd_sweep_stats(C.Structure):
     _fields_ = [("level", C.c_int32), ("partition", C.c_int32), ("eps", C.c_double), ("nnz", C.c_int64),
                 ("max_iters", C.c_int32), ("mean_iters", C.c_double), ("cells_not_converged", C.c_int32),
-                ("sweeps_done", C.c_int64), ("cells_rescued", C.c_int32)]
+                ("sweeps_done", C.c_int64), ("cells_rescued", C.c_int32), ("cells_escalated", C.c_int32)]
 
 
 class dd_profile(C.Structure):
@@ -46,7 +46,8 @@ class dd_profile(C.Structure):
                 ("cluster_ms", C.c_double), ("kernel_evals", C.c_double), ("sinkhorn_iters", C.c_double), ("cells", C.c_int64),
                 ("newton_steps", C.c_int64), ("hessian_fma", C.c_double), ("learned_cells", C.c_int64),
                 ("compared_cells", C.c_int64), ("rescued_cells", C.c_int64), ("graph_reruns", C.c_int64),
-                ("peak_nnz", C.c_int64), ("peak_state_bytes", C.c_int64), ("peak_work_bytes", C.c_int64)]
+                ("peak_nnz", C.c_int64), ("peak_state_bytes", C.c_int64), ("peak_work_bytes", C.c_int64),
+                ("escalated_cells", C.c_int64)]
 
 
 class DDError(RuntimeError):

@@ -112,7 +112,10 @@ def test_learned_warm_start_gains_over_plain(lib):
         Fs.append(f)
         Ts.append(t)
     net = learned.train((torch.cat(Fs), torch.cat(Ts)), epochs=40, batch=256, lr=1e-3)
-    # three new pairs; the prediction is compared at the first sweep on each new level
+    # three new pairs; the prediction is compared at the first sweep on each new
+    # level. Err = 1e-6 keeps every cell above the FP32 floor of its sums, so
+    # that the iteration counts measure the start and not cells that stall
+    # there and end in the safeguard
     iters = {0: 0.0, 1: 0.0}
     taken = compared = 0
     costs = {0: [], 1: []}
@@ -120,7 +123,7 @@ def test_learned_warm_start_gains_over_plain(lib):
         mu = syn.gaussian_mixture(n, 5, 300 + 2 * pair)
         nu = syn.gaussian_mixture(n, 5, 301 + 2 * pair)
         for warm in (0, 1):
-            g = lib.DD(mu, nu, b, L, sched, err_tol=1e-7, warm=warm)
+            g = lib.DD(mu, nu, b, L, sched, err_tol=1e-6, warm=warm)
             if warm:
                 g.attach_mlp(net)
             g.run_schedule()

@@ -159,3 +159,36 @@ def test_injected_workspace_allocation_failure(lib):
     r.run_schedule(strict=True)
     _assert_same_state(got, _state(r))
     r.close()
+
+
+def test_safeguard_escalates_epsilon_and_keeps_the_state_feasible(lib):
+    # a cold start at a small ε with 50 iterations per solve: the main solves
+    # and the re-solves at 4ε stop short, the safeguard goes on to 16ε, 64ε,
+    # … and keeps the first solve that converges (status bit 3). Cells left
+    # at max_iter are those the safeguard does not take: X-error at most
+    # 10·Err·‖μ_J‖. The state stays feasible.
+    n, b, err = 32, 4, 1e-6
+    mu = syn.gaussian_mixture(n, 3, 58)
+    nu = syn.gaussian_mixture(n, 3, 59)
+    g = lib.DD(mu, nu, b, 1, [(0.002, 2, 0)], err_tol=err, max_iter=50)
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        st = g.sweep(1)
+    cs = g.cell_stats()
+    prof = g.profile()
+    _, ex, ey = g.cost()
+    g.close()
+    assert st.cells_escalated > 0
+    assert int(((cs["status"] & 8) != 0).sum()) == st.cells_escalated
+    assert prof.escalated_cells >= st.cells_escalated
+    # ‖μ_J‖ of the B cells (the last half-sweep): basic cells 2a−1, 2a per axis
+    m = mu / mu.sum()
+    nb = n // b
+    M = np.zeros((nb + 2, nb + 2))
+    M[1:-1, 1:-1] = m.reshape(nb, b, nb, b).sum(axis=(1, 3))
+    muJ = M.reshape(nb // 2 + 1, 2, nb // 2 + 1, 2).sum(axis=(1, 3)).reshape(-1)
+    left = np.flatnonzero(cs["status"] & 1)
+    assert left.size == st.cells_not_converged
+    assert np.all(cs["err_x"][left] <= 10 * err * muJ[left] * (1 + 1e-6))
+    assert np.all((cs["status"][cs["status"] & 8 != 0] & 7) == 0)
+    assert ey < 1e-10
