@@ -135,8 +135,8 @@ typedef struct {
                             Bits 0 and 1 turn the graph replay of mode 1
                             off.                                               */
   int32_t safeguard;     /* 1: a cell whose solve stops at max_iter, or
-                            stagnates (its X-error falls by less than 1 % over
-                            128 iterations), with an X-error above
+                            stagnates (its X-error falls by less than 0.1 %
+                            over 128 iterations), with an X-error above
                             10·Err·‖μ_J‖ is solved again, warm-started from
                             where it stopped (the local safeguard of §7.3,
                             "temporarily increasing ε"): at 4ε, then at ε from

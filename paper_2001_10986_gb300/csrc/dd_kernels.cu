@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(SweepArgs a) {
 constexpr int kMaxHW = 256;
 constexpr int kTraceLen = 512;
 constexpr int kStagnationPeriod = 128;     // iterations between stagnation checks (a power of 2)
-constexpr float kStagnationRatio = 0.99f;  // error ratio over one period that counts as stagnation
+constexpr float kStagnationRatio = 0.999f;  // error ratio over one period that counts as stagnation
 constexpr float kSafeguardFactor = 4.0f;   // ε factor of each safeguard attempt
 constexpr int kClusterCTAs = 8;    // CTAs sharing one large cell
 constexpr int kMaxBig = 256;       // cells solved by clusters per launch
@@ -1128,15 +1128,16 @@ __device__ void sinkhorn_cell(const SweepArgs& a, const int J, const CellGeom& g
     ++it;
     // every thread takes the same decisions from the same ep
     int stop = 0;
-    // A solve whose error falls by less than 1 % over 128 iterations
-    // (contraction above 0.99992 per iteration) stops as one at max_iter
-    // would: such a cell needs far more iterations than any max_iter allows
-    // (its support lies so far from the cell that c/ε differs by thousands
-    // between its pixels and the cell problem is an assignment problem in
-    // all but name), and the safeguard's larger ε is what solves it.
+    // A solve whose error stays above 10·Err·‖μ_J‖ and falls by less than
+    // 0.1 % over 128 iterations (contraction above 0.999992 per iteration)
+    // stops as one at max_iter would: such a cell needs far more iterations
+    // than any max_iter allows (its support lies so far from the cell that
+    // c/ε differs by thousands between its pixels and the cell problem is an
+    // assignment problem in all but name), and the safeguard's larger ε,
+    // which takes exactly the cells above 10·Err·‖μ_J‖, is what solves it.
     bool stagnant = false;
     if ((it & (kStagnationPeriod - 1)) == 0) {
-      stagnant = it >= 2 * kStagnationPeriod && ep > kStagnationRatio * e_stag;
+      stagnant = it >= 2 * kStagnationPeriod && ep > 10.0f * tol && ep > kStagnationRatio * e_stag;
       e_stag = ep;
     }
     if (!(ep == ep) || isinf(ep)) stop = 2;
