@@ -43,10 +43,11 @@ SM_MAX_MHZ = 2070.0
 FMA_PER_ENTRY = 2.0
 HESS_SYM = 65.0 / 128.0
 # DRAM bytes per launch of the per-CTA cell-solve kernel k_sinkhorn, from an
-# ncu capture of the current kernel (dram__bytes_read.sum + write.sum: 66.6 MB
-# for the A and 61.4 MB for the B half-sweep at 512², averaged) scaled by the
-# 4× cell count to 1024²; the cluster kernel beside it is not included
-SOLVE_TRAFFIC_BYTES = 4 * 64.0e6
+# ncu capture of the current kernel (dram__bytes_read.sum + write.sum over the
+# last two finest-level sweeps at 512²: 63.5 and 51.8 MB for the A, 56.8 and
+# 54.9 MB for the B half-sweeps, mean 56.8 MB) scaled by the 4× cell count to
+# 1024²; the cluster kernel beside it is not included
+SOLVE_TRAFFIC_BYTES = 4 * 56.8e6
 
 
 def parse():

@@ -10,10 +10,10 @@ with the learned warm start: the coarse-to-fine schedule of
 final ε until both marginal L1 errors are ≤ 1e-6 and one sweep changes the
 transport cost by at most 1e-7 relative. Reported per run: wall time from
 host images, cells still at max_iter after the schedule and at the end,
-cells the local safeguard of §7.3 re-solved, Sinkhorn iterations and Newton
-steps, peak entries of (ν_i) and peak device memory of its CSR buffers and
-of the half-sweep work buffers, final-level sweep throughput, cost and
-marginal errors.
+cells the local safeguard of §7.3 re-solved (and kept at a larger ε),
+Sinkhorn iterations and Newton steps, peak entries of (ν_i) and peak device
+memory of its CSR buffers and of the half-sweep work buffers, final-level
+sweep throughput, cost and marginal errors.
 
     python -m paper_2001_10986_gb300.full_form [--dual-refine 0 1] [--learned]
 """
@@ -79,6 +79,7 @@ def run(dual_refine: int = 0, mlp=None, workload: str = "gm2048_b4_l5", err: flo
             "seconds_schedule": t_sched, "seconds_to_converged": seconds, "converged": done, "final_sweeps": k,
             "cells_not_converged_after_schedule": nc_sched, "cells_not_converged_last": st.cells_not_converged,
             "rescued_cells_schedule": p_sched.rescued_cells, "rescued_cells": p.rescued_cells,
+            "escalated_cells": p.escalated_cells,
             "sinkhorn_iters": p.sinkhorn_iters, "newton_steps": p.newton_steps,
             "peak_entries": p.peak_nnz, "peak_state_bytes": p.peak_state_bytes,
             "peak_work_bytes": p.peak_work_bytes, "entries_final": nnz,
