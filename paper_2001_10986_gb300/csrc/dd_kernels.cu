@@ -169,7 +169,7 @@ __device__ __forceinline__ uint64_t frac_to_u64(float f) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// S1: gather ν_cell (Algorithm 2, line "ν_cell ← Σ_{i∈J} ν_i")
+// S1: gather ν_cell = Σ_{i∈J} ν_i (Algorithm 2)
 // ---------------------------------------------------------------------------
 constexpr int kGatherStage = 3072;   // entries of a cell's rows staged in shared memory
 constexpr int kGatherThreads = 256;  // threads of a gather CTA

@@ -187,3 +187,70 @@ def test_coupling_image(lib, tmp_path):
     lib.write_ppm(path, img)
     data = path.read_bytes()
     assert data.startswith(b"P6\n4 4\n255\n") and len(data) == len(b"P6\n4 4\n255\n") + 48
+
+
+@pytest.mark.parametrize("n,b", [(16, 4), (24, 4), (40, 4), (32, 8), (36, 2)])
+def test_gluing_graph_is_the_nine_point_stencil(n, b):
+    # The GPU gluing stores no edge list: on the grid of A cells (row-major,
+    # A cell (R, C) = basic cells {2R, 2R+1} × {2C, 2C+1}) it applies the
+    # Laplacian DᵀD of the oracle's gluing graph as a 9-point stencil with
+    # weight 4 on the 4-neighbours and 2 on the diagonal ones, and builds
+    # the right-hand side −Dᵀ log q (log q = s⁺_i + s⁻_{i'} for the ordered
+    # pair (i, i') of basic cells of one B cell) per A cell from the B cells
+    # at its four corners. Both against the oracle's edges, for grids whose
+    # A-cell count is and is not a multiple of the 8 CTAs of the CG.
+    prob = odd.GridProblem(syn.gaussian_mixture(n, 2, 0), syn.gaussian_mixture(n, 2, 1), b, 1.0 / n)
+    nb = n // b
+    na = nb // 2
+    A = prob.parts["A"]
+    assert len(A) == na * na
+    for j, J in enumerate(A):   # row-major A cells, as on the device
+        R, C = divmod(j, na)
+        cells = sorted((i // nb, i % nb) for i in J)
+        assert cells == [(2 * R + dr, 2 * C + dc) for dr in (0, 1) for dc in (0, 1)]
+    edges = odd.gluing_graph(prob)
+    L = np.zeros((na * na, na * na))
+    for j1, j2, _, _, _ in edges:
+        L[j1, j1] += 1
+        L[j2, j2] += 1
+        L[j1, j2] -= 1
+        L[j2, j1] -= 1
+    S = np.zeros_like(L)
+    for R in range(na):
+        for C in range(na):
+            for dr in (-1, 0, 1):
+                for dc in (-1, 0, 1):
+                    R2, C2 = R + dr, C + dc
+                    if (dr, dc) == (0, 0) or not (0 <= R2 < na and 0 <= C2 < na):
+                        continue
+                    w = 4.0 if dr == 0 or dc == 0 else 2.0
+                    S[R * na + C, R2 * na + C2] -= w
+                    S[R * na + C, R * na + C] += w
+    assert np.array_equal(L, S)
+    # right-hand side from random s± per basic cell
+    rng = np.random.default_rng(5)
+    sp = rng.normal(size=nb * nb)
+    sm = rng.normal(size=nb * nb)
+
+    def basic_of(X):
+        r, c = divmod(int(X[0]), n)
+        return (r // b) * nb + c // b
+
+    rhs = np.zeros(na * na)
+    for j1, j2, _, X1, X2 in edges:
+        lq = sp[basic_of(X1)] + sm[basic_of(X2)]
+        rhs[j1] -= lq
+        rhs[j2] += lq
+    corner = np.zeros(na * na)
+    for R in range(na):
+        for C in range(na):
+            for dr in (0, 1):
+                for dc in (0, 1):
+                    Rb, Cb = R + dr, C + dc
+                    own = (2 * R + dr) * nb + 2 * C + dc
+                    for ei in (2 * Rb - 1, 2 * Rb):
+                        for ej in (2 * Cb - 1, 2 * Cb):
+                            o = ei * nb + ej
+                            if 0 <= ei < nb and 0 <= ej < nb and o != own:
+                                corner[R * na + C] += sp[o] + sm[own] - sp[own] - sm[o]
+    assert np.allclose(corner, rhs, rtol=0, atol=1e-12)
