@@ -1637,8 +1637,10 @@ __global__ void __maxnreg__(168) k_sinkhorn(SweepArgs a) {
 // cell, solves at 4ε, 16ε, … up to 4^escalate·ε, each warm-started from the
 // duals the last one ended with, until one converges. After a solve converged
 // at 4ε the cell is solved at ε from that result, and again at 4ε if that
-// fails; a kept solve at a larger ε sets status bit 3. A kernel of its own,
-// so that the attempt loop leaves the main solve kernel's registers alone.
+// fails; a kept solve at a larger ε sets status bit 3. The attempts at 16ε
+// and above and the repeat at 4ε stop after max_iter/4 iterations. A kernel
+// of its own, so that the attempt loop leaves the main solve kernel's
+// registers alone.
 __global__ void __maxnreg__(168) k_sinkhorn_safeguard(SweepArgs a) {
   __shared__ SinkSmem sm;
   __shared__ int s_pos, s_stop, s_step, s_phase, s_more;
@@ -1665,6 +1667,7 @@ __global__ void __maxnreg__(168) k_sinkhorn_safeguard(SweepArgs a) {
       s_step = 1;
       s_phase = 0;   // 0: escalating; 1: at ε after 4ε converged; 2: 4ε again
       s_args.eps = a.eps * s_f;
+      s_args.max_iter = a.max_iter;
     }
     __syncthreads();
     for (;;) {
@@ -1695,6 +1698,11 @@ __global__ void __maxnreg__(168) k_sinkhorn_safeguard(SweepArgs a) {
         }
         if (keep) a.cell_status[J] |= 8;
         s_args.eps = more ? a.eps * s_f : a.eps;
+        // the attempts at 16ε and above, and the repeat at 4ε, get a quarter
+        // of max_iter: a solve that needs more at a larger ε is better taken
+        // one factor further, and the attempts of one cell run one after
+        // another in one CTA, at the tail of the launch
+        s_args.max_iter = (more && (s_step > 1 || s_phase == 2)) ? max(a.max_iter / 4, 64) : a.max_iter;
         s_more = more;
       }
       __syncthreads();
