@@ -316,10 +316,10 @@ dd_status dd_objective(dd_ctx* ctx, int32_t partition, double eps, double* prima
  * Outputs (host, each may be NULL): alpha_hat (n_l² FP64, absolute frame as
  * dd_get_duals, 0 on pixels without mass), V ((n_l/2b)² FP64, row-major over
  * the A cells), *cg_iters, *rel_residual. Allocates and frees device scratch
- * (about 16 bytes per pixel); synchronises the stream; leaves the state as it
- * was. DD_ERR_CAPACITY when the A cells exceed 256 per side (the CG runs on
- * one cluster of 8 CTAs that holds at most 256 rows of 256 cells);
- * DD_ERR_NOT_CONVERGED (outputs written) when the CG stopped at its
+ * (8 bytes per pixel and 16 per basic cell); synchronises the stream; leaves
+ * the state as it was. DD_ERR_CAPACITY when the A cells exceed 256 per side
+ * (the CG runs on one cluster of 8 CTAs that holds at most 256 rows of 256
+ * cells); DD_ERR_NOT_CONVERGED (outputs written) when the CG stopped at its
  * iteration limit. */
 dd_status dd_glue_duals(dd_ctx* ctx, double* alpha_hat, double* V, int32_t* cg_iters, double* rel_residual);
 
@@ -338,8 +338,9 @@ dd_status dd_glue_duals(dd_ctx* ctx, double* alpha_hat, double* V, int32_t* cg_i
  * exponentials of the inner sums FP32 after an FP64 shift by their maximum
  * (the precision of the coupling's entries); S is accumulated with atomic
  * additions, so the last digits may vary from call to call. Outputs may be
- * NULL. Allocates and frees device scratch (about 40 bytes per pixel and 8
- * per stored entry); synchronises the stream; leaves the state as it was.
+ * NULL. Allocates and frees device scratch (24 bytes per pixel, 8 per
+ * gathered support point and 16 per composite cell); synchronises the
+ * stream; leaves the state as it was.
  * DD_ERR_STATE before the first half-sweep of a level or when a pixel with
  * ν > 0 carries no entry of the coupling; DD_ERR_CAPACITY and
  * DD_ERR_NOT_CONVERGED as dd_glue_duals. */
