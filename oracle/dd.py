@@ -53,6 +53,11 @@ the design notes of the repository):
 * Composite cells that consist of one basic cell (corners of partition B) are
   solved like the others; Example 3.3 shows it is redundant for the basic
   marginals, and solving keeps the duals of partition B complete.
+* The local safeguard of §7.3 ("temporarily increasing ε"; off unless
+  Params.safeguard): a cell whose solve stops at max_iter with an X-error
+  above 10·Err·‖μ_J‖ is solved again at 4ε, then at ε (4ε once more if ε
+  fails), else at 16ε … 4⁶ε, keeping the first solve that converges
+  (safeguard_solve).
 """
 from __future__ import annotations
 
@@ -70,6 +75,9 @@ class Params:
     max_iter: int = 10000      # cap on Sinkhorn iterations per cell solve
     trunc: float = 1e-15       # Truncate threshold on ν_i entries (§7.1)
     balance: bool = True       # run BalanceMeasures (§6.2)
+    safeguard: bool = False    # the local safeguard of §7.3 (see safeguard_solve)
+    main_max_iter: int = 0     # > 0: cap of the first solve of each cell only (the
+                               # safeguard's re-solves keep max_iter): a forced failure
 
 
 # ----------------------------------------------------------------------------
@@ -242,6 +250,58 @@ class SweepInfo:
     err_x: float = 0.0                 # Σ_J Σ_x |P_X π_J(x) − μ(x)|
     iters: list = field(default_factory=list)
     truncated_mass: float = 0.0
+    converged: list = field(default_factory=list)   # per cell: the kept solve met its stopping test
+    eps_used: list = field(default_factory=list)    # per cell: ε of the kept solve
+    rescued: int = 0                   # cells the safeguard solved again
+    escalated: int = 0                 # of these, cells kept at a larger ε
+
+
+SAFEGUARD_FACTOR = 4.0   # ε factor of each safeguard attempt
+SAFEGUARD_STEPS = 6      # attempts up to SAFEGUARD_FACTOR**6·ε
+
+
+def solve_converged(P, mu_x, nu_y, err):
+    """The stopping test of sinkhorn_cell for a plan P: Σ_x |P_X π − μ·‖ν‖/‖μ‖|
+    ≤ ‖μ‖·Err."""
+    target = mu_x * (nu_y.sum() / mu_x.sum())
+    return bool(np.abs(P.sum(axis=1) - target).sum() <= err * mu_x.sum())
+
+
+def safeguard_solve(C, mu_x, nu_y, alpha_x, eps, err, max_iter):
+    """The local safeguard of §7.3 ("fixed locally, e.g. by temporarily
+    increasing ε") for a cell whose solve at ε stopped at max_iter with an
+    X-error above 10·Err·‖μ_J‖. The paper fixes neither the factor nor the
+    order; read here as: solve at 4ε from the duals α the failed solve ended
+    with; if that converges, solve at ε from its result, and if that fails,
+    at 4ε once more; if 4ε fails, at 16ε, 64ε, … up to 4⁶ε (max_iter/4
+    iterations each, at least 64), keeping the first solve that converges. ε·log u = α carries over from one ε to the next (as at a
+    change of ε in §6.4). Returns f, g, P, total iterations, the unscaled
+    X-error, the ε of the kept solve and whether it converged."""
+    logmu = np.log(mu_x)
+    short = max(max_iter // 4, 64)
+    total = 0
+
+    def attempt(alpha, e, cap):
+        nonlocal total
+        f, g, P, it, ex = sinkhorn_cell(C, mu_x, nu_y, alpha + e * logmu, e, err, cap)
+        total += it
+        return f, g, P, ex, f - e * logmu, solve_converged(P, mu_x, nu_y, err)
+
+    e4 = SAFEGUARD_FACTOR * eps
+    f, g, P, ex, a4, ok = attempt(alpha_x, e4, max_iter)
+    if ok:
+        f1, g1, P1, ex1, a1, ok1 = attempt(a4, eps, max_iter)
+        if ok1:
+            return f1, g1, P1, total, ex1, eps, True
+        f, g, P, ex, _, ok = attempt(a1, e4, max_iter)
+        return f, g, P, total, ex, e4, ok
+    e, a = e4, a4
+    for _ in range(2, SAFEGUARD_STEPS + 1):
+        e *= SAFEGUARD_FACTOR
+        f, g, P, ex, a, ok = attempt(a, e, short)
+        if ok:
+            break
+    return f, g, P, total, ex, e, ok
 
 
 def half_sweep(prob, part, rows, alpha, eps, params, plans=None, cells=None):
@@ -268,9 +328,21 @@ def half_sweep(prob, part, rows, alpha, eps, params, plans=None, cells=None):
         live = mu_x > 0
         C = prob.cost(X[live], cols)
         f0 = alpha[X[live]] + eps * np.log(mu_x[live])
-        f, g, P_live, it, err_x = sinkhorn_cell(C, mu_x[live], nu_cell, f0, eps, params.err, params.max_iter)
-        alpha[X[live]] = f - eps * np.log(mu_x[live])
+        cap = params.main_max_iter if params.main_max_iter > 0 else params.max_iter
+        f, g, P_live, it, err_x = sinkhorn_cell(C, mu_x[live], nu_cell, f0, eps, params.err, cap)
+        ok = solve_converged(P_live, mu_x[live], nu_cell, params.err)
+        e_used = eps
+        if params.safeguard and not ok and err_x > 10.0 * params.err * mu_x[live].sum():
+            a_fail = f - eps * np.log(mu_x[live])
+            f, g, P_live, it2, err_x, e_used, ok = safeguard_solve(C, mu_x[live], nu_cell, a_fail, eps,
+                                                                   params.err, params.max_iter)
+            it += it2
+            info.rescued += 1
+            info.escalated += int(ok and e_used != eps)
+        alpha[X[live]] = f - e_used * np.log(mu_x[live])
         alpha[X[~live]] = 0.0
+        info.converged.append(ok)
+        info.eps_used.append(e_used)
         P = np.zeros((X.size, cols.size))
         P[live] = P_live
         info.cost += float((C * P_live).sum())

@@ -1638,7 +1638,7 @@ __global__ void __maxnreg__(168) k_sinkhorn(SweepArgs a) {
 // duals the last one ended with, until one converges. After a solve converged
 // at 4ε the cell is solved at ε from that result, and again at 4ε if that
 // fails; a kept solve at a larger ε sets status bit 3. The attempts at 16ε
-// and above and the repeat at 4ε stop after max_iter/4 iterations. A kernel
+// and above stop after max_iter/4 iterations. A kernel
 // of its own, so that the attempt loop leaves the main solve kernel's
 // registers alone.
 __global__ void __maxnreg__(168) k_sinkhorn_safeguard(SweepArgs a) {
@@ -1698,11 +1698,12 @@ __global__ void __maxnreg__(168) k_sinkhorn_safeguard(SweepArgs a) {
         }
         if (keep) a.cell_status[J] |= 8;
         s_args.eps = more ? a.eps * s_f : a.eps;
-        // the attempts at 16ε and above, and the repeat at 4ε, get a quarter
-        // of max_iter: a solve that needs more at a larger ε is better taken
-        // one factor further, and the attempts of one cell run one after
-        // another in one CTA, at the tail of the launch
-        s_args.max_iter = (more && (s_step > 1 || s_phase == 2)) ? max(a.max_iter / 4, 64) : a.max_iter;
+        // the attempts at 16ε and above get a quarter of max_iter: a solve
+        // that needs more at a larger ε is better taken one factor further,
+        // and the attempts of one cell run one after another in one CTA, at
+        // the tail of the launch (the repeat at 4ε starts from the failed
+        // solve at ε and gets all of max_iter, as the first solve at 4ε did)
+        s_args.max_iter = (more && s_step > 1) ? max(a.max_iter / 4, 64) : a.max_iter;
         s_more = more;
       }
       __syncthreads();

@@ -734,3 +734,67 @@ def test_fill_massless_affine_reproduces_an_affine_dual():
     np.testing.assert_allclose(out, alpha, rtol=0, atol=1e-11)
     live = prob.mu > 0
     np.testing.assert_array_equal(out[live], scrambled[live])
+
+
+def _cell_optimum(prob, rows, J, e):
+    """The cell problem's entropic optimum at ε = e, solved from zero duals
+    to a tight tolerance (independent of any warm start)."""
+    cols, nu_cell = dd.gather(rows, J)
+    X = prob.cell_points(J)
+    live = prob.mu[X] > 0
+    C = prob.cost(X[live], cols)
+    _, _, P, _, _ = dd.sinkhorn_cell(C, prob.mu[X][live], nu_cell, np.zeros(int(live.sum())), e, 1e-12, 200000)
+    return P
+
+
+def test_safeguard_keeps_the_cell_optimum_of_a_larger_eps():
+    # §7.3 safeguard: a cold start at a small ε with 60 iterations per solve;
+    # every cell fails at ε and is kept at 4ε or 16ε. The kept plan is the
+    # cell problem's optimum at that ε (an independent tight solve), and the
+    # state stays feasible (Σ_i ν_i = ν, ‖ν_i‖ = ‖μ_i‖)
+    n, eps = 16, 0.002
+    mu = syn.gaussian_mixture(n, 3, 60)
+    nu = syn.gaussian_mixture(n, 3, 61)
+    prob = dd.GridProblem(mu / mu.sum(), nu / nu.sum(), 4, 1.0 / n)
+    rows = dd.product_state(prob)
+    plans = {}
+    new_rows, info = dd.half_sweep(prob, "A", rows, np.zeros(n * n), eps,
+                                   dd.Params(err=1e-6, max_iter=60, safeguard=True), plans=plans)
+    assert info.rescued == 4 and info.escalated == 4 and all(info.converged)
+    assert sorted({round(e / eps) for e in info.eps_used}) == [4, 16]
+    for jn, J in enumerate(prob.parts["A"]):
+        X, cols, P = plans[jn]
+        live = prob.mu[X] > 0
+        want = _cell_optimum(prob, rows, J, info.eps_used[jn])
+        assert np.abs(P[live] - want).sum() <= 1e-4 * want.sum()
+    assert dd.y_marginal_error(prob, new_rows) <= info.truncated_mass + 1e-14
+    for i, (c, v) in enumerate(new_rows):
+        if i in {k for J in prob.parts["A"] for k in J}:
+            assert abs(v.sum() - prob.basic_mass[i]) <= 1e-13
+    # without the safeguard the same solves stop at max_iter far from the tolerance
+    _, info0 = dd.half_sweep(prob, "A", rows, np.zeros(n * n), eps, dd.Params(err=1e-6, max_iter=60))
+    assert not any(info0.converged) and info0.rescued == 0
+
+
+def test_safeguard_rescues_a_forced_failure_at_eps():
+    # the first solve of every cell cut off after one iteration (from duals
+    # converged at 2ε, far from the ε optimum): the safeguard solves at 4ε,
+    # then at ε, and keeps ε; the result is the plain half-sweep's at ε
+    n, eps = 16, 0.004
+    mu = syn.gaussian_mixture(n, 3, 62)
+    nu = syn.gaussian_mixture(n, 3, 63)
+    prob = dd.GridProblem(mu / mu.sum(), nu / nu.sum(), 4, 1.0 / n)
+    rows = dd.product_state(prob)
+    alpha = np.zeros(n * n)
+    p = dd.Params(err=1e-9, max_iter=20000)
+    for _ in range(6):
+        rows, _ = dd.half_sweep(prob, "A", rows, alpha, 2 * eps, p)
+        rows, _ = dd.half_sweep(prob, "B", rows, alpha, 2 * eps, p)
+    a_plain, a_safe = alpha.copy(), alpha.copy()
+    want, _ = dd.half_sweep(prob, "A", rows, a_plain, eps, dd.Params(err=1e-9, max_iter=20000))
+    got, info = dd.half_sweep(prob, "A", rows, a_safe, eps,
+                              dd.Params(err=1e-9, max_iter=20000, safeguard=True, main_max_iter=1))
+    assert info.rescued == 4 and info.escalated == 0 and all(info.converged)
+    assert all(e == eps for e in info.eps_used)
+    D1, D2 = dd.rows_to_dense(got, n * n), dd.rows_to_dense(want, n * n)
+    assert np.abs(D1 - D2).sum() <= 1e-7
