@@ -410,31 +410,6 @@ def partition_plan(prob, part, rows, alpha, eps):
     return P
 
 
-def partition_plan_sparse(prob, part, rows, alpha, eps, trunc=0.0):
-    """Same coupling as partition_plan as (row_ptr, col, val) over X pixels,
-    keeping entries above `trunc`."""
-    per_x = {}
-    for J in prob.parts[part]:
-        cols, nu_cell = gather(rows, J)
-        X = prob.cell_points(J)
-        C = prob.cost(X, cols)
-        f = alpha[X] + eps * np.log(prob.mu[X])
-        g = eps * np.log(nu_cell) - eps * logsumexp((f[:, None] - C) / eps, axis=0)
-        P = np.exp((f[:, None] + g[None, :] - C) / eps)
-        for r, x in enumerate(X):
-            keep = P[r] > trunc
-            per_x[int(x)] = (cols[keep], P[r][keep])
-    nx = prob.mu.size
-    row_ptr = np.zeros(nx + 1, dtype=np.int64)
-    cs, vs = [], []
-    for x in range(nx):
-        c, v = per_x.get(x, (np.zeros(0, np.int64), np.zeros(0)))
-        row_ptr[x + 1] = row_ptr[x] + c.size
-        cs.append(c)
-        vs.append(v)
-    return row_ptr, np.concatenate(cs), np.concatenate(vs)
-
-
 def cell_objectives(prob, part, rows, alpha, eps):
     """Objective values of the coupling of partition_plan, cell by cell (§6.3:
     the primal score is summed over the composite cells of the last loop).
