@@ -254,3 +254,48 @@ def test_gluing_graph_is_the_nine_point_stencil(n, b):
                             if 0 <= ei < nb and 0 <= ej < nb and o != own:
                                 corner[R * na + C] += sp[o] + sm[own] - sp[own] - sm[o]
     assert np.allclose(corner, rhs, rtol=0, atol=1e-12)
+
+
+def test_host_functions_reject_what_the_header_rejects(lib):
+    # the error paths documented in dd.h for the host functions (no GPU)
+    n, b = 16, 4
+    mu = syn.gaussian_mixture(n, 2, 70)
+    nu = syn.gaussian_mixture(n, 2, 71)
+    a = np.zeros(n * n)
+
+    def status(fn, *args):
+        with pytest.raises(lib.DDError) as e:
+            fn(*args)
+        return e.value.status
+
+    # gluing: n/b odd, a basic cell without mass, negative μ, non-finite α, ε ≤ 0
+    assert status(lib.dd_glue_duals_host, np.ones((12, 12)), np.zeros(144), np.zeros(144), 4, 0.1) == lib.DD_ERR_ARG
+    m0 = mu.copy()
+    m0[:b, :b] = 0.0
+    assert status(lib.dd_glue_duals_host, m0, a, a, b, 0.1) == lib.DD_ERR_ARG
+    m1 = mu.copy()
+    m1[3, 3] = -1e-9
+    assert status(lib.dd_glue_duals_host, m1, a, a, b, 0.1) == lib.DD_ERR_ARG
+    a1 = a.copy()
+    a1[7] = np.inf
+    assert status(lib.dd_glue_duals_host, mu, a1, a, b, 0.1) == lib.DD_ERR_ARG
+    assert status(lib.dd_glue_duals_host, mu, a, a, b, 0.0) == lib.DD_ERR_ARG
+    # the gap: an entry of π where ν has no mass, a pixel with ν > 0 that π
+    # does not reach, a negative entry
+    prob = odd.GridProblem(mu, nu, b, 1.0 / n)
+    P = np.outer(prob.mu, prob.nu)
+    rp, col, val = _csr(P)
+    rel, _, _ = lib.dd_relative_pd_gap_host(mu, nu, 0.05, (rp, col, val), a)
+    assert np.isfinite(rel)
+    nu0 = nu.copy().ravel()
+    nu0[int(col[0])] = 0.0
+    assert status(lib.dd_relative_pd_gap_host, mu, nu0.reshape(n, n), 0.05, (rp, col, val), a) == lib.DD_ERR_ARG
+    P2 = P.copy()
+    P2[:, 5] = 0.0
+    assert status(lib.dd_relative_pd_gap_host, mu, nu, 0.05, _csr(P2), a) == lib.DD_ERR_ARG
+    v2 = val.copy()
+    v2[3] = -v2[3]
+    assert status(lib.dd_relative_pd_gap_host, mu, nu, 0.05, (rp, col, v2), a) == lib.DD_ERR_ARG
+    # the image: a column outside the image
+    rows = [(np.array([n * n]), np.array([1.0]))]
+    assert status(lib.dd_coupling_image_host, n, _rows_csr(rows), np.zeros((1, 3), np.float32)) == lib.DD_ERR_ARG
